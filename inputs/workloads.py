@@ -1,0 +1,103 @@
+"""Workload definitions (pure data, no arithmetic of the method).
+
+Each workload fixes the box, the particle lattice, the Information Optimized
+Storage (IOS) mesh, the PM levels (coarsest first, each with its softening
+factor beta in its own mesh cells), the PP softening b_PP, the cosmology and
+the time span.  Both the CUDA path and the FP64 oracle read these records;
+each derives its own softening/truncation lengths from them.
+
+Cosmology and spectrum follow the workload recipe of this project: flat
+LCDM with Omega_m = 0.3, Omega_L = 0.7, h = 0.7, sigma_8 = 0.8, a BBKS
+transfer function and Zel'dovich initial conditions.  The paper's own runs
+(Sec. 3.2) use CAMB spectra at z_i = 200; those inputs are not reproduced.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field, replace
+
+
+@dataclass(frozen=True)
+class Level:
+    n_mesh: int      # mesh cells per dimension
+    beta: float      # softening length b = beta * H in this level's cells
+
+
+@dataclass(frozen=True)
+class Workload:
+    name: str
+    n_p: int                     # particles per dimension on the Lagrangian lattice
+    box: float                   # comoving box side L [Mpc/h]
+    n_ios: int                   # IOS cells per dimension (cell = PP cell)
+    levels: tuple                # tuple[Level], coarsest first
+    b_pp: float                  # PP softening [Mpc/h]
+    z_init: float = 49.0
+    z_final: float = 0.0
+    n_steps: int = 1
+    seed: int = 1
+    omega_m: float = 0.3
+    omega_l: float = 0.7
+    h: float = 0.7
+    sigma8: float = 0.8
+    # growth factor used for the displacement: None -> D(a_init);
+    # a float -> D at that scale factor (e.g. 1.0 for a z=0-like state)
+    displace_to_a: float | None = None
+
+    @property
+    def n_particles(self) -> int:
+        return self.n_p ** 3
+
+    @property
+    def a_init(self) -> float:
+        return 1.0 / (1.0 + self.z_init)
+
+    @property
+    def a_final(self) -> float:
+        return 1.0 / (1.0 + self.z_final)
+
+    def scale_factors(self):
+        """Constant-Delta-a schedule a_0 < a_1 < ... < a_{n_steps}."""
+        a0, a1 = self.a_init, self.a_final
+        return [a0 + (a1 - a0) * i / self.n_steps for i in range(self.n_steps + 1)]
+
+    def with_(self, **kw) -> "Workload":
+        return replace(self, **kw)
+
+
+# 32^3 particles, 64 Mpc/h, one 64^3 PM level with a 2-cell softening (= PP
+# cutoff), 1 force evaluation + 1 KDK step from z = 49.
+C1 = Workload(
+    name="pm1-32c-64mesh", n_p=32, box=64.0, n_ios=32,
+    levels=(Level(64, 2.0),), b_pp=0.2,
+    z_init=49.0, z_final=0.0, n_steps=50, seed=1,
+)
+
+# 256^3 particles, 256 Mpc/h, coarse 128^3 (beta 3.5) + fine 512^3 (beta 2),
+# FP32 velocities, 50 constant-Delta-a KDK steps z = 49 -> 0.
+C2 = Workload(
+    name="pm2-256c-128x512mesh", n_p=256, box=256.0, n_ios=256,
+    levels=(Level(128, 3.5), Level(512, 2.0)), b_pp=0.1,
+    z_init=49.0, z_final=0.0, n_steps=50, seed=2,
+)
+
+# Same recipe as C2 at 1/64 of the volume (64^3 particles, 32^3 + 128^3
+# meshes): the size used for element-wise parity of the two-level path.
+C2_SMALL = C2.with_(name="pm2-64c-32x128mesh", n_p=64, box=64.0, n_ios=64,
+                    levels=(Level(32, 3.5), Level(128, 2.0)), seed=12)
+
+# Differentiation workload: 128^3 particles, 128 Mpc/h, one 256^3 level,
+# 10 KDK steps z = 9 -> 0.
+C3 = Workload(
+    name="pm1-128c-256mesh", n_p=128, box=128.0, n_ios=128,
+    levels=(Level(256, 2.0),), b_pp=0.1,
+    z_init=9.0, z_final=0.0, n_steps=10, seed=3,
+)
+
+# 1024^3 particles, 1 Gpc/h, coarse 512^3 + fine 2048^3, one force
+# evaluation on a z=0-like Zel'dovich state.
+C5 = Workload(
+    name="pm2-1024c-512x2048mesh", n_p=1024, box=1000.0, n_ios=1024,
+    levels=(Level(512, 3.5), Level(2048, 2.0)), b_pp=0.1 * 1000.0 / 1024,
+    z_init=49.0, z_final=0.0, n_steps=1, seed=5, displace_to_a=1.0,
+)
+
+WORKLOADS = {w.name: w for w in (C1, C2, C2_SMALL, C3, C5)}
