@@ -1,0 +1,413 @@
+#!/usr/bin/env python
+"""Benchmark: particle-steps/s of the PM+PP force + KDK step on one GB300.
+
+Workload (default): 256^3 particles in a 256 Mpc/h box, two PM levels (coarse
+128^3 + fine 512^3), FP32 velocities, seeded Zel'dovich ICs at z = 49
+(BBKS spectrum), the 50-step constant-Delta-a KDK schedule to z = 0.  A step is
+one kdk_step of that schedule over the whole box (drift + re-bin, deposit on
+both meshes, both Poisson solves, interpolation, PP, both kicks).  W warm-up
+steps run first from the ICs; the state is then reset to the ICs and K steps
+are timed with CUDA events on the library's stream (K > 50 restarts the
+schedule from the ICs inside the timed region).
+
+Also reported on the same JSON line:
+  roofline      dominant kernel class: algorithmic bytes per launch / its mean
+                CUDA-event duration inside the timed region, against the
+                measured HBM copy bandwidth
+  e2e           the same metric through cube2_kdk_step_host with the particle
+                state in pinned host memory (H2D + step + D2H every step)
+  cpu_baseline  the FP64 oracle on a bounded sample of the same recipe
+  clocks        nvidia-smi samples taken during the timed region
+
+--impl reference times the FP64 oracle alone (this project's reference arm).
+With torchrun (N > 1) every rank runs an independent replica of the box
+(the single box does not shard; replicas only) and the slowest rank's time
+sets the aggregate.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "particle-steps/sec (PM+PP force + KDK) on 1 GB300; adjoint/forward ratio"
+UNIT = "particle-steps/s"
+HBM_FALLBACK_GBS = 6800.0
+SAMPLE_NP = 32          # oracle sample: same recipe as the workload at 32^3 particles
+
+
+def parse_args():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="cube2", choices=["cube2", "reference"])
+    ap.add_argument("--workload", default="pm2-256c-128x512mesh")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0, help="budget of the oracle sample")
+    return ap.parse_args()
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return HBM_FALLBACK_GBS, "fallback"
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+# ----------------------------------------------------------------- clocks
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, bus_id=None):
+        self.bus_id = bus_id
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            cmd = ["nvidia-smi", f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits", "-lms", "100"]
+            if self.bus_id:
+                cmd += ["-i", self.bus_id]
+            self.out = open(self.path, "w")
+            self.proc = subprocess.Popen(cmd, stdout=self.out, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.out.close()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for n, v in zip(names, r[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(rows)}
+
+
+def bus_id_of(dev):
+    try:
+        import torch
+        p = torch.cuda.get_device_properties(dev)
+        return f"{p.pci_domain_id:08X}:{p.pci_bus_id:02X}:{p.pci_device_id:02X}.0"
+    except Exception:
+        return None
+
+
+# ------------------------------------------------------ algorithmic bytes
+def algorithmic_bytes(w, n_part, cls, level):
+    """Compulsory HBM bytes of one launch group of a kernel class (each array once)."""
+    N, C = n_part, w.n_ios ** 3
+    meshes = [lv.n_mesh for lv in w.levels]
+    n = meshes[level] if level < len(meshes) else meshes[-1]
+    half = n * n * (n // 2 + 1)
+    table = {
+        "deposit": 6 * N + 8 * C + sum(4 * m ** 3 for m in meshes),
+        "fft_x_fwd": 4 * n ** 3 + 8 * half,
+        "fft_y_fwd": 16 * half,
+        "fft_z_green": 20 * half,
+        "fft_y_inv": 16 * half,
+        "fft_x_inv": 8 * half + 4 * n ** 3,
+        "interp": sum(4 * m ** 3 for m in meshes) + 22 * N,
+        "pp": 58 * N + 8 * C,
+        "kick": 36 * N,
+        "kick_drift": 68 * N + 4 * C,
+        "scan": 8 * C,
+        "scatter": 16 * N,
+        "sort": 8 * C + 8 * N,
+        "gather": 48 * N,
+        "cellid": 8 * C + 4 * N,
+        "green": 4 * half,
+    }
+    return table[cls]
+
+
+def traffic_record(kernel):
+    """ncu DRAM bytes per launch for `kernel` from profiles/traffic.json, if the
+    kernel's source is unchanged since the capture (else None)."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            rec = json.load(f).get(kernel)
+        if not rec:
+            return None
+        src = os.path.join(ROOT, "paper_2512_12629_gb300", "csrc", rec["source"])
+        digest = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        return rec["bytes_per_launch"] if digest == rec["sha256_16"] else None
+    except Exception:
+        return None
+
+
+# ------------------------------------------------------------- CPU oracle
+def oracle_sample(w, steps_budget_s, min_steps=1, max_steps=None):
+    """Time the FP64 oracle on the workload's recipe at SAMPLE_NP^3 particles.
+
+    Returns (particle-steps/s, steps, seconds, description)."""
+    from inputs.workloads import Level
+    from inputs.zeldovich import zeldovich_ios
+    from oracle import kdk as okdk
+    from oracle import mesh as omesh
+    scale = SAMPLE_NP / w.n_p
+    sw = w.with_(name=w.name + "-sample", n_p=SAMPLE_NP, box=w.box * scale, n_ios=int(w.n_ios * scale),
+                 levels=tuple(Level(int(lv.n_mesh * scale), lv.beta) for lv in w.levels))
+    st = zeldovich_ios(sw)
+    greens = omesh.green_tables(sw)
+    state = dict(off=st["off"], count=st["count"], start=st["start"], vel=st["vel"].astype("float64"))
+    state["acc"] = okdk.total_force(st["off"], st["count"], st["start"], sw, greens)
+    a = sw.scale_factors()
+    t0 = time.perf_counter()
+    k = 0
+    while True:
+        i = k % sw.n_steps
+        state = okdk.kdk_step(state, sw, a[i], a[i + 1], greens)
+        k += 1
+        el = time.perf_counter() - t0
+        if (k >= min_steps and el >= steps_budget_s) or (max_steps and k >= max_steps):
+            break
+    el = time.perf_counter() - t0
+    desc = (f"FP64 numpy oracle, {k} KDK steps of the same recipe scaled to {SAMPLE_NP}^3 particles "
+            f"(box {sw.box:g} Mpc/h, meshes {[lv.n_mesh for lv in sw.levels]}, IOS {sw.n_ios}^3), "
+            f"Green's tables built outside the timing")
+    return sw.n_particles * k / el, k, el, desc
+
+
+def run_reference(args, w):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return
+    from inputs.workloads import Level
+    from inputs.zeldovich import zeldovich_ios
+    from oracle import kdk as okdk
+    from oracle import mesh as omesh
+    scale = SAMPLE_NP / w.n_p
+    sw = w.with_(name=w.name + "-sample", n_p=SAMPLE_NP, box=w.box * scale, n_ios=int(w.n_ios * scale),
+                 levels=tuple(Level(int(lv.n_mesh * scale), lv.beta) for lv in w.levels))
+    st = zeldovich_ios(sw)
+    greens = omesh.green_tables(sw)
+    base = dict(off=st["off"], count=st["count"], start=st["start"], vel=st["vel"].astype("float64"))
+    base["acc"] = okdk.total_force(st["off"], st["count"], st["start"], sw, greens)
+    a = sw.scale_factors()
+    state = dict(base)
+    for k in range(args.warmup):
+        i = k % sw.n_steps
+        state = okdk.kdk_step(state, sw, a[i], a[i + 1], greens)
+    state = dict(base)
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        i = k % sw.n_steps
+        if i == 0 and k > 0:
+            state = dict(base)
+        state = okdk.kdk_step(state, sw, a[i], a[i + 1], greens)
+    el = time.perf_counter() - t0
+    value = sw.n_particles * args.steps / el
+    sample = (f"each step: one FP64 oracle KDK step of the workload recipe at {SAMPLE_NP}^3 particles "
+              f"(box {sw.box:g}, meshes {[lv.n_mesh for lv in sw.levels]})")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded Zel'dovich ICs, BBKS spectrum)", "config": workload_config(w),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def workload_config(w):
+    return {"workload": w.name, "particles": w.n_particles, "box_mpc_h": w.box,
+            "meshes": [lv.n_mesh for lv in w.levels], "ios_cells": w.n_ios,
+            "schedule": f"{w.n_steps} KDK steps z={w.z_init:g}->{w.z_final:g}, constant Delta a",
+            "l2": "inputs larger than L2 (>= 2 GB resident working set)", "parallelism": "replicas"}
+
+
+# ------------------------------------------------------------------ main
+def main():
+    args = parse_args()
+    from inputs.workloads import WORKLOADS
+    w = WORKLOADS[args.workload]
+    if args.impl == "reference":
+        run_reference(args, w)
+        return
+    import numpy as np
+    import torch
+    world, rank, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        dist = None
+        torch.cuda.set_device(0)
+    from paper_2512_12629_gb300 import build as pkg_build
+    pkg_build.build()
+    from inputs.zeldovich import zeldovich_ios
+    from paper_2512_12629_gb300 import cube2
+
+    st = zeldovich_ios(w)
+    n_part = int(st["count"].sum())
+    ctx = cube2.init_mesh(cube2.make_config(w, n_particles=n_part))
+    for l in range(len(w.levels)):
+        ctx.set_green(l)
+    p0 = cube2.IOSState.from_numpy(st)
+    ctx.force(p0)
+    p = p0.clone()
+    a = w.scale_factors()
+    S = w.n_steps
+
+    def reset(dst):
+        for x, y in zip((dst.off, dst.count, dst.start, dst.vel, dst.acc),
+                        (p0.off, p0.count, p0.start, p0.vel, p0.acc)):
+            x.copy_(y)
+
+    for k in range(args.warmup):
+        i = k % S
+        ctx.kdk_step(p, a[i], a[i + 1])
+    reset(p)
+    ctx.check()
+    torch.cuda.synchronize()
+
+    stream = ctx.stream
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ctx.profile(capacity=64 * (args.steps + 2))
+    launches0 = ctx.launch_count()
+    clocks = ClockSampler(bus_id_of(torch.cuda.current_device()))
+    clocks.start()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    for k in range(args.steps):
+        i = k % S
+        if i == 0 and k > 0:
+            reset(p)
+        ctx.kdk_step(p, a[i], a[i + 1])
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+    launches = ctx.launch_count() - launches0
+    ms = ev0.elapsed_time(ev1)
+    prof = ctx.profile_read()
+    ctx.profile(0)
+    ctx.check()
+    ms_max = ms
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_max = float(t.item())
+    value = n_part * args.steps * world / (ms_max / 1e3)
+
+    # dominant kernel class -> roofline
+    peak, peak_kind = peaks()
+    total_prof = sum(v[0] for v in prof.values())
+    dom = max(prof.items(), key=lambda kv: kv[1][0])
+    (cls, lvl), (dms, dcount) = dom
+    per_launch_ms = dms / dcount
+    alg = algorithmic_bytes(w, n_part, cls, lvl)
+    achieved = alg / (per_launch_ms / 1e3) / 1e9
+    kname = f"{cls}[level {lvl}]" if cls.startswith("fft") else cls
+    roofline = {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "peak_source": peak_kind,
+                "algorithmic_bytes_per_launch": alg, "mean_launch_ms": per_launch_ms,
+                "traffic": traffic_record(cls)}
+    kernels = {}
+    for (c, l), (kms, kc) in sorted(prof.items(), key=lambda kv: -kv[1][0]):
+        b = algorithmic_bytes(w, n_part, c, l)
+        kernels[f"{c}/{l}"] = {"share": kms / total_prof, "ms_per_launch": kms / kc, "launches": kc,
+                               "GBps_alg": b / (kms / kc / 1e3) / 1e9}
+
+    # end to end through the host-buffer entry point
+    e2e = None
+    if not args.no_e2e:
+        host = cube2.IOSState(*(x.cpu().pin_memory() for x in (p0.off, p0.count, p0.start, p0.vel, p0.acc)))
+        pe = p0.clone()
+        bytes_step = sum(x.numel() * x.element_size() for x in (host.off, host.count, host.start, host.vel, host.acc))
+        ctx.kdk_step_host(pe, host, a[0], a[1])                # warm
+        host = cube2.IOSState(*(x.cpu().pin_memory() for x in (p0.off, p0.count, p0.start, p0.vel, p0.acc)))
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        t0 = time.perf_counter()
+        for k in range(args.steps):
+            i = k % S
+            if i == 0 and k > 0:
+                for x, y in zip((host.off, host.count, host.start, host.vel, host.acc),
+                                (p0.off, p0.count, p0.start, p0.vel, p0.acc)):
+                    x.copy_(y)
+            ctx.kdk_step_host(pe, host, a[i], a[i + 1])
+        el = time.perf_counter() - t0
+        if dist:
+            t = torch.tensor([el], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            el = float(t.item())
+        e2e = {"value": n_part * args.steps * world / el, "unit": UNIT,
+               "h2d_bytes_per_step": bytes_step, "d2h_bytes_per_step": bytes_step,
+               "api": "cube2_kdk_step_host (pinned host state, H2D + step + D2H each step)"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, k, el, desc = oracle_sample(w, args.cpu_seconds)
+        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc,
+               "seconds": el}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (seeded Zel'dovich ICs, BBKS spectrum)", "config": workload_config(w),
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+            "clocks": clk, "kernels": kernels,
+        }
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,210 @@
+/*
+ * cube2.h -- C ABI of the GB300 (sm_103a) multi-level PM + PP gravity step.
+ *
+ * Method: CUBE2 (Yu et al., Sci. China PMA 2026), Sec. 2.1 (force
+ * decomposition, optimised Green's function), Sec. 2.2 (kick/drift) and
+ * Sec. 2.3 (Information Optimized Storage, IOS).  Every operation below runs
+ * in hand-written CUDA kernels; nothing falls back to the CPU or to cuFFT.
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * - Periodic comoving box of side L [Mpc/h] (Sec. 2, periodic boundary
+ *   conditions).  Time variable is the scale factor a; H_0 = 1 units.
+ * - IOS (Sec. 2.3): the box is cut into n_ios^3 cells (linear id
+ *   c = (cz*n_ios + cy)*n_ios + cx, x fastest).  Particles are stored sorted by
+ *   cell; particle p of cell c has uint16 in-cell offsets off[d][p] in units
+ *   of 2^-16 cell, i.e. fixed-point coordinate X_d = c_d*2^16 + off_d.
+ *   count[c] is the number of particles in cell c and start[c] its exclusive
+ *   prefix sum, so the particles of c are [start[c], start[c]+count[c]).
+ *   The IOS order doubles as the PP cell list.
+ * - PM levels are numbered coarsest first.  Level l has an n_mesh[l]^3 mesh
+ *   whose cell H_l = L/n_mesh[l] relates to the IOS cell by a power of two
+ *   (n_ios/n_mesh[l] in {1/4, 1/2, 1, 2}); its softening is
+ *   b_l = beta[l]*H_l and its truncation is b_{l-1} (infinity for l = 0),
+ *   Eq. (force_decomp) and Eqs. (PM1)-(PM3).  The PP range is b_{last}
+ *   (must not exceed the IOS cell), the PP softening b_pp, Eq. (PP).
+ * - Force: acc = F = -grad u with lap u = delta (mean density one), in
+ *   Mpc/h units; the PP pair term is V_p R_PP(r)/(4 pi) with V_p = L^3/N.
+ * - Velocities are canonical momenta p = a^2 dx/dt.  dp/da = 1.5 Omega_m F /
+ *   (a^2 E(a)),  dx/da = p / (a^3 E(a)),  E = sqrt(Omega_m a^-3 + Omega_L).
+ *
+ * Memory and streams
+ * ------------------
+ * All particle arrays are DEVICE pointers owned by the caller (for instance
+ * torch tensors); the library never frees them.  cube2_init_mesh allocates
+ * every buffer the context needs (meshes, Green's tables, FFT spectrum,
+ * re-binning scratch) once; no later call allocates.  Every call enqueues
+ * work on the stream given to cube2_init_mesh and returns without waiting,
+ * except where stated.
+ *
+ * Errors
+ * ------
+ * Every call returns CUBE2_OK (0) or a negative CUBE2_ERR_* code and records
+ * a message readable with cube2_last_error.  Argument errors are detected on
+ * the host before any launch.  Errors found by kernels (uint64 deposit
+ * overflow, non-finite forces, an IOS displacement that cannot be encoded)
+ * set a sticky device status word; cube2_check synchronises the stream and
+ * returns it.  After a device error the particle state is unspecified.
+ */
+#ifndef CUBE2_H
+#define CUBE2_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define CUBE2_OK                    0
+#define CUBE2_ERR_BAD_ARG          -1  /* null pointer, bad level, size mismatch   */
+#define CUBE2_ERR_CUDA             -2  /* a CUDA runtime call failed               */
+#define CUBE2_ERR_CAPACITY         -3  /* a uint64 deposit cell overflowed          */
+#define CUBE2_ERR_TIMEOUT          -4  /* a bounded device wait ran out            */
+#define CUBE2_ERR_NONFINITE        -5  /* NaN/Inf in a force or velocity           */
+#define CUBE2_ERR_UNSUPPORTED_SIZE -6  /* mesh not 2^a 3^b, ratio not a power of 2 */
+#define CUBE2_ERR_STATE            -7  /* call order violated (no table/density)   */
+#define CUBE2_ERR_DISPLACEMENT     -8  /* drift moved a particle by >= n_ios/2     */
+
+#define CUBE2_MAX_LEVELS 2
+
+typedef struct cube2_ctx cube2_ctx;
+
+/* Problem definition (host struct, copied by cube2_init_mesh). */
+typedef struct {
+    double  box;                       /* L [Mpc/h]                               */
+    int32_t n_ios;                     /* IOS cells per dimension (>= 4)           */
+    int32_t n_levels;                  /* number of PM levels, 1 or 2              */
+    int32_t n_mesh[CUBE2_MAX_LEVELS];  /* mesh cells per dimension, coarsest first */
+    double  beta[CUBE2_MAX_LEVELS];    /* softening in own mesh cells              */
+    double  b_pp;                      /* PP softening [Mpc/h]                      */
+    double  omega_m, omega_l;          /* flat LCDM density parameters             */
+    int64_t n_particles;               /* particle count N (fixes V_p = L^3/N)     */
+    int32_t alias_max;                 /* images per axis in Eq. (Gk); 2 in paper  */
+} cube2_config;
+
+/* Particle set in IOS form; every pointer is a device pointer (see above). */
+typedef struct {
+    int64_t   n;          /* number of particles, must equal cfg.n_particles      */
+    uint16_t *off[3];     /* [3][n] in-cell offsets, SoA, sorted by IOS cell      */
+    int32_t  *count;      /* [n_ios^3] particles per IOS cell                      */
+    int32_t  *start;      /* [n_ios^3] exclusive prefix sum of count               */
+    float    *vel[3];     /* [3][n] canonical momenta (FP32)                       */
+    float    *acc[3];     /* [3][n] force F = -grad u (FP32, output of force calls) */
+} cube2_particles;
+
+/* Validate cfg, allocate the context and all device buffers, and build the
+ * FFT twiddle tables.  stream is a cudaStream_t (NULL = legacy default).
+ * The context is bound to the device current at this call.  Returns
+ * CUBE2_ERR_UNSUPPORTED_SIZE for meshes outside 2^a 3^b in [8, 2048] or level
+ * ratios that are not powers of two, CUBE2_ERR_BAD_ARG for other bad fields,
+ * CUBE2_ERR_CUDA if an allocation fails (nothing is leaked). */
+int cube2_init_mesh(cube2_ctx **ctx, const cube2_config *cfg, void *stream);
+
+/* Eq. (Gk) with Eqs. (Rk), (Sk), (diff) and the CIC W(k) = prod sinc^2(k_d/2),
+ * alias sum over |n_d| <= alias_max, evaluated in FP64 on the GPU for level
+ * `level` and stored as FP32 on the r2c half spectrum [kz][ky][kx <= n/2]
+ * with the inverse-FFT factor 1/n^3 folded in.  G = 0 where |D(k)| = 0.
+ * cache_path (optional, may be NULL) names a file: if it holds a table for
+ * the same (n, b_soft, b_trunc, alias) it is read instead of computed,
+ * otherwise the computed table is written there (Sec. 2.1.2: tables may be
+ * stored as files).  Synchronises the stream when a file is used. */
+int cube2_set_green(cube2_ctx *ctx, int level, const char *cache_path);
+
+/* CIC mass assignment (Eq. filter, CIC reading) of the particles onto level
+ * `level` (or every level in one particle pass when level = -1).  Integer
+ * fixed point: 1-D weights are exact integers at scale 2^16 of the mesh cell,
+ * the 3-D weight their product, accumulated as uint64 in shared-memory tiles
+ * (exact, so the result does not depend on order).  The internal FP32 grid is
+ * RN32(acc - M) * RN32(n^3/N * 2^-48) with M = floor(N 2^48 / n^3): the
+ * overdensity in mean-one units.  A uint64 wrap sets CUBE2_ERR_CAPACITY. */
+int cube2_deposit(cube2_ctx *ctx, int level, const cube2_particles *p);
+
+/* Test access: the exact uint64 accumulator of `level` for particles p,
+ * written to out ([n][n][n] uint64, device, x fastest).  Same kernel as
+ * cube2_deposit with an integer epilogue. */
+int cube2_deposit_u64(cube2_ctx *ctx, int level, const cube2_particles *p, uint64_t *out);
+
+/* Poisson solve of level `level` (Sec. 2.1.2): forward 3-D r2c FFT of the
+ * deposited grid (batched radix line passes along x, y, z), multiplication
+ * by G on the last forward pass, inverse 3-D c2r FFT.  Leaves phi (mesh
+ * units, lap phi = rho) in the level's real grid.  Needs cube2_set_green and
+ * cube2_deposit for that level first (else CUBE2_ERR_STATE). */
+int cube2_solve_pm(cube2_ctx *ctx, int level);
+
+/* Force interpolation (Sec. 2.1.2): E = D * phi with the 4-point difference
+ * of Eq. (diff) evaluated on the fly, gathered with the deposit's CIC
+ * weights, scaled to F = -H_l E.  level = -1 sums every level in one
+ * particle pass.  accumulate = 0 overwrites acc, 1 adds to it. */
+int cube2_interp_force(cube2_ctx *ctx, int level, const cube2_particles *p, int accumulate);
+
+/* PP force (Sec. 2.2.3, Eq. PP): for all pairs closer than the PP range,
+ * F_i += V_p (R(r,b_pp) - R(r,b_range))/(4 pi) (x_j - x_i)/r, separations
+ * formed exactly in fixed point over the 27 neighbouring IOS cells, FP32
+ * sums with Kahan compensation.  accumulate as above. */
+int cube2_pp_force(cube2_ctx *ctx, const cube2_particles *p, int accumulate);
+
+/* Full force: deposit every level, solve every level, interpolate, PP.
+ * Writes acc = F.  Requires every level's Green's table. */
+int cube2_force(cube2_ctx *ctx, const cube2_particles *p);
+
+/* One kick-drift-kick step a0 -> a1 (Secs. 2.2.3, 2.3, 3.2): requires acc
+ * to hold F at the current positions (from cube2_force or the previous step).
+ * p += 1.5 Om K(a0,ah) acc; X += rint(p Dr(a0,a1) 2^16/s_ios) mod n_ios 2^16
+ * (round half even); stable re-bin by new cell (ties keep the old order),
+ * rewriting off, count, start, vel in place; acc = F(new positions);
+ * p += 1.5 Om K(ah,a1) acc, with ah = (a0+a1)/2 and K, Dr Gauss-Legendre
+ * integrals of 1/(a^2 E) and 1/(a^3 E). */
+int cube2_kdk_step(cube2_ctx *ctx, cube2_particles *p, double a0, double a1);
+
+/* The same step for a particle set held in HOST memory (pinned for speed):
+ * copies host -> dev, runs cube2_kdk_step on dev, copies dev -> host (off,
+ * count, start, vel, acc), all on the context stream, then synchronises. */
+int cube2_kdk_step_host(cube2_ctx *ctx, cube2_particles *dev, cube2_particles *host,
+                        double a0, double a1);
+
+/* Test/diagnostic copies of internal grids into caller device buffers:
+ * density after cube2_deposit, potential after cube2_solve_pm ([n][n][n]
+ * FP32), Green's table ([n][n][n/2+1] FP32 including the 1/n^3 factor). */
+int cube2_get_density(cube2_ctx *ctx, int level, float *out);
+int cube2_get_potential(cube2_ctx *ctx, int level, float *out);
+int cube2_get_green(cube2_ctx *ctx, int level, float *out);
+
+/* Forward r2c FFT of the deposited grid only, written to out as interleaved
+ * complex FP32 [n][n][n/2+1] (unnormalised, numpy.fft.rfftn convention). */
+int cube2_debug_forward_fft(cube2_ctx *ctx, int level, float *out);
+
+/* Host helper: out = {K(a0,ah), Dr(a0,a1), K(ah,a1)} for cfg's cosmology. */
+int cube2_kdk_factors(const cube2_config *cfg, double a0, double a1, double out[3]);
+
+/* Synchronise the context stream, then return the sticky device status
+ * (CUBE2_OK or the first kernel-detected CUBE2_ERR_*), clearing it. */
+int cube2_check(cube2_ctx *ctx);
+
+/* Message of the last error recorded on ctx ("" if none); NULL ctx gives
+ * the message of the last failed cube2_init_mesh. */
+const char *cube2_last_error(cube2_ctx *ctx);
+
+/* Optional per-kernel-class timing with CUDA events on the context stream.
+ * cube2_profile(ctx, cap) discards earlier records and, for cap > 0, records
+ * a start/stop event pair around each launch group of the later calls (up to
+ * cap groups; cap = 0 switches profiling off).  cube2_profile_read
+ * synchronises, writes the summed milliseconds and group counts per
+ * (class, level) into ms[class * CUBE2_MAX_LEVELS + level] and
+ * counts[...] (arrays of CUBE2_PROFILE_CLASSES * CUBE2_MAX_LEVELS), clears the
+ * records, and returns CUBE2_ERR_CAPACITY if the pool overflowed.  Class
+ * names: cube2_profile_class_name. */
+#define CUBE2_PROFILE_CLASSES 16
+int cube2_profile(cube2_ctx *ctx, int cap);
+int cube2_profile_read(cube2_ctx *ctx, double *ms, int64_t *counts);
+const char *cube2_profile_class_name(int cls);
+
+/* Number of kernel launches this context has issued (for launch accounting). */
+int64_t cube2_launch_count(cube2_ctx *ctx);
+
+/* Free every buffer the context owns.  Synchronises its stream first. */
+void cube2_destroy(cube2_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CUBE2_H */

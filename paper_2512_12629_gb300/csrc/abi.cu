@@ -1,0 +1,572 @@
+// C ABI entry points of libcube2gb (declared in include/cube2.h): argument
+// validation, buffer ownership, stream ordering and the host-side scalars of
+// the kick-drift-kick step.  All particle and mesh arithmetic runs in the
+// kernels of deposit.cu, fft.cu, green.cu, interp.cu, pp.cu and kdk.cu.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+
+namespace cube2 {
+bool fft_size_supported(int n);
+
+int set_error(cube2_ctx *ctx, int code, const std::string &msg) {
+    if (ctx) ctx->err = msg;
+    return code;
+}
+
+int prof_begin(cube2_ctx *ctx, int cls, int level) {
+    if (!ctx->prof) return -1;
+    if (ctx->prof_used >= ctx->prof_cap) { ctx->prof_overflow = 1; return -1; }
+    const int slot = ctx->prof_used++;
+    ctx->prof_cls[slot] = cls * CUBE2_MAX_LEVELS + level;
+    cudaEventRecord(ctx->ev[2 * slot], ctx->stream);
+    return slot;
+}
+
+void prof_end(cube2_ctx *ctx, int slot) {
+    if (slot >= 0) cudaEventRecord(ctx->ev[2 * slot + 1], ctx->stream);
+}
+
+int cuda_error(cube2_ctx *ctx, cudaError_t e, const char *what) {
+    return set_error(ctx, CUBE2_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+namespace {
+
+thread_local std::string g_init_error;
+
+// Gauss-Legendre nodes/weights on [-1, 1] by Newton iteration on P_n.
+void gauss_legendre(int n, std::vector<double> &x, std::vector<double> &w) {
+    x.assign(n, 0.0);
+    w.assign(n, 0.0);
+    for (int i = 0; i < n; ++i) {
+        double z = cos(M_PI * (i + 0.75) / (n + 0.5));
+        double dp = 0.0;
+        for (int it = 0; it < 100; ++it) {
+            double p0 = 1.0, p1 = z;
+            for (int k = 2; k <= n; ++k) {
+                const double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+                p0 = p1;
+                p1 = p2;
+            }
+            dp = n * (z * p1 - p0) / (z * z - 1.0);
+            const double dz = p1 / dp;
+            z -= dz;
+            if (fabs(dz) < 1e-16) break;
+        }
+        x[i] = z;
+        w[i] = 2.0 / ((1.0 - z * z) * dp * dp);
+    }
+}
+
+double integrate(double a0, double a1, double om, double ol, int power) {
+    static std::vector<double> gx, gw;
+    if (gx.empty()) gauss_legendre(48, gx, gw);
+    const double mid = 0.5 * (a0 + a1), half = 0.5 * (a1 - a0);
+    double s = 0.0;
+    for (size_t i = 0; i < gx.size(); ++i) {
+        const double a = mid + half * gx[i];
+        const double e = sqrt(om / (a * a * a) + ol);
+        s += gw[i] / (pow(a, power) * e);
+    }
+    return half * s;
+}
+
+int ilog2_ratio(int big, int small) {
+    if (small <= 0 || big % small) return -100;
+    int q = big / small, s = 0;
+    while ((1 << s) < q) ++s;
+    return (1 << s) == q ? s : -100;
+}
+
+int level_shift(int n_ios, int n) {
+    if (n_ios >= n) return ilog2_ratio(n_ios, n);
+    const int s = ilog2_ratio(n, n_ios);
+    return s == -100 ? -100 : -s;
+}
+
+void prof_free(cube2_ctx *c) {
+    if (c->ev) {
+        for (int i = 0; i < 2 * c->prof_cap; ++i) cudaEventDestroy(c->ev[i]);
+        delete[] c->ev;
+        delete[] c->prof_cls;
+    }
+    c->ev = nullptr;
+    c->prof_cls = nullptr;
+    c->prof_cap = c->prof_used = 0;
+    c->prof = false;
+}
+
+void free_ctx(cube2_ctx *c) {
+    if (!c) return;
+    prof_free(c);
+    for (int l = 0; l < CUBE2_MAX_LEVELS; ++l) {
+        cudaFree(c->lev[l].real);
+        cudaFree(c->lev[l].spec);
+        cudaFree(c->lev[l].green);
+        cudaFree(c->lev[l].tw);
+    }
+    cudaFree(c->cellid);
+    cudaFree(c->toff);
+    cudaFree(c->tvel);
+    cudaFree(c->tcell);
+    cudaFree(c->tslot);
+    cudaFree(c->perm);
+    cudaFree(c->scan_tmp);
+    cudaFree(c->ncount);
+    cudaFree(c->nstart);
+    cudaFree(c->far);
+    cudaFree(c->dev_status);
+    cudaFreeHost(c->host_status);
+    delete c;
+}
+
+bool particles_ok(cube2_ctx *ctx, const cube2_particles *p, bool need_vel, bool need_acc) {
+    if (!p) return false;
+    if (p->n != ctx->N) return false;
+    if (ctx->N == 0) return p->count && p->start;
+    for (int d = 0; d < 3; ++d) {
+        if (!p->off[d]) return false;
+        if (need_vel && !p->vel[d]) return false;
+        if (need_acc && !p->acc[d]) return false;
+    }
+    return p->count && p->start;
+}
+
+int level_ok(cube2_ctx *ctx, int level, bool allow_all) {
+    if (allow_all && level == -1) return CUBE2_OK;
+    if (level < 0 || level >= ctx->nl) return set_error(ctx, CUBE2_ERR_BAD_ARG, "level out of range");
+    return CUBE2_OK;
+}
+
+}  // namespace
+}  // namespace cube2
+
+using namespace cube2;
+
+extern "C" {
+
+int cube2_init_mesh(cube2_ctx **out, const cube2_config *cfg, void *stream) {
+    g_init_error.clear();
+    auto fail = [](int code, const std::string &m) { g_init_error = m; return code; };
+    if (!out || !cfg) return fail(CUBE2_ERR_BAD_ARG, "null ctx or config");
+    *out = nullptr;
+    if (!(cfg->box > 0) || cfg->n_ios < 4 || cfg->n_levels < 1 || cfg->n_levels > CUBE2_MAX_LEVELS ||
+        cfg->n_particles < 0 || cfg->n_particles > 2147483647LL || !(cfg->b_pp > 0) ||
+        !(cfg->omega_m > 0) || cfg->omega_l < 0 || cfg->alias_max < 0 || cfg->alias_max > 4)
+        return fail(CUBE2_ERR_BAD_ARG, "invalid config field");
+    if ((int64_t)cfg->n_ios * cfg->n_ios * cfg->n_ios > 2147483647LL)
+        return fail(CUBE2_ERR_UNSUPPORTED_SIZE, "n_ios^3 exceeds int32 cell ids");
+    for (int l = 0; l < cfg->n_levels; ++l) {
+        const int n = cfg->n_mesh[l];
+        if (!fft_size_supported(n)) return fail(CUBE2_ERR_UNSUPPORTED_SIZE, "mesh size not supported (2^a 3^b, 8..2048)");
+        const int s = level_shift(cfg->n_ios, n);
+        if (s < -2 || s > 1) return fail(CUBE2_ERR_UNSUPPORTED_SIZE, "n_ios / n_mesh must be 1/4, 1/2, 1 or 2");
+        if (!(cfg->beta[l] > 0)) return fail(CUBE2_ERR_BAD_ARG, "beta must be positive");
+        if (l > 0 && cfg->n_mesh[l] <= cfg->n_mesh[l - 1]) return fail(CUBE2_ERR_BAD_ARG, "levels must be coarsest first");
+    }
+    cube2_ctx *c = new cube2_ctx();
+    c->cfg = *cfg;
+    c->stream = (cudaStream_t)stream;
+    cudaGetDevice(&c->device);
+    c->nl = cfg->n_levels;
+    c->N = cfg->n_particles;
+    c->n_ios = cfg->n_ios;
+    c->n_cells = (int64_t)cfg->n_ios * cfg->n_ios * cfg->n_ios;
+    c->s_ios = cfg->box / cfg->n_ios;
+    double prev_b = -1.0;  // softening of the coarser level [Mpc/h]
+    for (int l = 0; l < c->nl; ++l) {
+        Level &L = c->lev[l];
+        L.index = l;
+        L.n = cfg->n_mesh[l];
+        L.kxp = ((L.n / 2 + 1) + 15) / 16 * 16;
+        L.shift = level_shift(cfg->n_ios, L.n);
+        L.H = cfg->box / L.n;
+        L.b_soft = cfg->beta[l];
+        L.b_trunc = prev_b < 0 ? -1.0 : prev_b / L.H;
+        prev_b = cfg->beta[l] * L.H;
+        const int64_t n3 = (int64_t)L.n * L.n * L.n;
+        // M = floor(N 2^48 / n^3) in 128-bit integer arithmetic
+        const unsigned __int128 num = (unsigned __int128)(uint64_t)c->N << 48;
+        L.mean_int = (uint64_t)(num / (unsigned __int128)n3);
+        L.dens_scale = c->N > 0 ? (float)((double)n3 / (double)c->N * ldexp(1.0, -48)) : 0.0f;
+    }
+    c->b_range = prev_b;
+    if (c->b_range > c->s_ios * (1.0 + 1e-12)) {
+        delete c;
+        return fail(CUBE2_ERR_BAD_ARG, "PP range (finest softening) exceeds the IOS cell");
+    }
+    if (cfg->b_pp >= c->b_range) {
+        delete c;
+        return fail(CUBE2_ERR_BAD_ARG, "b_pp must be below the PP range");
+    }
+    cudaError_t e = cudaSuccess;
+    auto alloc = [&](void **ptr, size_t bytes) {
+        if (e != cudaSuccess) return;
+        e = cudaMalloc(ptr, bytes > 0 ? bytes : 16);
+    };
+    for (int l = 0; l < c->nl; ++l) {
+        Level &L = c->lev[l];
+        const size_t n3 = (size_t)L.n * L.n * L.n;
+        const size_t nh = (size_t)L.n * L.n * L.kxp;
+        alloc((void **)&L.real, n3 * sizeof(float));
+        alloc((void **)&L.spec, nh * sizeof(float2));
+        alloc((void **)&L.green, nh * sizeof(float));
+        alloc((void **)&L.tw, (size_t)L.n * sizeof(float2));
+        if (e == cudaSuccess) e = cudaMemsetAsync(L.spec, 0, nh * sizeof(float2), c->stream);
+    }
+    const size_t N = (size_t)c->N;
+    alloc((void **)&c->cellid, N * 4);
+    alloc((void **)&c->toff, N * 3 * 2);
+    alloc((void **)&c->tvel, N * 3 * 4);
+    alloc((void **)&c->tcell, N * 4);
+    alloc((void **)&c->tslot, N * 4);
+    alloc((void **)&c->perm, N * 4);
+    alloc((void **)&c->ncount, (size_t)c->n_cells * 4);
+    alloc((void **)&c->nstart, (size_t)c->n_cells * 4);
+    alloc((void **)&c->far, sizeof(int));
+    c->scan_tmp_len = scan_scratch_len(c->n_cells);
+    alloc((void **)&c->scan_tmp, (size_t)c->scan_tmp_len * 4);
+    alloc((void **)&c->dev_status, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->dev_status, 0, sizeof(int), c->stream);
+    if (e == cudaSuccess) e = cudaHostAlloc((void **)&c->host_status, sizeof(int), cudaHostAllocDefault);
+    for (int l = 0; l < c->nl && e == cudaSuccess; ++l) e = launch_init_twiddles(c, c->lev[l]);
+    if (e != cudaSuccess) {
+        g_init_error = std::string("allocation/setup failed: ") + cudaGetErrorString(e);
+        cudaGetLastError();
+        free_ctx(c);
+        return CUBE2_ERR_CUDA;
+    }
+    *out = c;
+    return CUBE2_OK;
+}
+
+int cube2_set_green(cube2_ctx *ctx, int level, const char *cache_path) {
+    if (!ctx) return CUBE2_ERR_BAD_ARG;
+    int r = level_ok(ctx, level, false);
+    if (r) return r;
+    Level &L = ctx->lev[level];
+    const size_t nh = (size_t)L.n * L.n * L.kxp;
+    // cache header: magic, n, kxp, alias, b_soft, b_trunc
+    struct Header { char magic[8]; int32_t n, kxp, alias, pad; double b_soft, b_trunc; } hdr{};
+    memcpy(hdr.magic, "CUBE2G01", 8);
+    hdr.n = L.n;
+    hdr.kxp = L.kxp;
+    hdr.alias = ctx->cfg.alias_max;
+    hdr.b_soft = L.b_soft;
+    hdr.b_trunc = L.b_trunc;
+    if (cache_path && cache_path[0]) {
+        FILE *f = fopen(cache_path, "rb");
+        if (f) {
+            Header h{};
+            bool ok = fread(&h, sizeof h, 1, f) == 1 && memcmp(&h, &hdr, sizeof h) == 0;
+            if (ok) {
+                std::vector<float> buf(nh);
+                ok = fread(buf.data(), sizeof(float), nh, f) == nh;
+                fclose(f);
+                if (ok) {
+                    cudaError_t e = cudaMemcpyAsync(L.green, buf.data(), nh * 4, cudaMemcpyHostToDevice, ctx->stream);
+                    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+                    if (e != cudaSuccess) return cuda_error(ctx, e, "green cache upload");
+                    L.has_green = true;
+                    return CUBE2_OK;
+                }
+            } else {
+                fclose(f);
+            }
+        }
+    }
+    cudaError_t e = launch_green(ctx, L, ctx->cfg.alias_max);
+    if (e != cudaSuccess) return cuda_error(ctx, e, "green kernel");
+    L.has_green = true;
+    if (cache_path && cache_path[0]) {
+        std::vector<float> buf(nh);
+        e = cudaMemcpyAsync(buf.data(), L.green, nh * 4, cudaMemcpyDeviceToHost, ctx->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+        if (e != cudaSuccess) return cuda_error(ctx, e, "green cache download");
+        FILE *f = fopen(cache_path, "wb");
+        if (!f) return set_error(ctx, CUBE2_ERR_BAD_ARG, std::string("cannot write green cache ") + cache_path);
+        const bool ok = fwrite(&hdr, sizeof hdr, 1, f) == 1 && fwrite(buf.data(), 4, nh, f) == nh;
+        fclose(f);
+        if (!ok) return set_error(ctx, CUBE2_ERR_BAD_ARG, "short write of green cache");
+    }
+    return CUBE2_OK;
+}
+
+int cube2_deposit(cube2_ctx *ctx, int level, const cube2_particles *p) {
+    if (!ctx) return CUBE2_ERR_BAD_ARG;
+    int r = level_ok(ctx, level, true);
+    if (r) return r;
+    if (!particles_ok(ctx, p, false, false)) return set_error(ctx, CUBE2_ERR_BAD_ARG, "bad particle arrays");
+    cudaError_t e = launch_deposit(ctx, level, p, nullptr);
+    if (e != cudaSuccess) return cuda_error(ctx, e, "deposit");
+    for (int l = 0; l < ctx->nl; ++l)
+        if (level < 0 || l == level) { ctx->lev[l].has_density = true; ctx->lev[l].has_potential = false; }
+    return CUBE2_OK;
+}
+
+int cube2_deposit_u64(cube2_ctx *ctx, int level, const cube2_particles *p, uint64_t *out) {
+    if (!ctx) return CUBE2_ERR_BAD_ARG;
+    int r = level_ok(ctx, level, false);
+    if (r) return r;
+    if (!out || !particles_ok(ctx, p, false, false)) return set_error(ctx, CUBE2_ERR_BAD_ARG, "bad arguments");
+    cudaError_t e = launch_deposit(ctx, level, p, out);
+    if (e != cudaSuccess) return cuda_error(ctx, e, "deposit_u64");
+    return CUBE2_OK;
+}
+
+int cube2_solve_pm(cube2_ctx *ctx, int level) {
+    if (!ctx) return CUBE2_ERR_BAD_ARG;
+    int r = level_ok(ctx, level, false);
+    if (r) return r;
+    Level &L = ctx->lev[level];
+    if (!L.has_green || !L.has_density) return set_error(ctx, CUBE2_ERR_STATE, "solve_pm needs set_green and deposit");
+    cudaError_t e = launch_fft_forward(ctx, L);
+    if (e == cudaSuccess) e = launch_fft_z_green(ctx, L);
+    if (e == cudaSuccess) e = launch_fft_inverse(ctx, L);
+    if (e != cudaSuccess) return cuda_error(ctx, e, "solve_pm");
+    L.has_density = false;
+    L.has_potential = true;
+    return CUBE2_OK;
+}
+
+int cube2_interp_force(cube2_ctx *ctx, int level, const cube2_particles *p, int accumulate) {
+    if (!ctx) return CUBE2_ERR_BAD_ARG;
+    int r = level_ok(ctx, level, true);
+    if (r) return r;
+    if (!particles_ok(ctx, p, false, true)) return set_error(ctx, CUBE2_ERR_BAD_ARG, "bad particle arrays");
+    for (int l = 0; l < ctx->nl; ++l)
+        if ((level < 0 || l == level) && !ctx->lev[l].has_potential)
+            return set_error(ctx, CUBE2_ERR_STATE, "interp_force needs solve_pm");
+    cudaError_t e = launch_cellid(ctx, p);
+    if (e == cudaSuccess) e = launch_interp(ctx, level, p, accumulate);
+    if (e != cudaSuccess) return cuda_error(ctx, e, "interp_force");
+    return CUBE2_OK;
+}
+
+int cube2_pp_force(cube2_ctx *ctx, const cube2_particles *p, int accumulate) {
+    if (!ctx) return CUBE2_ERR_BAD_ARG;
+    if (!particles_ok(ctx, p, false, true)) return set_error(ctx, CUBE2_ERR_BAD_ARG, "bad particle arrays");
+    cudaError_t e = launch_cellid(ctx, p);
+    if (e == cudaSuccess) e = launch_pp(ctx, p, accumulate, 0.0f);
+    if (e != cudaSuccess) return cuda_error(ctx, e, "pp_force");
+    return CUBE2_OK;
+}
+
+// deposit + solve (all levels) + interp + PP (+ optional fused kick); cellid must be valid.
+static int force_core(cube2_ctx *ctx, const cube2_particles *p, float kick) {
+    for (int l = 0; l < ctx->nl; ++l)
+        if (!ctx->lev[l].has_green) return set_error(ctx, CUBE2_ERR_STATE, "force needs every level's Green's table");
+    cudaError_t e = launch_deposit(ctx, -1, p, nullptr);
+    for (int l = 0; l < ctx->nl && e == cudaSuccess; ++l) {
+        e = launch_fft_forward(ctx, ctx->lev[l]);
+        if (e == cudaSuccess) e = launch_fft_z_green(ctx, ctx->lev[l]);
+        if (e == cudaSuccess) e = launch_fft_inverse(ctx, ctx->lev[l]);
+        ctx->lev[l].has_density = false;
+        ctx->lev[l].has_potential = true;
+    }
+    if (e == cudaSuccess) e = launch_interp(ctx, -1, p, 0);
+    if (e == cudaSuccess) e = launch_pp(ctx, p, 1, kick);
+    if (e != cudaSuccess) return cuda_error(ctx, e, "force");
+    return CUBE2_OK;
+}
+
+int cube2_force(cube2_ctx *ctx, const cube2_particles *p) {
+    if (!ctx) return CUBE2_ERR_BAD_ARG;
+    if (!particles_ok(ctx, p, false, true)) return set_error(ctx, CUBE2_ERR_BAD_ARG, "bad particle arrays");
+    cudaError_t e = launch_cellid(ctx, p);
+    if (e != cudaSuccess) return cuda_error(ctx, e, "cellid");
+    return force_core(ctx, p, 0.0f);
+}
+
+int cube2_kdk_factors(const cube2_config *cfg, double a0, double a1, double out[3]) {
+    if (!cfg || !out || !(a0 > 0) || !(a1 > a0)) return CUBE2_ERR_BAD_ARG;
+    const double ah = 0.5 * (a0 + a1);
+    out[0] = integrate(a0, ah, cfg->omega_m, cfg->omega_l, 2);
+    out[1] = integrate(a0, a1, cfg->omega_m, cfg->omega_l, 3);
+    out[2] = integrate(ah, a1, cfg->omega_m, cfg->omega_l, 2);
+    return CUBE2_OK;
+}
+
+int cube2_kdk_step(cube2_ctx *ctx, cube2_particles *p, double a0, double a1) {
+    if (!ctx) return CUBE2_ERR_BAD_ARG;
+    if (!particles_ok(ctx, p, true, true)) return set_error(ctx, CUBE2_ERR_BAD_ARG, "bad particle arrays");
+    double f[3];
+    if (cube2_kdk_factors(&ctx->cfg, a0, a1, f)) return set_error(ctx, CUBE2_ERR_BAD_ARG, "need 0 < a0 < a1");
+    const double c = 1.5 * ctx->cfg.omega_m;
+    cudaError_t e = launch_cellid(ctx, p);
+    if (e == cudaSuccess) e = launch_kick_drift(ctx, p, (float)(c * f[0]), (float)(f[1] * FIX / ctx->s_ios));
+    if (e == cudaSuccess) e = launch_rebin(ctx, p);
+    if (e != cudaSuccess) return cuda_error(ctx, e, "kick/drift/rebin");
+    return force_core(ctx, p, (float)(c * f[2]));
+}
+
+int cube2_kdk_step_host(cube2_ctx *ctx, cube2_particles *dev, cube2_particles *host, double a0, double a1) {
+    if (!ctx || !host) return CUBE2_ERR_BAD_ARG;
+    if (!particles_ok(ctx, dev, true, true) || !particles_ok(ctx, host, true, true))
+        return set_error(ctx, CUBE2_ERR_BAD_ARG, "bad particle arrays");
+    const size_t N = (size_t)ctx->N, C = (size_t)ctx->n_cells;
+    cudaError_t e = cudaSuccess;
+    auto cp = [&](void *dst, const void *src, size_t bytes, cudaMemcpyKind k) {
+        if (e == cudaSuccess && bytes) e = cudaMemcpyAsync(dst, src, bytes, k, ctx->stream);
+    };
+    for (int d = 0; d < 3; ++d) {
+        cp(dev->off[d], host->off[d], N * 2, cudaMemcpyHostToDevice);
+        cp(dev->vel[d], host->vel[d], N * 4, cudaMemcpyHostToDevice);
+        cp(dev->acc[d], host->acc[d], N * 4, cudaMemcpyHostToDevice);
+    }
+    cp(dev->count, host->count, C * 4, cudaMemcpyHostToDevice);
+    cp(dev->start, host->start, C * 4, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_error(ctx, e, "upload");
+    int r = cube2_kdk_step(ctx, dev, a0, a1);
+    if (r) return r;
+    for (int d = 0; d < 3; ++d) {
+        cp(host->off[d], dev->off[d], N * 2, cudaMemcpyDeviceToHost);
+        cp(host->vel[d], dev->vel[d], N * 4, cudaMemcpyDeviceToHost);
+        cp(host->acc[d], dev->acc[d], N * 4, cudaMemcpyDeviceToHost);
+    }
+    cp(host->count, dev->count, C * 4, cudaMemcpyDeviceToHost);
+    cp(host->start, dev->start, C * 4, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return cuda_error(ctx, e, "download");
+    return CUBE2_OK;
+}
+
+static int copy_grid(cube2_ctx *ctx, void *out, const void *src, size_t bytes) {
+    cudaError_t e = cudaMemcpyAsync(out, src, bytes, cudaMemcpyDeviceToDevice, ctx->stream);
+    return e == cudaSuccess ? CUBE2_OK : cuda_error(ctx, e, "grid copy");
+}
+
+int cube2_get_density(cube2_ctx *ctx, int level, float *out) {
+    if (!ctx) return CUBE2_ERR_BAD_ARG;
+    int r = level_ok(ctx, level, false);
+    if (r) return r;
+    if (!out) return set_error(ctx, CUBE2_ERR_BAD_ARG, "null out");
+    const Level &L = ctx->lev[level];
+    if (!L.has_density) return set_error(ctx, CUBE2_ERR_STATE, "no density (deposit first)");
+    return copy_grid(ctx, out, L.real, (size_t)L.n * L.n * L.n * 4);
+}
+
+int cube2_get_potential(cube2_ctx *ctx, int level, float *out) {
+    if (!ctx) return CUBE2_ERR_BAD_ARG;
+    int r = level_ok(ctx, level, false);
+    if (r) return r;
+    if (!out) return set_error(ctx, CUBE2_ERR_BAD_ARG, "null out");
+    const Level &L = ctx->lev[level];
+    if (!L.has_potential) return set_error(ctx, CUBE2_ERR_STATE, "no potential (solve_pm first)");
+    return copy_grid(ctx, out, L.real, (size_t)L.n * L.n * L.n * 4);
+}
+
+int cube2_get_green(cube2_ctx *ctx, int level, float *out) {
+    if (!ctx) return CUBE2_ERR_BAD_ARG;
+    int r = level_ok(ctx, level, false);
+    if (r) return r;
+    if (!out) return set_error(ctx, CUBE2_ERR_BAD_ARG, "null out");
+    const Level &L = ctx->lev[level];
+    if (!L.has_green) return set_error(ctx, CUBE2_ERR_STATE, "no Green's table");
+    const int nh = L.n / 2 + 1;
+    cudaError_t e = cudaMemcpy2DAsync(out, nh * 4, L.green, L.kxp * 4, nh * 4, (size_t)L.n * L.n,
+                                      cudaMemcpyDeviceToDevice, ctx->stream);
+    return e == cudaSuccess ? CUBE2_OK : cuda_error(ctx, e, "green copy");
+}
+
+int cube2_debug_forward_fft(cube2_ctx *ctx, int level, float *out) {
+    if (!ctx) return CUBE2_ERR_BAD_ARG;
+    int r = level_ok(ctx, level, false);
+    if (r) return r;
+    Level &L = ctx->lev[level];
+    if (!out) return set_error(ctx, CUBE2_ERR_BAD_ARG, "null out");
+    if (!L.has_density) return set_error(ctx, CUBE2_ERR_STATE, "no density (deposit first)");
+    cudaError_t e = launch_fft_forward(ctx, L);
+    if (e == cudaSuccess) e = launch_fft_z_forward(ctx, L);
+    if (e != cudaSuccess) return cuda_error(ctx, e, "forward fft");
+    const int nh = L.n / 2 + 1;
+    e = cudaMemcpy2DAsync(out, nh * 8, L.spec, L.kxp * 8, nh * 8, (size_t)L.n * L.n, cudaMemcpyDeviceToDevice,
+                          ctx->stream);
+    return e == cudaSuccess ? CUBE2_OK : cuda_error(ctx, e, "spectrum copy");
+}
+
+int cube2_check(cube2_ctx *ctx) {
+    if (!ctx) return CUBE2_ERR_BAD_ARG;
+    cudaError_t e = cudaMemcpyAsync(ctx->host_status, ctx->dev_status, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return cuda_error(ctx, e, "check");
+    const int st = *ctx->host_status;
+    if (!st) return CUBE2_OK;
+    e = cudaMemsetAsync(ctx->dev_status, 0, sizeof(int), ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return cuda_error(ctx, e, "check reset");
+    if (st & ST_CAPACITY) return set_error(ctx, CUBE2_ERR_CAPACITY, "uint64 deposit accumulator overflowed");
+    if (st & ST_NONFINITE) return set_error(ctx, CUBE2_ERR_NONFINITE, "non-finite force or momentum");
+    if (st & ST_DISPLACEMENT) return set_error(ctx, CUBE2_ERR_DISPLACEMENT, "drift displacement too large");
+    return set_error(ctx, CUBE2_ERR_TIMEOUT, "device wait timed out");
+}
+
+int cube2_profile(cube2_ctx *ctx, int capacity) {
+    if (!ctx || capacity < 0) return CUBE2_ERR_BAD_ARG;
+    cudaError_t e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return cuda_error(ctx, e, "profile sync");
+    prof_free(ctx);
+    ctx->prof_overflow = 0;
+    if (capacity == 0) return CUBE2_OK;
+    ctx->ev = new cudaEvent_t[2 * (size_t)capacity];
+    ctx->prof_cls = new int[capacity];
+    for (int i = 0; i < 2 * capacity; ++i) {
+        e = cudaEventCreate(&ctx->ev[i]);
+        if (e != cudaSuccess) {
+            for (int j = 0; j < i; ++j) cudaEventDestroy(ctx->ev[j]);
+            delete[] ctx->ev;
+            delete[] ctx->prof_cls;
+            ctx->ev = nullptr;
+            ctx->prof_cls = nullptr;
+            return cuda_error(ctx, e, "profile events");
+        }
+    }
+    ctx->prof_cap = capacity;
+    ctx->prof_used = 0;
+    ctx->prof = true;
+    return CUBE2_OK;
+}
+
+int cube2_profile_read(cube2_ctx *ctx, double *ms, int64_t *counts) {
+    if (!ctx || !ms || !counts) return CUBE2_ERR_BAD_ARG;
+    const int nslots = CUBE2_PROFILE_CLASSES * CUBE2_MAX_LEVELS;
+    for (int i = 0; i < nslots; ++i) { ms[i] = 0.0; counts[i] = 0; }
+    cudaError_t e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return cuda_error(ctx, e, "profile sync");
+    for (int s = 0; s < ctx->prof_used; ++s) {
+        float t = 0.f;
+        e = cudaEventElapsedTime(&t, ctx->ev[2 * s], ctx->ev[2 * s + 1]);
+        if (e != cudaSuccess) return cuda_error(ctx, e, "profile elapsed");
+        ms[ctx->prof_cls[s]] += t;
+        counts[ctx->prof_cls[s]] += 1;
+    }
+    ctx->prof_used = 0;
+    const int over = ctx->prof_overflow;
+    ctx->prof_overflow = 0;
+    return over ? set_error(ctx, CUBE2_ERR_CAPACITY, "profile event pool overflowed") : CUBE2_OK;
+}
+
+const char *cube2_profile_class_name(int cls) {
+    static const char *names[CUBE2_PROFILE_CLASSES] = {
+        "deposit", "fft_x_fwd", "fft_y_fwd", "fft_z_green", "fft_y_inv", "fft_x_inv", "interp", "pp",
+        "kick", "kick_drift", "scan", "scatter", "sort", "gather", "cellid", "green"};
+    return (cls >= 0 && cls < CUBE2_PROFILE_CLASSES) ? names[cls] : "";
+}
+
+const char *cube2_last_error(cube2_ctx *ctx) { return ctx ? ctx->err.c_str() : g_init_error.c_str(); }
+
+int64_t cube2_launch_count(cube2_ctx *ctx) { return ctx ? ctx->launches : 0; }
+
+void cube2_destroy(cube2_ctx *ctx) {
+    if (!ctx) return;
+    cudaStreamSynchronize(ctx->stream);
+    free_ctx(ctx);
+}
+
+}  // extern "C"

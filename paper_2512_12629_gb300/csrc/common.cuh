@@ -1,0 +1,130 @@
+// Internal declarations shared by the CUDA translation units of libcube2gb.
+// The public C ABI is include/cube2.h; nothing here is exported.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/cube2.h"
+
+namespace cube2 {
+
+constexpr int FIX_BITS = 16;              // IOS fixed point: 2^16 sub-cells per cell
+constexpr int FIX = 1 << FIX_BITS;
+constexpr int FFT_LINES = 16;             // lines (columns) per FFT tile
+constexpr int DEPOSIT_BRICK = 8;          // IOS cells per CTA brick edge
+
+// Sticky device status bits (first error wins when mapped to a code).
+enum StatusBits : int {
+    ST_CAPACITY = 1,
+    ST_NONFINITE = 2,
+    ST_DISPLACEMENT = 4,
+    ST_TIMEOUT = 8,
+};
+
+// Kernel classes for the optional CUDA-event profile (cube2_profile).
+enum ProfClass : int {
+    P_DEPOSIT = 0, P_FFT_X_FWD, P_FFT_Y_FWD, P_FFT_Z_GREEN, P_FFT_Y_INV, P_FFT_X_INV,
+    P_INTERP, P_PP, P_KICK, P_KICK_DRIFT, P_SCAN, P_SCATTER, P_SORT, P_GATHER, P_CELLID, P_GREEN,
+    P_NCLASS
+};
+
+struct Level {
+    int index = 0;           // level number (coarsest = 0)
+    int n = 0;               // mesh cells per dimension
+    int kxp = 0;             // padded width of the half spectrum (>= n/2+1, multiple of 16)
+    int shift = 0;           // n_ios / n = 2^shift
+    double H = 0;            // cell size [Mpc/h]
+    double b_soft = 0;       // softening, this level's cells
+    double b_trunc = -1;     // truncation, this level's cells (< 0: infinity)
+    float *real = nullptr;   // [n^3]  density, then potential
+    float2 *spec = nullptr;  // [n][n][kxp] half spectrum scratch
+    float *green = nullptr;  // [n][n][kxp] Green's table (1/n^3 folded in)
+    float2 *tw = nullptr;    // [n] twiddles exp(-2 pi i k / n)
+    uint64_t mean_int = 0;   // M = floor(N 2^48 / n^3)
+    float dens_scale = 0;    // RN32(n^3/N 2^-48)
+    bool has_green = false, has_density = false, has_potential = false;
+};
+
+}  // namespace cube2
+
+struct cube2_ctx {
+    cube2_config cfg{};
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    int nl = 0;
+    cube2::Level lev[CUBE2_MAX_LEVELS];
+    int64_t N = 0;
+    int n_ios = 0;
+    int64_t n_cells = 0;     // n_ios^3
+    double s_ios = 0;        // IOS cell [Mpc/h]
+    double b_range = 0;      // PP range [Mpc/h] (softening of the finest level)
+    // particle scratch (all [N] unless noted)
+    int32_t *cellid = nullptr;
+    uint16_t *toff = nullptr;      // [3][N]
+    float *tvel = nullptr;         // [3][N]
+    int32_t *tcell = nullptr;
+    int32_t *tslot = nullptr;
+    int32_t *perm = nullptr;
+    int32_t *ncount = nullptr;     // [n_cells] histogram of the new cells
+    int32_t *nstart = nullptr;     // [n_cells] its exclusive scan
+    int *far = nullptr;            // device flag: a particle moved > 1 IOS cell on an axis
+    int32_t *scan_tmp = nullptr;   // block sums of the multi-level scan
+    int64_t scan_tmp_len = 0;
+    int *dev_status = nullptr;     // sticky device status word
+    int *host_status = nullptr;    // pinned mirror
+    std::string err;
+    int64_t launches = 0;
+    // optional per-kernel-class CUDA-event profile
+    bool prof = false;
+    int prof_overflow = 0;
+    cudaEvent_t *ev = nullptr;     // pool of 2 * prof_cap events
+    int prof_cap = 0, prof_used = 0;
+    int *prof_cls = nullptr;       // [prof_cap] class * CUBE2_MAX_LEVELS + level
+};
+
+namespace cube2 {
+
+int set_error(cube2_ctx *ctx, int code, const std::string &msg);
+
+// Bracket a launch group with profile events (no-ops unless profiling is on).
+int prof_begin(cube2_ctx *ctx, int cls, int level);
+void prof_end(cube2_ctx *ctx, int slot);
+struct ProfScope {
+    cube2_ctx *c;
+    int slot;
+    ProfScope(cube2_ctx *ctx, int cls, int level = 0) : c(ctx), slot(prof_begin(ctx, cls, level)) {}
+    ~ProfScope() { prof_end(c, slot); }
+};
+int cuda_error(cube2_ctx *ctx, cudaError_t e, const char *what);
+
+// Launch wrappers implemented in the kernel translation units.  Each returns
+// the cudaError_t of its last launch and bumps ctx->launches.
+cudaError_t launch_init_twiddles(cube2_ctx *ctx, Level &L);
+cudaError_t launch_green(cube2_ctx *ctx, Level &L, int alias);
+cudaError_t launch_deposit(cube2_ctx *ctx, int level, const cube2_particles *p, uint64_t *out_u64);
+cudaError_t launch_fft_forward(cube2_ctx *ctx, Level &L);          // real -> spec (x, y passes)
+cudaError_t launch_fft_z_green(cube2_ctx *ctx, Level &L);          // z fwd * G * z inv
+cudaError_t launch_fft_z_forward(cube2_ctx *ctx, Level &L);        // z fwd only (diagnostic)
+cudaError_t launch_fft_inverse(cube2_ctx *ctx, Level &L);          // spec -> real (y, x passes)
+cudaError_t launch_cellid(cube2_ctx *ctx, const cube2_particles *p);
+cudaError_t launch_interp(cube2_ctx *ctx, int level, const cube2_particles *p, int accumulate);
+cudaError_t launch_pp(cube2_ctx *ctx, const cube2_particles *p, int accumulate, float kick);
+cudaError_t launch_kick(cube2_ctx *ctx, const cube2_particles *p, float kick);
+cudaError_t launch_kick_drift(cube2_ctx *ctx, const cube2_particles *p, float kick, float drift_fix);
+cudaError_t launch_scan(cube2_ctx *ctx, const int32_t *in, int32_t *out, int64_t n);
+cudaError_t launch_rebin(cube2_ctx *ctx, const cube2_particles *p);
+int64_t scan_scratch_len(int64_t n);
+
+}  // namespace cube2
+
+// Device helpers ------------------------------------------------------------
+namespace cube2 {
+
+__device__ __forceinline__ void set_status(int *status, int bit) { atomicOr(status, bit); }
+
+__device__ __forceinline__ int wrap(int j, int n) { return j < 0 ? j + n : (j >= n ? j - n : j); }
+
+}  // namespace cube2

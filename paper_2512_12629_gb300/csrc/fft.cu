@@ -1,0 +1,386 @@
+// 3-D real FFT Poisson solve of one PM level (paper Sec. 2.1.2: phi(k) = rho(k) G(k);
+// Sec. 2.2.2: batches of 1-D line FFTs along each axis).
+//
+// Layout: real grid [z][y][x] (x fastest, n^3 FP32); half spectrum
+// [kz][ky][kx] complex64 with kx in [0, n/2] stored in rows of kxp >= n/2+1
+// (multiple of 16, so every row starts on a 128-byte boundary).
+//
+// Passes (each one read + one write of the grid, in place where possible):
+//   X  r2c : 2L real rows per CTA packed as L complex lines a + ib, one complex
+//            FFT per line, split into the two half spectra.
+//   Y      : L consecutive kx columns x n rows of one kz plane per CTA.
+//   Z+G    : L consecutive kx columns x n planes of one ky row per CTA: forward
+//            FFT along z, multiply by G(k) (1/n^3 folded in), inverse FFT along z.
+//   Y^-1, X^-1 c2r : mirror images of Y and X.
+// Within a CTA the L lines live in shared memory as S[pos * (L+1) + line]; the
+// odd line stride keeps both line-parallel and position-parallel accesses free
+// of bank conflicts.  Each line is transformed by a Stockham autosort sequence of
+// radix-8/4/3/2 stages (natural order in and out): a stage reads R values with
+// stride n/R, applies the twiddles exp(-2 pi i r (j mod Ns) / (Ns R)), does an
+// R-point DFT in registers and writes them with stride Ns to position
+// (j / Ns) Ns R + (j mod Ns).  Every thread holds its values in registers
+// across a barrier, so stages run in place.  Twiddles are an FP32 table
+// exp(-2 pi i k/n) built from FP64 sincospi.
+#include "common.cuh"
+
+namespace cube2 {
+namespace {
+
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+// multiply by -i (forward) or +i (inverse)
+template <bool INV>
+__device__ __forceinline__ float2 rot90(float2 a) {
+    return INV ? make_float2(-a.y, a.x) : make_float2(a.y, -a.x);
+}
+
+template <int R, bool INV>
+struct Dft;
+
+template <bool INV>
+struct Dft<2, INV> {
+    __device__ __forceinline__ static void run(float2 *v) {
+        const float2 a = v[0], b = v[1];
+        v[0] = cadd(a, b);
+        v[1] = csub(a, b);
+    }
+};
+
+template <bool INV>
+struct Dft<4, INV> {
+    __device__ __forceinline__ static void run(float2 *v) {
+        const float2 s02 = cadd(v[0], v[2]), d02 = csub(v[0], v[2]);
+        const float2 s13 = cadd(v[1], v[3]), d13 = rot90<INV>(csub(v[1], v[3]));
+        v[0] = cadd(s02, s13);
+        v[2] = csub(s02, s13);
+        v[1] = cadd(d02, d13);
+        v[3] = csub(d02, d13);
+    }
+};
+
+template <bool INV>
+struct Dft<8, INV> {
+    __device__ __forceinline__ static void run(float2 *v) {
+        const float h = 0.70710678118654752440f;
+        // radix-2 split: even/odd halves
+        float2 a[4] = {v[0], v[2], v[4], v[6]};
+        float2 b[4] = {v[1], v[3], v[5], v[7]};
+        Dft<4, INV>::run(a);
+        Dft<4, INV>::run(b);
+        // twiddle b[k] by w8^k, w8 = exp(-+ i pi/4)
+        const float2 b1 = b[1], b3 = b[3];
+        b[1] = INV ? make_float2(h * (b1.x - b1.y), h * (b1.x + b1.y))
+                   : make_float2(h * (b1.x + b1.y), h * (b1.y - b1.x));
+        b[2] = rot90<INV>(b[2]);
+        b[3] = INV ? make_float2(-h * (b3.x + b3.y), h * (b3.x - b3.y))
+                   : make_float2(h * (b3.y - b3.x), -h * (b3.x + b3.y));
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            v[k] = cadd(a[k], b[k]);
+            v[k + 4] = csub(a[k], b[k]);
+        }
+    }
+};
+
+template <bool INV>
+struct Dft<3, INV> {
+    __device__ __forceinline__ static void run(float2 *v) {
+        const float c = -0.5f;
+        const float s = INV ? 0.86602540378443864676f : -0.86602540378443864676f;
+        const float2 t = cadd(v[1], v[2]);
+        const float2 d = csub(v[1], v[2]);
+        const float2 m = make_float2(v[0].x + c * t.x, v[0].y + c * t.y);
+        const float2 r = make_float2(-s * d.y, s * d.x);   // i s d
+        v[0] = cadd(v[0], t);
+        v[1] = cadd(m, r);
+        v[2] = csub(m, r);
+    }
+};
+
+__host__ __device__ constexpr int pick_radix(int rem) {
+    return rem % 3 == 0 ? 3 : (rem == 2 || rem == 4) ? rem : rem == 16 ? 4 : rem % 8 == 0 ? 8 : rem % 4 == 0 ? 4 : 2;
+}
+
+template <int N, int L, int T, int R, int NS, bool INV>
+__device__ __forceinline__ void stockham_stage(float2 *S, const float2 *__restrict__ tw) {
+    constexpr int LP = L + 1;
+    constexpr int NB = N / R;
+    constexpr int TOT = NB * L;
+    constexpr int PER = (TOT + T - 1) / T;
+    float2 v[PER][R];
+#pragma unroll
+    for (int p = 0; p < PER; ++p) {
+        const int b = threadIdx.x + p * T;
+        if (TOT % T == 0 || b < TOT) {
+            const int line = b % L, j = b / L;
+#pragma unroll
+            for (int r = 0; r < R; ++r) v[p][r] = S[(j + r * NB) * LP + line];
+            if (NS > 1) {
+                const int k = j % NS;
+#pragma unroll
+                for (int r = 1; r < R; ++r) {
+                    float2 w = __ldg(&tw[r * k * (N / (NS * R))]);
+                    if (INV) w.y = -w.y;
+                    v[p][r] = cmul(v[p][r], w);
+                }
+            }
+            Dft<R, INV>::run(v[p]);
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int p = 0; p < PER; ++p) {
+        const int b = threadIdx.x + p * T;
+        if (TOT % T == 0 || b < TOT) {
+            const int line = b % L, j = b / L;
+            const int k = j % NS;
+            const int base = (j / NS) * NS * R + k;
+#pragma unroll
+            for (int r = 0; r < R; ++r) S[(base + r * NS) * LP + line] = v[p][r];
+        }
+    }
+    __syncthreads();
+}
+
+template <int N, int L, int T, int NS, bool INV>
+__device__ __forceinline__ void fft_lines(float2 *S, const float2 *__restrict__ tw) {
+    if constexpr (NS < N) {
+        constexpr int R = pick_radix(N / NS);
+        stockham_stage<N, L, T, R, NS, INV>(S, tw);
+        fft_lines<N, L, T, NS * R, INV>(S, tw);
+    }
+}
+
+template <int N>
+struct Tile {
+    static constexpr int L = N >= 2048 ? 8 : FFT_LINES;
+    static constexpr int LP = L + 1;
+    static constexpr int T0 = N * L / 32;
+    static constexpr int T = T0 < 64 ? 64 : (T0 > 512 ? 512 : T0);
+    static constexpr size_t SMEM = (size_t)N * LP * sizeof(float2);
+};
+
+// ---------------------------------------------------------------- X passes
+template <int N>
+__global__ void __launch_bounds__(Tile<N>::T) fft_x_r2c(const float *__restrict__ in, float2 *__restrict__ out,
+                                                       int64_t nrows, int kxp, const float2 *__restrict__ tw) {
+    constexpr int L = Tile<N>::L, LP = Tile<N>::LP, T = Tile<N>::T;
+    extern __shared__ float2 S[];
+    const int64_t row0 = (int64_t)blockIdx.x * 2 * L;
+    for (int i = threadIdx.x; i < 2 * L * N; i += T) {
+        const int r = i / N, x = i % N;
+        const int64_t row = row0 + r;
+        const float v = row < nrows ? __ldg(&in[row * N + x]) : 0.0f;
+        reinterpret_cast<float *>(&S[x * LP + (r >> 1)])[r & 1] = v;
+    }
+    __syncthreads();
+    fft_lines<N, L, T, 1, false>(S, tw);
+    constexpr int NH = N / 2 + 1;
+    for (int i = threadIdx.x; i < L * NH; i += T) {
+        const int l = i / NH, k = i % NH;
+        const float2 z = S[k * LP + l];
+        const float2 zc = S[((N - k) % N) * LP + l];
+        const float2 A = make_float2(0.5f * (z.x + zc.x), 0.5f * (z.y - zc.y));
+        const float2 B = make_float2(0.5f * (z.y + zc.y), -0.5f * (z.x - zc.x));
+        const int64_t ra = row0 + 2 * l;
+        if (ra < nrows) out[ra * kxp + k] = A;
+        if (ra + 1 < nrows) out[(ra + 1) * kxp + k] = B;
+    }
+}
+
+template <int N>
+__global__ void __launch_bounds__(Tile<N>::T) fft_x_c2r(const float2 *__restrict__ in, float *__restrict__ out,
+                                                       int64_t nrows, int kxp, const float2 *__restrict__ tw) {
+    constexpr int L = Tile<N>::L, LP = Tile<N>::LP, T = Tile<N>::T;
+    extern __shared__ float2 S[];
+    const int64_t row0 = (int64_t)blockIdx.x * 2 * L;
+    constexpr int NH = N / 2 + 1;
+    for (int i = threadIdx.x; i < L * NH; i += T) {
+        const int l = i / NH, k = i % NH;
+        const int64_t ra = row0 + 2 * l;
+        float2 A = ra < nrows ? in[ra * kxp + k] : make_float2(0.f, 0.f);
+        float2 B = ra + 1 < nrows ? in[(ra + 1) * kxp + k] : make_float2(0.f, 0.f);
+        if (k == 0 || k == N / 2) { A.y = 0.f; B.y = 0.f; }
+        S[k * LP + l] = make_float2(A.x - B.y, A.y + B.x);                    // A + iB
+        if (k > 0 && k < N / 2) S[(N - k) * LP + l] = make_float2(A.x + B.y, B.x - A.y);  // conj(A) + i conj(B)
+    }
+    __syncthreads();
+    fft_lines<N, L, T, 1, true>(S, tw);
+    for (int i = threadIdx.x; i < 2 * L * N; i += T) {
+        const int r = i / N, x = i % N;
+        const int64_t row = row0 + r;
+        if (row < nrows) out[row * N + x] = reinterpret_cast<const float *>(&S[x * LP + (r >> 1)])[r & 1];
+    }
+}
+
+// ---------------------------------------------------------------- Y passes
+template <int N, bool INV>
+__global__ void __launch_bounds__(Tile<N>::T) fft_y(float2 *__restrict__ data, int kxp, const float2 *__restrict__ tw) {
+    constexpr int L = Tile<N>::L, LP = Tile<N>::LP, T = Tile<N>::T;
+    extern __shared__ float2 S[];
+    const int tiles_x = kxp / L;
+    const int tx = blockIdx.x % tiles_x;
+    const int64_t z = blockIdx.x / tiles_x;
+    float2 *base = data + z * N * kxp + tx * L;
+    for (int i = threadIdx.x; i < N * L; i += T) {
+        const int y = i / L, l = i % L;
+        S[y * LP + l] = base[(int64_t)y * kxp + l];
+    }
+    __syncthreads();
+    fft_lines<N, L, T, 1, INV>(S, tw);
+    for (int i = threadIdx.x; i < N * L; i += T) {
+        const int y = i / L, l = i % L;
+        base[(int64_t)y * kxp + l] = S[y * LP + l];
+    }
+}
+
+// ------------------------------------------------------------ Z (+ Green)
+template <int N, bool GREEN>
+__global__ void __launch_bounds__(Tile<N>::T) fft_z(float2 *__restrict__ data, const float *__restrict__ green,
+                                                   int kxp, const float2 *__restrict__ tw) {
+    constexpr int L = Tile<N>::L, LP = Tile<N>::LP, T = Tile<N>::T;
+    extern __shared__ float2 S[];
+    const int tiles_x = kxp / L;
+    const int tx = blockIdx.x % tiles_x;
+    const int64_t ky = blockIdx.x / tiles_x;
+    const int64_t zstride = (int64_t)N * kxp;
+    float2 *base = data + ky * kxp + tx * L;
+    for (int i = threadIdx.x; i < N * L; i += T) {
+        const int z = i / L, l = i % L;
+        S[z * LP + l] = base[z * zstride + l];
+    }
+    __syncthreads();
+    fft_lines<N, L, T, 1, false>(S, tw);
+    if (GREEN) {
+        const float *g = green + ky * kxp + tx * L;
+        for (int i = threadIdx.x; i < N * L; i += T) {
+            const int z = i / L, l = i % L;
+            const float gv = __ldg(&g[z * zstride + l]);
+            float2 v = S[z * LP + l];
+            v.x *= gv;
+            v.y *= gv;
+            S[z * LP + l] = v;
+        }
+        __syncthreads();
+        fft_lines<N, L, T, 1, true>(S, tw);
+    }
+    for (int i = threadIdx.x; i < N * L; i += T) {
+        const int z = i / L, l = i % L;
+        base[z * zstride + l] = S[z * LP + l];
+    }
+}
+
+template <int N>
+struct Launcher {
+    static cudaError_t forward(cube2_ctx *ctx, Level &Lv) {
+        setup();
+        const int64_t nrows = (int64_t)N * N;
+        const unsigned bx = (unsigned)((nrows + 2 * Tile<N>::L - 1) / (2 * Tile<N>::L));
+        {
+            ProfScope prof(ctx, P_FFT_X_FWD, Lv.index);
+            fft_x_r2c<N><<<bx, Tile<N>::T, Tile<N>::SMEM, ctx->stream>>>(Lv.real, Lv.spec, nrows, Lv.kxp, Lv.tw);
+        }
+        const unsigned by = (unsigned)((int64_t)N * (Lv.kxp / Tile<N>::L));
+        {
+            ProfScope prof(ctx, P_FFT_Y_FWD, Lv.index);
+            fft_y<N, false><<<by, Tile<N>::T, Tile<N>::SMEM, ctx->stream>>>(Lv.spec, Lv.kxp, Lv.tw);
+        }
+        ctx->launches += 2;
+        return cudaGetLastError();
+    }
+    static cudaError_t z_pass(cube2_ctx *ctx, Level &Lv, bool green) {
+        setup();
+        const unsigned bz = (unsigned)((int64_t)N * (Lv.kxp / Tile<N>::L));
+        ProfScope prof(ctx, P_FFT_Z_GREEN, Lv.index);
+        if (green)
+            fft_z<N, true><<<bz, Tile<N>::T, Tile<N>::SMEM, ctx->stream>>>(Lv.spec, Lv.green, Lv.kxp, Lv.tw);
+        else
+            fft_z<N, false><<<bz, Tile<N>::T, Tile<N>::SMEM, ctx->stream>>>(Lv.spec, nullptr, Lv.kxp, Lv.tw);
+        ctx->launches += 1;
+        return cudaGetLastError();
+    }
+    static cudaError_t inverse(cube2_ctx *ctx, Level &Lv) {
+        setup();
+        const unsigned by = (unsigned)((int64_t)N * (Lv.kxp / Tile<N>::L));
+        {
+            ProfScope prof(ctx, P_FFT_Y_INV, Lv.index);
+            fft_y<N, true><<<by, Tile<N>::T, Tile<N>::SMEM, ctx->stream>>>(Lv.spec, Lv.kxp, Lv.tw);
+        }
+        const int64_t nrows = (int64_t)N * N;
+        const unsigned bx = (unsigned)((nrows + 2 * Tile<N>::L - 1) / (2 * Tile<N>::L));
+        {
+            ProfScope prof(ctx, P_FFT_X_INV, Lv.index);
+            fft_x_c2r<N><<<bx, Tile<N>::T, Tile<N>::SMEM, ctx->stream>>>(Lv.spec, Lv.real, nrows, Lv.kxp, Lv.tw);
+        }
+        ctx->launches += 2;
+        return cudaGetLastError();
+    }
+    static void setup() {
+        static bool done = false;
+        if (done) return;
+        const int smem = (int)Tile<N>::SMEM;
+        cudaFuncSetAttribute(fft_x_r2c<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        cudaFuncSetAttribute(fft_x_c2r<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        cudaFuncSetAttribute(fft_y<N, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        cudaFuncSetAttribute(fft_y<N, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        cudaFuncSetAttribute(fft_z<N, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        cudaFuncSetAttribute(fft_z<N, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        done = true;
+    }
+};
+
+enum class Op { Forward, ZGreen, ZForward, Inverse };
+
+template <int N>
+cudaError_t run_op(cube2_ctx *ctx, Level &Lv, Op op) {
+    switch (op) {
+        case Op::Forward: return Launcher<N>::forward(ctx, Lv);
+        case Op::ZGreen: return Launcher<N>::z_pass(ctx, Lv, true);
+        case Op::ZForward: return Launcher<N>::z_pass(ctx, Lv, false);
+        case Op::Inverse: return Launcher<N>::inverse(ctx, Lv);
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t dispatch(cube2_ctx *ctx, Level &Lv, Op op) {
+    switch (Lv.n) {
+        case 8: return run_op<8>(ctx, Lv, op);
+        case 12: return run_op<12>(ctx, Lv, op);
+        case 16: return run_op<16>(ctx, Lv, op);
+        case 24: return run_op<24>(ctx, Lv, op);
+        case 32: return run_op<32>(ctx, Lv, op);
+        case 48: return run_op<48>(ctx, Lv, op);
+        case 64: return run_op<64>(ctx, Lv, op);
+        case 96: return run_op<96>(ctx, Lv, op);
+        case 128: return run_op<128>(ctx, Lv, op);
+        case 192: return run_op<192>(ctx, Lv, op);
+        case 256: return run_op<256>(ctx, Lv, op);
+        case 384: return run_op<384>(ctx, Lv, op);
+        case 512: return run_op<512>(ctx, Lv, op);
+        case 768: return run_op<768>(ctx, Lv, op);
+        case 1024: return run_op<1024>(ctx, Lv, op);
+        case 1536: return run_op<1536>(ctx, Lv, op);
+        case 2048: return run_op<2048>(ctx, Lv, op);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace
+
+bool fft_size_supported(int n) {
+    switch (n) {
+        case 8: case 12: case 16: case 24: case 32: case 48: case 64: case 96: case 128: case 192:
+        case 256: case 384: case 512: case 768: case 1024: case 1536: case 2048: return true;
+        default: return false;
+    }
+}
+
+cudaError_t launch_fft_forward(cube2_ctx *ctx, Level &L) { return dispatch(ctx, L, Op::Forward); }
+cudaError_t launch_fft_z_green(cube2_ctx *ctx, Level &L) { return dispatch(ctx, L, Op::ZGreen); }
+cudaError_t launch_fft_z_forward(cube2_ctx *ctx, Level &L) { return dispatch(ctx, L, Op::ZForward); }
+cudaError_t launch_fft_inverse(cube2_ctx *ctx, Level &L) { return dispatch(ctx, L, Op::Inverse); }
+
+}  // namespace cube2

@@ -1,0 +1,132 @@
+// Optimised Green's function of one PM level, Eq. (Gk) of the paper (Sec. 2.1.2),
+// and the FFT twiddle tables.  FP64 arithmetic on the GPU, FP32 result.
+//
+// For a mode k = 2 pi m / n (m_d in (-n/2, n/2]) the kernel forms
+//   d_d   = 4/3 sin k_d - 1/6 sin 2k_d                     (Eq. diff, D = i d)
+//   W^2   = prod_d sinc^4((k_d + 2 pi n_d)/2)               (CIC)
+//   dS2   = S^2(|k_n|, b_soft) - S^2(|k_n|, b_trunc)        (Eqs. Rk, Sk)
+//   G     = -sum_n W^2 (d.k_n) dS2/|k_n|^2 / (|d|^2 [sum_n W^2]^2)
+// over the images |n_d| <= alias, and stores G / n^3 (the inverse FFT is
+// unnormalised).  G = 0 where |d| = 0.  The alias sum of W^2 factorises per
+// axis; the numerator does not and is summed image by image.
+#include "common.cuh"
+
+namespace cube2 {
+namespace {
+
+constexpr int MAX_ALIAS = 4;
+
+// S(k, b) of Eq. (Sk) with x = k b / 2.  Below x = 1/2 the closed form
+// cancels badly, so the Taylor series of 2 - 2cos x - x sin x divided by
+// x^4/12 is used there: 12 * sum_{j>=2} (-1)^j (2j-2) x^(2j-4) / (2j)!.
+__device__ double profile_transform(double k, double b) {
+    if (b < 0) return 0.0;                       // b = infinity
+    const double x = 0.5 * k * b;
+    if (x < 0.5) {
+        const double x2 = x * x;
+        double term = 1.0 / 24.0;                // j = 2: (2j-2)/(2j)! = 2/24
+        double sum = 0.0;
+        double p = 1.0;                          // x^(2j-4)
+        for (int j = 2; j <= 13; ++j) {
+            // term = 1/(2j)!
+            const double c = ((j & 1) ? -1.0 : 1.0) * (2.0 * j - 2.0) * term;
+            sum += c * p;
+            p *= x2;
+            term /= (2.0 * j + 1.0) * (2.0 * j + 2.0);
+        }
+        return 12.0 * sum;
+    }
+    double s, c;
+    sincos(x, &s, &c);
+    const double x2 = x * x;
+    return 12.0 / (x2 * x2) * (2.0 - 2.0 * c - x * s);
+}
+
+__device__ double fd_weight(int m, int n) {
+    // 4/3 sin(2 pi m/n) - 1/6 sin(4 pi m/n); sinpi gives exact zeros at k in {0, pi}
+    const double t = 2.0 * (double)m / (double)n;
+    return 4.0 / 3.0 * sinpi(t) - 1.0 / 6.0 * sinpi(2.0 * t);
+}
+
+__global__ void green_kernel(float *__restrict__ G, int n, int kxp, double b_soft, double b_trunc,
+                             int alias, double norm) {
+    const int64_t total = (int64_t)n * n * kxp;
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= total) return;
+    const int kx = (int)(idx % kxp);
+    const int ky = (int)((idx / kxp) % n);
+    const int kz = (int)(idx / ((int64_t)kxp * n));
+    if (kx > n / 2) { G[idx] = 0.0f; return; }
+    const int m[3] = {kx, ky <= n / 2 ? ky : ky - n, kz <= n / 2 ? kz : kz - n};
+    double d[3], d2 = 0.0;
+    for (int a = 0; a < 3; ++a) { d[a] = fd_weight(m[a], n); d2 += d[a] * d[a]; }
+    if (d2 == 0.0) { G[idx] = 0.0f; return; }
+    const double two_pi = 6.283185307179586476925286766559;
+    const double pi = 3.141592653589793238462643383279;
+    // per-axis image wavenumbers and CIC factors sinc^4(k_n/2)
+    double kn[3][2 * MAX_ALIAS + 1], w2[3][2 * MAX_ALIAS + 1];
+    double den = 1.0;
+    for (int a = 0; a < 3; ++a) {
+        const double frac = (double)m[a] / (double)n;
+        const double s = sinpi(frac);
+        double sum = 0.0;
+        for (int i = -alias; i <= alias; ++i) {
+            const double u = frac + i;           // k_n / (2 pi)
+            kn[a][i + alias] = two_pi * u;
+            double w;
+            if (u == 0.0) w = 1.0;
+            else { const double sc = s / (pi * u); const double sc2 = sc * sc; w = sc2 * sc2; }
+            w2[a][i + alias] = w;
+            sum += w;
+        }
+        den *= sum;
+    }
+    double num = 0.0;
+    for (int iz = 0; iz <= 2 * alias; ++iz) {
+        for (int iy = 0; iy <= 2 * alias; ++iy) {
+            const double wyz = w2[1][iy] * w2[2][iz];
+            for (int ix = 0; ix <= 2 * alias; ++ix) {
+                const double k0 = kn[0][ix], k1 = kn[1][iy], k2 = kn[2][iz];
+                const double kk = k0 * k0 + k1 * k1 + k2 * k2;
+                if (kk == 0.0) continue;
+                const double kabs = sqrt(kk);
+                const double s1 = profile_transform(kabs, b_soft);
+                const double s2 = profile_transform(kabs, b_trunc);
+                const double ds2 = s1 * s1 - s2 * s2;
+                num -= w2[0][ix] * wyz * (d[0] * k0 + d[1] * k1 + d[2] * k2) * ds2 / kk;
+            }
+        }
+    }
+    G[idx] = (float)(num / (d2 * den * den) * norm);
+}
+
+__global__ void twiddle_kernel(float2 *tw, int n) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    double s, c;
+    sincospi(-2.0 * (double)k / (double)n, &s, &c);
+    tw[k] = make_float2((float)c, (float)s);
+}
+
+}  // namespace
+
+cudaError_t launch_init_twiddles(cube2_ctx *ctx, Level &L) {
+    twiddle_kernel<<<(L.n + 255) / 256, 256, 0, ctx->stream>>>(L.tw, L.n);
+    ctx->launches++;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_green(cube2_ctx *ctx, Level &L, int alias) {
+    if (alias > MAX_ALIAS) alias = MAX_ALIAS;
+    const int64_t total = (int64_t)L.n * L.n * L.kxp;
+    const double norm = 1.0 / ((double)L.n * (double)L.n * (double)L.n);
+    const int threads = 128;
+    const int64_t blocks = (total + threads - 1) / threads;
+    ProfScope prof(ctx, P_GREEN, L.index);
+    green_kernel<<<(unsigned)blocks, threads, 0, ctx->stream>>>(L.green, L.n, L.kxp, L.b_soft,
+                                                                 L.b_trunc, alias, norm);
+    ctx->launches++;
+    return cudaGetLastError();
+}
+
+}  // namespace cube2

@@ -1,0 +1,322 @@
+"""Python binding of libcube2gb (include/cube2.h): argument marshalling only.
+
+Every function forwards to the C entry point of the same name
+(``cube2_<name>``); all arithmetic runs in the library's CUDA kernels.  Torch
+tensors own the device memory of the particle arrays and give the stream.
+There is no CPU fallback: importing this module without the built library,
+or calling it without a CUDA device, raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "lib", "libcube2gb.so")
+
+OK = 0
+ERR_BAD_ARG = -1
+ERR_CUDA = -2
+ERR_CAPACITY = -3
+ERR_TIMEOUT = -4
+ERR_NONFINITE = -5
+ERR_UNSUPPORTED_SIZE = -6
+ERR_STATE = -7
+ERR_DISPLACEMENT = -8
+MAX_LEVELS = 2
+PROFILE_CLASSES = 16
+
+
+class Cube2Error(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"cube2 error {code}: {msg}")
+        self.code = code
+
+
+class Config(ctypes.Structure):
+    _fields_ = [
+        ("box", ctypes.c_double),
+        ("n_ios", ctypes.c_int32),
+        ("n_levels", ctypes.c_int32),
+        ("n_mesh", ctypes.c_int32 * MAX_LEVELS),
+        ("beta", ctypes.c_double * MAX_LEVELS),
+        ("b_pp", ctypes.c_double),
+        ("omega_m", ctypes.c_double),
+        ("omega_l", ctypes.c_double),
+        ("n_particles", ctypes.c_int64),
+        ("alias_max", ctypes.c_int32),
+    ]
+
+
+class Particles(ctypes.Structure):
+    _fields_ = [
+        ("n", ctypes.c_int64),
+        ("off", ctypes.c_void_p * 3),
+        ("count", ctypes.c_void_p),
+        ("start", ctypes.c_void_p),
+        ("vel", ctypes.c_void_p * 3),
+        ("acc", ctypes.c_void_p * 3),
+    ]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: build it with paper_2512_12629_gb300.build.build()")
+    lib = ctypes.CDLL(LIB_PATH)
+    P, I, D = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+    sig = {
+        "cube2_init_mesh": (I, [ctypes.POINTER(P), ctypes.POINTER(Config), P]),
+        "cube2_set_green": (I, [P, I, ctypes.c_char_p]),
+        "cube2_deposit": (I, [P, I, ctypes.POINTER(Particles)]),
+        "cube2_deposit_u64": (I, [P, I, ctypes.POINTER(Particles), P]),
+        "cube2_solve_pm": (I, [P, I]),
+        "cube2_interp_force": (I, [P, I, ctypes.POINTER(Particles), I]),
+        "cube2_pp_force": (I, [P, ctypes.POINTER(Particles), I]),
+        "cube2_force": (I, [P, ctypes.POINTER(Particles)]),
+        "cube2_kdk_step": (I, [P, ctypes.POINTER(Particles), D, D]),
+        "cube2_kdk_step_host": (I, [P, ctypes.POINTER(Particles), ctypes.POINTER(Particles), D, D]),
+        "cube2_get_density": (I, [P, I, P]),
+        "cube2_get_potential": (I, [P, I, P]),
+        "cube2_get_green": (I, [P, I, P]),
+        "cube2_debug_forward_fft": (I, [P, I, P]),
+        "cube2_kdk_factors": (I, [ctypes.POINTER(Config), D, D, ctypes.POINTER(D)]),
+        "cube2_check": (I, [P]),
+        "cube2_last_error": (ctypes.c_char_p, [P]),
+        "cube2_launch_count": (ctypes.c_int64, [P]),
+        "cube2_profile": (I, [P, I]),
+        "cube2_profile_read": (I, [P, ctypes.POINTER(D), ctypes.POINTER(ctypes.c_int64)]),
+        "cube2_profile_class_name": (ctypes.c_char_p, [I]),
+        "cube2_destroy": (None, [P]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+_lib = _load()
+
+
+def library():
+    return _lib
+
+
+def make_config(w, n_particles=None, alias_max=2) -> Config:
+    """Config from an ``inputs.workloads.Workload`` record."""
+    c = Config()
+    c.box = w.box
+    c.n_ios = w.n_ios
+    c.n_levels = len(w.levels)
+    for i, lev in enumerate(w.levels):
+        c.n_mesh[i] = lev.n_mesh
+        c.beta[i] = lev.beta
+    c.b_pp = w.b_pp
+    c.omega_m = w.omega_m
+    c.omega_l = w.omega_l
+    c.n_particles = w.n_particles if n_particles is None else n_particles
+    c.alias_max = alias_max
+    return c
+
+
+@dataclass
+class IOSState:
+    """Particle set in IOS form as torch tensors (device or pinned host)."""
+    off: torch.Tensor     # (3, N) int16 storage of the uint16 offsets
+    count: torch.Tensor   # (n_ios^3,) int32
+    start: torch.Tensor   # (n_ios^3,) int32
+    vel: torch.Tensor     # (3, N) float32
+    acc: torch.Tensor     # (3, N) float32
+
+    @property
+    def n(self):
+        return self.off.shape[1]
+
+    @staticmethod
+    def from_numpy(st, device="cuda", pin=False):
+        def t(a, dtype=None):
+            x = torch.from_numpy(np.ascontiguousarray(a))
+            if dtype is not None:
+                x = x.to(dtype)
+            if device == "cpu":
+                return x.pin_memory() if pin else x
+            return x.to(device)
+        off = np.ascontiguousarray(st["off"]).view(np.int16)
+        n = off.shape[1]
+        vel = st.get("vel")
+        vel = np.zeros((3, n), np.float32) if vel is None else np.asarray(vel, np.float32)
+        acc = np.zeros((3, n), np.float32)
+        return IOSState(t(off), t(st["count"].astype(np.int32)), t(st["start"].astype(np.int32)),
+                        t(vel), t(acc))
+
+    def to_numpy(self):
+        return dict(off=self.off.cpu().numpy().view(np.uint16), count=self.count.cpu().numpy(),
+                    start=self.start.cpu().numpy(), vel=self.vel.cpu().numpy(), acc=self.acc.cpu().numpy())
+
+    def clone(self):
+        return IOSState(*(x.clone() for x in (self.off, self.count, self.start, self.vel, self.acc)))
+
+    def struct(self) -> Particles:
+        p = Particles()
+        p.n = self.n
+        for d in range(3):
+            p.off[d] = self.off[d].data_ptr()
+            p.vel[d] = self.vel[d].data_ptr()
+            p.acc[d] = self.acc[d].data_ptr()
+        p.count = self.count.data_ptr()
+        p.start = self.start.data_ptr()
+        return p
+
+
+class Context:
+    """Owner of a cube2_ctx (meshes, Green's tables, scratch) on one device/stream."""
+
+    def __init__(self, cfg: Config, stream=None):
+        if not torch.cuda.is_available():
+            raise RuntimeError("cube2 needs a CUDA device (no CPU fallback)")
+        self.cfg = cfg
+        self.stream = torch.cuda.current_stream() if stream is None else stream
+        ptr = ctypes.c_void_p()
+        code = _lib.cube2_init_mesh(ctypes.byref(ptr), ctypes.byref(cfg), ctypes.c_void_p(self.stream.cuda_stream))
+        if code != OK:
+            raise Cube2Error(code, _lib.cube2_last_error(None).decode())
+        self.ptr = ptr
+
+    def _chk(self, code):
+        if code != OK:
+            raise Cube2Error(code, _lib.cube2_last_error(self.ptr).decode())
+
+    def close(self):
+        if getattr(self, "ptr", None):
+            _lib.cube2_destroy(self.ptr)
+            self.ptr = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # same names as the C ABI ------------------------------------------------
+    def set_green(self, level, cache_path=None):
+        self._chk(_lib.cube2_set_green(self.ptr, level, cache_path.encode() if cache_path else None))
+
+    def deposit(self, level, p: IOSState):
+        self._chk(_lib.cube2_deposit(self.ptr, level, ctypes.byref(p.struct())))
+
+    def deposit_u64(self, level, p: IOSState):
+        n = self.cfg.n_mesh[level]
+        out = torch.empty((n, n, n), dtype=torch.int64, device=p.off.device)
+        self._chk(_lib.cube2_deposit_u64(self.ptr, level, ctypes.byref(p.struct()), out.data_ptr()))
+        return out
+
+    def solve_pm(self, level):
+        self._chk(_lib.cube2_solve_pm(self.ptr, level))
+
+    def interp_force(self, level, p: IOSState, accumulate=False):
+        self._chk(_lib.cube2_interp_force(self.ptr, level, ctypes.byref(p.struct()), int(accumulate)))
+
+    def pp_force(self, p: IOSState, accumulate=False):
+        self._chk(_lib.cube2_pp_force(self.ptr, ctypes.byref(p.struct()), int(accumulate)))
+
+    def force(self, p: IOSState):
+        self._chk(_lib.cube2_force(self.ptr, ctypes.byref(p.struct())))
+
+    def kdk_step(self, p: IOSState, a0, a1):
+        self._chk(_lib.cube2_kdk_step(self.ptr, ctypes.byref(p.struct()), float(a0), float(a1)))
+
+    def kdk_step_host(self, dev: IOSState, host: IOSState, a0, a1):
+        self._chk(_lib.cube2_kdk_step_host(self.ptr, ctypes.byref(dev.struct()), ctypes.byref(host.struct()),
+                                           float(a0), float(a1)))
+
+    def _grid(self, fn, level, shape, dtype, device):
+        out = torch.empty(shape, dtype=dtype, device=device)
+        self._chk(fn(self.ptr, level, out.data_ptr()))
+        return out
+
+    def get_density(self, level, device="cuda"):
+        n = self.cfg.n_mesh[level]
+        return self._grid(_lib.cube2_get_density, level, (n, n, n), torch.float32, device)
+
+    def get_potential(self, level, device="cuda"):
+        n = self.cfg.n_mesh[level]
+        return self._grid(_lib.cube2_get_potential, level, (n, n, n), torch.float32, device)
+
+    def get_green(self, level, device="cuda"):
+        n = self.cfg.n_mesh[level]
+        return self._grid(_lib.cube2_get_green, level, (n, n, n // 2 + 1), torch.float32, device)
+
+    def debug_forward_fft(self, level, device="cuda"):
+        n = self.cfg.n_mesh[level]
+        out = self._grid(_lib.cube2_debug_forward_fft, level, (n, n, n // 2 + 1, 2), torch.float32, device)
+        return torch.view_as_complex(out)
+
+    def check(self):
+        self._chk(_lib.cube2_check(self.ptr))
+
+    def launch_count(self):
+        return int(_lib.cube2_launch_count(self.ptr))
+
+    def profile(self, capacity):
+        """Start (capacity > 0) or stop (0) per-kernel-class CUDA-event timing."""
+        self._chk(_lib.cube2_profile(self.ptr, int(capacity)))
+
+    def profile_read(self):
+        """{(class_name, level): (milliseconds, launch_groups)} since the last read."""
+        n = PROFILE_CLASSES * MAX_LEVELS
+        ms = (ctypes.c_double * n)()
+        cnt = (ctypes.c_int64 * n)()
+        self._chk(_lib.cube2_profile_read(self.ptr, ms, cnt))
+        out = {}
+        for c in range(PROFILE_CLASSES):
+            name = _lib.cube2_profile_class_name(c).decode()
+            for l in range(MAX_LEVELS):
+                k = c * MAX_LEVELS + l
+                if cnt[k]:
+                    out[(name, l)] = (ms[k], int(cnt[k]))
+        return out
+
+
+def kdk_factors(cfg: Config, a0, a1):
+    out = (ctypes.c_double * 3)()
+    code = _lib.cube2_kdk_factors(ctypes.byref(cfg), float(a0), float(a1), out)
+    if code != OK:
+        raise Cube2Error(code, "kdk_factors")
+    return tuple(out)
+
+
+# module-level functions with the C names -------------------------------------
+def init_mesh(cfg: Config, stream=None) -> Context:
+    return Context(cfg, stream)
+
+
+def set_green(ctx: Context, level, cache_path=None):
+    ctx.set_green(level, cache_path)
+
+
+def deposit(ctx: Context, level, p: IOSState):
+    ctx.deposit(level, p)
+
+
+def solve_pm(ctx: Context, level):
+    ctx.solve_pm(level)
+
+
+def interp_force(ctx: Context, level, p: IOSState, accumulate=False):
+    ctx.interp_force(level, p, accumulate)
+
+
+def pp_force(ctx: Context, p: IOSState, accumulate=False):
+    ctx.pp_force(p, accumulate)
+
+
+def force(ctx: Context, p: IOSState):
+    ctx.force(p)
+
+
+def kdk_step(ctx: Context, p: IOSState, a0, a1):
+    ctx.kdk_step(p, a0, a1)
