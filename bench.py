@@ -161,8 +161,23 @@ def algorithmic_bytes(w, n_part, cls, level):
         "gather": 48 * N,
         "cellid": 8 * C + 4 * N,
         "green": 4 * half,
+        "prep": 26 * N,
+        "pp_dense": 0,
+        "sort_big": 8 * N,
     }
     return table[cls]
+
+
+# FP32 operations of one in-range PP pair (separation 6, r^2 5, rsqrt and
+# range logic 6, the R_PP polynomial and scaling 12, force components 3,
+# Kahan updates 12) and of one candidate test (separation and r^2 11)
+PP_FLOPS_PAIR = 44
+PP_FLOPS_CANDIDATE = 11
+
+
+def fp32_peak_tflops(sm_mhz):
+    """152 SMs x 128 FP32 lanes x 2 (FMA) x clock."""
+    return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
 
 
 def traffic_record(kernel):
@@ -313,6 +328,7 @@ def main():
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
     ctx.profile(capacity=64 * (args.steps + 2))
+    ctx.pp_stats()
     launches0 = ctx.launch_count()
     clocks = ClockSampler(bus_id_of(torch.cuda.current_device()))
     clocks.start()
@@ -335,6 +351,7 @@ def main():
     prof = ctx.profile_read()
     ctx.profile(0)
     ctx.check()
+    pp_pairs, pp_cands = ctx.pp_stats()
     ms_max = ms
     if dist:
         t = torch.tensor([ms], device="cuda")
@@ -342,24 +359,43 @@ def main():
         ms_max = float(t.item())
     value = n_part * args.steps * world / (ms_max / 1e3)
 
-    # dominant kernel class -> roofline
+    # dominant kernel class -> roofline (PP counts both of its kernels)
     peak, peak_kind = peaks()
     total_prof = sum(v[0] for v in prof.values())
-    dom = max(prof.items(), key=lambda kv: kv[1][0])
+    merged = dict(prof)
+    if ("pp", 0) in merged and ("pp_dense", 0) in merged:
+        a_, b_ = merged.pop(("pp", 0)), merged.pop(("pp_dense", 0))
+        merged[("pp", 0)] = (a_[0] + b_[0], a_[1])
+    dom = max(merged.items(), key=lambda kv: kv[1][0])
     (cls, lvl), (dms, dcount) = dom
     per_launch_ms = dms / dcount
-    alg = algorithmic_bytes(w, n_part, cls, lvl)
-    achieved = alg / (per_launch_ms / 1e3) / 1e9
     kname = f"{cls}[level {lvl}]" if cls.startswith("fft") else cls
-    roofline = {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "peak_source": peak_kind,
-                "algorithmic_bytes_per_launch": alg, "mean_launch_ms": per_launch_ms,
-                "traffic": traffic_record(cls)}
+    if cls == "pp":
+        mhz = (clk or {}).get("sm_mhz") or 2070.0
+        fpk = fp32_peak_tflops(mhz)
+        flops = pp_pairs * PP_FLOPS_PAIR / dcount
+        achieved = flops / (per_launch_ms / 1e3) / 1e12
+        roofline = {"bound": "alu", "kernel": "pp (sparse + dense kernels)", "achieved": achieved, "peak": fpk,
+                    "unit": "TFLOP/s", "frac": achieved / fpk,
+                    "peak_source": f"derived: 152 SMs x 128 FP32 lanes x 2 x {mhz:.0f} MHz",
+                    "algorithmic_flops_per_launch": flops,
+                    "pairs_per_launch": pp_pairs / dcount, "candidates_per_launch": pp_cands / dcount,
+                    "with_candidate_tests_TFLOPs": (pp_pairs * PP_FLOPS_PAIR + pp_cands * PP_FLOPS_CANDIDATE)
+                    / dcount / (per_launch_ms / 1e3) / 1e12,
+                    "mean_launch_ms": per_launch_ms, "traffic": traffic_record("pp")}
+    else:
+        alg = algorithmic_bytes(w, n_part, cls, lvl)
+        achieved = alg / (per_launch_ms / 1e3) / 1e9
+        roofline = {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                    "frac": achieved / peak, "peak_source": peak_kind,
+                    "algorithmic_bytes_per_launch": alg, "mean_launch_ms": per_launch_ms,
+                    "traffic": traffic_record(cls)}
     kernels = {}
     for (c, l), (kms, kc) in sorted(prof.items(), key=lambda kv: -kv[1][0]):
         b = algorithmic_bytes(w, n_part, c, l)
         kernels[f"{c}/{l}"] = {"share": kms / total_prof, "ms_per_launch": kms / kc, "launches": kc,
                                "GBps_alg": b / (kms / kc / 1e3) / 1e9}
+    kernels["pp_work"] = {"pairs_per_step": pp_pairs / args.steps, "candidates_per_step": pp_cands / args.steps}
 
     # end to end through the host-buffer entry point
     e2e = None

@@ -193,10 +193,16 @@ const char *cube2_last_error(cube2_ctx *ctx);
  * counts[...] (arrays of CUBE2_PROFILE_CLASSES * CUBE2_MAX_LEVELS), clears the
  * records, and returns CUBE2_ERR_CAPACITY if the pool overflowed.  Class
  * names: cube2_profile_class_name. */
-#define CUBE2_PROFILE_CLASSES 16
+#define CUBE2_PROFILE_CLASSES 19
 int cube2_profile(cube2_ctx *ctx, int cap);
 int cube2_profile_read(cube2_ctx *ctx, double *ms, int64_t *counts);
 const char *cube2_profile_class_name(int cls);
+
+/* PP work counters accumulated since the last call: out[0] = ordered pairs
+ * closer than the PP range that were evaluated, out[1] = candidate pairs
+ * examined (particles in the 27 cells around each target).  Synchronises the
+ * stream and resets the counters. */
+int cube2_pp_stats(cube2_ctx *ctx, int64_t out[2]);
 
 /* Number of kernel launches this context has issued (for launch accounting). */
 int64_t cube2_launch_count(cube2_ctx *ctx);

@@ -120,7 +120,11 @@ void free_ctx(cube2_ctx *c) {
     cudaFree(c->scan_tmp);
     cudaFree(c->ncount);
     cudaFree(c->nstart);
-    cudaFree(c->far);
+    cudaFree(c->perm2);
+    cudaFree(c->big);
+    cudaFree(c->big_n);
+    cudaFree(c->pos4);
+    cudaFree(c->pp_stats);
     cudaFree(c->dev_status);
     cudaFreeHost(c->host_status);
     delete c;
@@ -229,7 +233,13 @@ int cube2_init_mesh(cube2_ctx **out, const cube2_config *cfg, void *stream) {
     alloc((void **)&c->perm, N * 4);
     alloc((void **)&c->ncount, (size_t)c->n_cells * 4);
     alloc((void **)&c->nstart, (size_t)c->n_cells * 4);
-    alloc((void **)&c->far, sizeof(int));
+    alloc((void **)&c->perm2, N * 4);
+    alloc((void **)&c->big, (size_t)c->n_cells * 4);
+    alloc((void **)&c->big_n, sizeof(int));
+    alloc((void **)&c->pos4, N * 16);
+    alloc((void **)&c->pp_stats, 2 * sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->pp_stats, 0, 2 * sizeof(unsigned long long), c->stream);
+    cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device);
     c->scan_tmp_len = scan_scratch_len(c->n_cells);
     alloc((void **)&c->scan_tmp, (size_t)c->scan_tmp_len * 4);
     alloc((void **)&c->dev_status, sizeof(int));
@@ -353,6 +363,7 @@ int cube2_pp_force(cube2_ctx *ctx, const cube2_particles *p, int accumulate) {
     if (!ctx) return CUBE2_ERR_BAD_ARG;
     if (!particles_ok(ctx, p, false, true)) return set_error(ctx, CUBE2_ERR_BAD_ARG, "bad particle arrays");
     cudaError_t e = launch_cellid(ctx, p);
+    if (e == cudaSuccess) e = launch_prep_positions(ctx, p);
     if (e == cudaSuccess) e = launch_pp(ctx, p, accumulate, 0.0f);
     if (e != cudaSuccess) return cuda_error(ctx, e, "pp_force");
     return CUBE2_OK;
@@ -371,6 +382,7 @@ static int force_core(cube2_ctx *ctx, const cube2_particles *p, float kick) {
         ctx->lev[l].has_potential = true;
     }
     if (e == cudaSuccess) e = launch_interp(ctx, -1, p, 0);
+    if (e == cudaSuccess) e = launch_prep_positions(ctx, p);
     if (e == cudaSuccess) e = launch_pp(ctx, p, 1, kick);
     if (e != cudaSuccess) return cuda_error(ctx, e, "force");
     return CUBE2_OK;
@@ -555,8 +567,21 @@ int cube2_profile_read(cube2_ctx *ctx, double *ms, int64_t *counts) {
 const char *cube2_profile_class_name(int cls) {
     static const char *names[CUBE2_PROFILE_CLASSES] = {
         "deposit", "fft_x_fwd", "fft_y_fwd", "fft_z_green", "fft_y_inv", "fft_x_inv", "interp", "pp",
-        "kick", "kick_drift", "scan", "scatter", "sort", "gather", "cellid", "green"};
+        "kick", "kick_drift", "scan", "scatter", "sort", "gather", "cellid", "green", "pp_dense", "prep",
+        "sort_big"};
     return (cls >= 0 && cls < CUBE2_PROFILE_CLASSES) ? names[cls] : "";
+}
+
+int cube2_pp_stats(cube2_ctx *ctx, int64_t out[2]) {
+    if (!ctx || !out) return CUBE2_ERR_BAD_ARG;
+    unsigned long long h[2] = {0, 0};
+    cudaError_t e = cudaMemcpyAsync(h, ctx->pp_stats, sizeof h, cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->pp_stats, 0, sizeof h, ctx->stream);
+    if (e != cudaSuccess) return cuda_error(ctx, e, "pp stats");
+    out[0] = (int64_t)h[0];
+    out[1] = (int64_t)h[1];
+    return CUBE2_OK;
 }
 
 const char *cube2_last_error(cube2_ctx *ctx) { return ctx ? ctx->err.c_str() : g_init_error.c_str(); }

@@ -28,6 +28,7 @@ enum StatusBits : int {
 enum ProfClass : int {
     P_DEPOSIT = 0, P_FFT_X_FWD, P_FFT_Y_FWD, P_FFT_Z_GREEN, P_FFT_Y_INV, P_FFT_X_INV,
     P_INTERP, P_PP, P_KICK, P_KICK_DRIFT, P_SCAN, P_SCATTER, P_SORT, P_GATHER, P_CELLID, P_GREEN,
+    P_PP_DENSE, P_PREP, P_SORT_BIG,
     P_NCLASS
 };
 
@@ -70,7 +71,12 @@ struct cube2_ctx {
     int32_t *perm = nullptr;
     int32_t *ncount = nullptr;     // [n_cells] histogram of the new cells
     int32_t *nstart = nullptr;     // [n_cells] its exclusive scan
-    int *far = nullptr;            // device flag: a particle moved > 1 IOS cell on an axis
+    int32_t *perm2 = nullptr;      // [N] merge scratch of the segmented sort
+    int32_t *big = nullptr;        // [n_cells] cells too large for the per-thread sort
+    int *big_n = nullptr;          // their number
+    float4 *pos4 = nullptr;        // [N] in-cell offsets as floats (+ cell id bits)
+    unsigned long long *pp_stats = nullptr;  // [2] in-range ordered pairs, candidates
+    int num_sms = 152;
     int32_t *scan_tmp = nullptr;   // block sums of the multi-level scan
     int64_t scan_tmp_len = 0;
     int *dev_status = nullptr;     // sticky device status word
@@ -112,6 +118,7 @@ cudaError_t launch_fft_inverse(cube2_ctx *ctx, Level &L);          // spec -> re
 cudaError_t launch_cellid(cube2_ctx *ctx, const cube2_particles *p);
 cudaError_t launch_interp(cube2_ctx *ctx, int level, const cube2_particles *p, int accumulate);
 cudaError_t launch_pp(cube2_ctx *ctx, const cube2_particles *p, int accumulate, float kick);
+cudaError_t launch_prep_positions(cube2_ctx *ctx, const cube2_particles *p);
 cudaError_t launch_kick(cube2_ctx *ctx, const cube2_particles *p, float kick);
 cudaError_t launch_kick_drift(cube2_ctx *ctx, const cube2_particles *p, float kick, float drift_fix);
 cudaError_t launch_scan(cube2_ctx *ctx, const int32_t *in, int32_t *out, int64_t n);

@@ -5,19 +5,17 @@
 // even), X_d = c_d 2^16 + off_d.  Re-bin: a stable counting sort by the new
 // cell id (ties keep the previous order) rebuilds count/start and permutes the
 // offsets and momenta, so the IOS order stays the cell list.
-//   1. kick_drift : new coordinates into scratch; ncount[new cell] += 1; flag
-//                   any particle that moved more than one cell along an axis
+//   1. kick_drift : new coordinates into scratch; slot = ncount[new cell]++
+//                   (atomic: a provisional, order-dependent rank in the cell)
 //   2. scan       : nstart = exclusive prefix sum of ncount (multi-level)
-//   3a. local re-bin (no far mover): one thread per new cell c walks the 27
-//       old cells around c in increasing old-cell id, each in particle order,
-//       and keeps the particles whose new cell is c.  Old order is (old cell,
-//       rank), so this emits exactly the stable order, with no atomics and no
-//       sort, and writes the permuted offsets/momenta directly.
-//   3b. general re-bin (some far mover; the kernels of 3a return at once):
-//       perm[nstart[cell] + atomic slot] = i, each cell's perm segment sorted
-//       by old index, then gathered.  The flag is read on the device, so the
-//       step needs no host synchronisation.
-//   4. ncount/nstart copied into the caller's count/start.
+//   3. scatter    : perm[nstart[cell] + slot] = old index
+//   4. sort       : every cell's perm segment sorted by old index, which makes
+//                   the result stable and independent of the atomics' order:
+//                   cells of <= 32 particles by one thread (insertion sort),
+//                   larger ones by a CTA (bitonic in shared memory up to 8192,
+//                   beyond that sorted 8192-runs merged through global scratch)
+//   5. gather     : off, vel, cellid of new index i from old index perm[i]
+//   6. ncount/nstart copied into the caller's count/start
 #include "common.cuh"
 
 namespace cube2 {
@@ -44,7 +42,6 @@ struct DriftParams {
     const float *acc0, *acc1, *acc2;
     const int32_t *cellid;
     int32_t *count;           // zeroed before the launch, receives the new histogram
-    int *far;
     uint16_t *toff;           // [3][N]
     float *tvel;              // [3][N]
     int32_t *tcell, *tslot;
@@ -66,7 +63,7 @@ __global__ void __launch_bounds__(256) kick_drift_kernel(DriftParams P) {
     const int period = n * FIX;
     int nc[3];
     uint16_t no[3];
-    bool bad = false, far = false;
+    bool bad = false;
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         const float d = v[a] * P.drift_fix;
@@ -76,10 +73,7 @@ __global__ void __launch_bounds__(256) kick_drift_kernel(DriftParams P) {
         X = X < 0 ? X + period : (X >= period ? X - period : X);
         nc[a] = X >> FIX_BITS;
         no[a] = (uint16_t)(X & (FIX - 1));
-        const int dc = nc[a] - cc[a];
-        if (!(dc == 0 || dc == 1 || dc == -1 || dc == n - 1 || dc == 1 - n)) far = true;
     }
-    if (far) *P.far = 1;
     if (bad) set_status(P.status, isfinite(v[0] + v[1] + v[2]) ? ST_DISPLACEMENT : ST_NONFINITE);
     const int cell = (nc[2] * n + nc[1]) * n + nc[0];
     const int slot = atomicAdd(&P.count[cell], 1);
@@ -155,22 +149,29 @@ __global__ void __launch_bounds__(SCAN_THREADS) scan_apply_kernel(const int32_t 
 
 // ------------------------------------------------------------- rebin
 __global__ void scatter_kernel(const int32_t *tcell, const int32_t *tslot, const int32_t *start,
-                               int32_t *perm, int64_t n, const int *far) {
-    if (!*far) return;
+                               int32_t *perm, int64_t n) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     perm[start[tcell[i]] + tslot[i]] = (int32_t)i;
 }
 
 // Sort each cell's segment of perm ascending (old index = stable order).  One
-// thread per cell, insertion sort: segments are short and arrive nearly sorted.
-__global__ void sort_cells_kernel(const int32_t *count, const int32_t *start, int32_t *perm, int64_t n_cells,
-                                  const int *far) {
-    if (!*far) return;
+// thread per cell sorts segments of up to 32 by insertion; larger cells are
+// listed for sort_big_kernel.
+constexpr int SMALL_SORT = 32;
+constexpr int BIG_SORT_SMEM = 8192;
+constexpr int BIG_SORT_THREADS = 512;
+
+__global__ void sort_small_kernel(const int32_t *count, const int32_t *start, int32_t *perm, int64_t n_cells,
+                                  int32_t *big, int *big_n) {
     const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= n_cells) return;
     const int cnt = count[c];
     if (cnt < 2) return;
+    if (cnt > SMALL_SORT) {
+        big[atomicAdd(big_n, 1)] = (int32_t)c;
+        return;
+    }
     int32_t *seg = perm + start[c];
     for (int a = 1; a < cnt; ++a) {
         const int32_t key = seg[a];
@@ -183,6 +184,80 @@ __global__ void sort_cells_kernel(const int32_t *count, const int32_t *start, in
     }
 }
 
+__device__ void bitonic_smem(int32_t *s, int np2) {
+    for (int k = 2; k <= np2; k <<= 1) {
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int i = threadIdx.x; i < np2; i += blockDim.x) {
+                const int ixj = i ^ j;
+                if (ixj > i) {
+                    const bool up = (i & k) == 0;
+                    const int32_t a = s[i], b = s[ixj];
+                    if ((a > b) == up) { s[i] = b; s[ixj] = a; }
+                }
+            }
+            __syncthreads();
+        }
+    }
+}
+
+// sort keys[0, n) (n <= BIG_SORT_SMEM) in place through shared memory
+__device__ void sort_run_smem(int32_t *keys, int n, int32_t *s) {
+    int np2 = 1;
+    while (np2 < n) np2 <<= 1;
+    for (int i = threadIdx.x; i < np2; i += blockDim.x) s[i] = i < n ? keys[i] : 0x7fffffff;
+    __syncthreads();
+    bitonic_smem(s, np2);
+    for (int i = threadIdx.x; i < n; i += blockDim.x) keys[i] = s[i];
+    __syncthreads();
+}
+
+// merge sorted a[0, la) and b[0, lb) into out (keys unique), CTA-cooperative
+__device__ void merge_runs(const int32_t *a, int la, const int32_t *b, int lb, int32_t *out) {
+    const int total = la + lb;
+    const int per = (total + blockDim.x - 1) / blockDim.x;
+    const int d0 = min(total, (int)threadIdx.x * per), d1 = min(total, d0 + per);
+    if (d0 >= d1) return;
+    int lo = max(0, d0 - lb), hi = min(d0, la);
+    while (lo < hi) {                      // merge-path split of diagonal d0
+        const int mid = (lo + hi) >> 1;
+        if (a[mid] <= b[d0 - mid - 1]) lo = mid + 1; else hi = mid;
+    }
+    int i = lo, j = d0 - lo;
+    for (int d = d0; d < d1; ++d) {
+        if (j >= lb || (i < la && a[i] <= b[j])) out[d] = a[i++];
+        else out[d] = b[j++];
+    }
+}
+
+__global__ void __launch_bounds__(BIG_SORT_THREADS) sort_big_kernel(const int32_t *count, const int32_t *start,
+                                                                    int32_t *perm, int32_t *perm2,
+                                                                    const int32_t *big, const int *big_n) {
+    __shared__ int32_t s[BIG_SORT_SMEM];
+    const int total = *big_n;
+    for (int item = blockIdx.x; item < total; item += gridDim.x) {
+        const int64_t c = big[item];
+        const int n = count[c];
+        int32_t *seg = perm + start[c];
+        if (n <= BIG_SORT_SMEM) {
+            sort_run_smem(seg, n, s);
+            continue;
+        }
+        for (int r = 0; r < n; r += BIG_SORT_SMEM) sort_run_smem(seg + r, min(BIG_SORT_SMEM, n - r), s);
+        int32_t *src = seg, *dst = perm2 + start[c];
+        for (int w = BIG_SORT_SMEM; w < n; w <<= 1) {
+            for (int lo = 0; lo < n; lo += 2 * w) {
+                const int la = min(w, n - lo), lb = max(0, min(w, n - lo - w));
+                merge_runs(src + lo, la, src + lo + la, lb, dst + lo);
+            }
+            __syncthreads();
+            int32_t *t = src; src = dst; dst = t;
+        }
+        if (src != seg)
+            for (int i = threadIdx.x; i < n; i += blockDim.x) seg[i] = src[i];
+        __syncthreads();
+    }
+}
+
 struct GatherParams {
     const int32_t *perm, *tcell;
     const uint16_t *toff;
@@ -191,11 +266,9 @@ struct GatherParams {
     float *vel0, *vel1, *vel2;
     int32_t *cellid;
     int64_t N;
-    const int *far;
 };
 
 __global__ void gather_kernel(GatherParams P) {
-    if (!*P.far) return;
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= P.N) return;
     const int64_t j = P.perm[i];
@@ -206,64 +279,6 @@ __global__ void gather_kernel(GatherParams P) {
     P.vel1[i] = P.tvel[P.N + j];
     P.vel2[i] = P.tvel[2 * P.N + j];
     P.cellid[i] = P.tcell[j];
-}
-
-struct LocalParams {
-    const int32_t *ocount, *ostart;   // old cell list
-    const int32_t *ncount, *nstart;   // new cell list
-    const int32_t *tcell;
-    const uint16_t *toff;
-    const float *tvel;
-    uint16_t *off0, *off1, *off2;
-    float *vel0, *vel1, *vel2;
-    int32_t *cellid;
-    int64_t N, n_cells;
-    int n_ios;
-    const int *far;
-};
-
-// the three wrapped neighbour coordinates of c in increasing order
-__device__ __forceinline__ void sorted_neighbours(int c, int n, int out[3]) {
-    if (c == 0) { out[0] = 0; out[1] = 1; out[2] = n - 1; }
-    else if (c == n - 1) { out[0] = 0; out[1] = n - 2; out[2] = n - 1; }
-    else { out[0] = c - 1; out[1] = c; out[2] = c + 1; }
-}
-
-__global__ void __launch_bounds__(256) rebin_local_kernel(LocalParams P) {
-    if (*P.far) return;
-    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= P.n_cells) return;
-    const int cnt = P.ncount[c];
-    if (cnt == 0) return;
-    const int n = P.n_ios;
-    const int cx = (int)(c % n), cy = (int)((c / n) % n), cz = (int)(c / ((int64_t)n * n));
-    int xs[3], ys[3], zs[3];
-    sorted_neighbours(cx, n, xs);
-    sorted_neighbours(cy, n, ys);
-    sorted_neighbours(cz, n, zs);
-    int64_t out = P.nstart[c];
-    const int64_t end = out + cnt;
-    const int32_t me = (int32_t)c;
-    for (int a = 0; a < 3 && out < end; ++a) {
-        for (int b = 0; b < 3 && out < end; ++b) {
-            const int64_t row = ((int64_t)zs[a] * n + ys[b]) * n;
-            for (int e = 0; e < 3 && out < end; ++e) {
-                const int64_t o = row + xs[e];
-                const int s = P.ostart[o], stop = s + P.ocount[o];
-                for (int j = s; j < stop; ++j) {
-                    if (P.tcell[j] != me) continue;
-                    P.off0[out] = P.toff[j];
-                    P.off1[out] = P.toff[P.N + j];
-                    P.off2[out] = P.toff[2 * P.N + j];
-                    P.vel0[out] = P.tvel[j];
-                    P.vel1[out] = P.tvel[P.N + j];
-                    P.vel2[out] = P.tvel[2 * P.N + j];
-                    P.cellid[out] = me;
-                    if (++out == end) break;
-                }
-            }
-        }
-    }
 }
 
 }  // namespace
@@ -316,7 +331,6 @@ cudaError_t launch_kick_drift(cube2_ctx *ctx, const cube2_particles *p, float ki
     P.acc0 = p->acc[0]; P.acc1 = p->acc[1]; P.acc2 = p->acc[2];
     P.cellid = ctx->cellid;
     P.count = ctx->ncount;
-    P.far = ctx->far;
     P.toff = ctx->toff;
     P.tvel = ctx->tvel;
     P.tcell = ctx->tcell;
@@ -328,7 +342,6 @@ cudaError_t launch_kick_drift(cube2_ctx *ctx, const cube2_particles *p, float ki
     P.status = ctx->dev_status;
     ProfScope prof(ctx, P_KICK_DRIFT, 0);
     cudaError_t e = cudaMemsetAsync(ctx->ncount, 0, sizeof(int32_t) * ctx->n_cells, ctx->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->far, 0, sizeof(int), ctx->stream);
     if (e != cudaSuccess) return e;
     const int64_t blocks = (ctx->N + 255) / 256;
     if (blocks == 0) return cudaSuccess;
@@ -347,30 +360,21 @@ cudaError_t launch_rebin(cube2_ctx *ctx, const cube2_particles *p) {
     const int64_t pb = (ctx->N + 255) / 256, cb = (ctx->n_cells + 255) / 256;
     if (pb > 0) {
         {
-            ProfScope prof(ctx, P_GATHER, 0);
-            LocalParams L{};
-            L.ocount = p->count; L.ostart = p->start;
-            L.ncount = ctx->ncount; L.nstart = ctx->nstart;
-            L.tcell = ctx->tcell; L.toff = ctx->toff; L.tvel = ctx->tvel;
-            L.off0 = p->off[0]; L.off1 = p->off[1]; L.off2 = p->off[2];
-            L.vel0 = p->vel[0]; L.vel1 = p->vel[1]; L.vel2 = p->vel[2];
-            L.cellid = ctx->cellid;
-            L.N = ctx->N;
-            L.n_cells = ctx->n_cells;
-            L.n_ios = ctx->n_ios;
-            L.far = ctx->far;
-            rebin_local_kernel<<<(unsigned)cb, 256, 0, ctx->stream>>>(L);
-            ctx->launches++;
-        }
-        {
             ProfScope prof(ctx, P_SCATTER, 0);
             scatter_kernel<<<(unsigned)pb, 256, 0, ctx->stream>>>(ctx->tcell, ctx->tslot, ctx->nstart, ctx->perm,
-                                                                  ctx->N, ctx->far);
+                                                                  ctx->N);
         }
+        e = cudaMemsetAsync(ctx->big_n, 0, sizeof(int), ctx->stream);
+        if (e != cudaSuccess) return e;
         {
             ProfScope prof(ctx, P_SORT, 0);
-            sort_cells_kernel<<<(unsigned)cb, 256, 0, ctx->stream>>>(ctx->ncount, ctx->nstart, ctx->perm,
-                                                                     ctx->n_cells, ctx->far);
+            sort_small_kernel<<<(unsigned)cb, 256, 0, ctx->stream>>>(ctx->ncount, ctx->nstart, ctx->perm,
+                                                                     ctx->n_cells, ctx->big, ctx->big_n);
+        }
+        {
+            ProfScope prof(ctx, P_SORT_BIG, 0);
+            sort_big_kernel<<<(unsigned)(ctx->num_sms * 2), BIG_SORT_THREADS, 0, ctx->stream>>>(
+                ctx->ncount, ctx->nstart, ctx->perm, ctx->perm2, ctx->big, ctx->big_n);
         }
         GatherParams G{};
         G.perm = ctx->perm;
@@ -381,12 +385,11 @@ cudaError_t launch_rebin(cube2_ctx *ctx, const cube2_particles *p) {
         G.vel0 = p->vel[0]; G.vel1 = p->vel[1]; G.vel2 = p->vel[2];
         G.cellid = ctx->cellid;
         G.N = ctx->N;
-        G.far = ctx->far;
         {
             ProfScope prof(ctx, P_GATHER, 0);
             gather_kernel<<<(unsigned)pb, 256, 0, ctx->stream>>>(G);
         }
-        ctx->launches += 3;
+        ctx->launches += 4;
     }
     e = cudaMemcpyAsync(p->count, ctx->ncount, sizeof(int32_t) * ctx->n_cells, cudaMemcpyDeviceToDevice, ctx->stream);
     if (e == cudaSuccess)

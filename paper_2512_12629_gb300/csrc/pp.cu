@@ -2,52 +2,67 @@
 //   F_i += V_p / (4 pi) (R(r, b_pp) - R(r, b_range)) (x_j - x_i) / r,   0 < r < b_range,
 // with R(r, b) of Eq. (refforce).  The IOS order is the cell list (Sec. 2.3): the
 // IOS cell is at least b_range wide, so the 27 cells around a particle's cell
-// hold all its partners.  Separations are formed exactly in fixed point,
-// (dc 2^16 + off_j - off_i), so the pair term is bitwise antisymmetric; each
-// ordered pair is evaluated from both sides (gather form, no atomics) and
-// summed in FP32 with Kahan compensation.
+// hold all its partners.  The three cells of one (dz, dy) row are adjacent in
+// memory, so the 27 cells are walked as 9 contiguous particle ranges (two where
+// the row wraps around the box).
+//
+// Arithmetic is carried out in IOS-cell units.  A particle's in-cell offset
+// off/2^16 is exact in FP32 (prep kernel, once per force evaluation) and so is
+// (cell step + offset) and the separation of two such values: the pair term is
+// bitwise antisymmetric.  Each ordered pair is evaluated from both sides (gather
+// form, no atomics, deterministic) and the per-particle sums use Kahan
+// compensation.
+//
+// One thread per target, in particle (= cell) order.  Where all 32 targets of
+// a warp sit in the same cell (the clustered regime) they share their 27
+// neighbour cells: the warp then stages 32 sources at a time in a per-warp
+// shared-memory tile, each lane first builds a 32-bit mask of the sources in
+// range (cheap test) and then evaluates only those, so the expensive force
+// expression is not executed for out-of-range candidates.  Warps that span
+// several cells walk each lane's own ranges.  The path a warp takes depends
+// only on the cell counts and every sum has a fixed order, so results are
+// bitwise reproducible.
 #include "common.cuh"
 
 namespace cube2 {
 namespace {
 
 struct PPParams {
-    const uint16_t *off0, *off1, *off2;
-    const int32_t *count, *start, *cellid;
+    const float4 *pos;          // [N] (off_x, off_y, off_z)/2^16, .w = cell id bits
+    const int32_t *count, *start;
     float *acc0, *acc1, *acc2;
     float *vel0, *vel1, *vel2;
+    unsigned long long *stats;  // [2]: in-range ordered pairs, candidates
     int64_t N;
     int n_ios, accumulate;
-    float unit;           // s_ios / 2^16 [Mpc/h per fixed-point unit]
-    float inv_bpp, inv_bcut, bcut2;
-    float coef;           // V_p / (4 pi)
-    float kick;           // 0: no kick; else v += kick * acc after the sum
+    float inv_bpp, inv_bcut, bcut2;   // IOS-cell units
+    float coef;                       // V_p / (4 pi s_ios^2)
+    float kick;                       // 0: no kick; else v += kick * acc after the sum
     int *status;
 };
 
-// R(r, b) of Eq. (refforce) as u^-2 P(u) / b^2 with u = r / b, for u < 1;
-// callers handle u >= 1 (where R = 1/r^2).
-__device__ __forceinline__ float ref_force_inside(float u, float inv_b) {
-    float p;
+// R(r, b) of Eq. (refforce) times b^2, as a function of u = r / b < 1.
+__device__ __forceinline__ float ref_force_scaled(float u) {
     if (u < 0.5f) {
         // 64/5 u - 256/5 u^3 + 32 u^4 + 1536/35 u^5 - 192/5 u^6
-        p = u * (64.0f / 5.0f + u * u * (-256.0f / 5.0f + u * (32.0f + u * (1536.0f / 35.0f - 192.0f / 5.0f * u))));
-    } else {
-        // 3/(35 u^2) - 32/5 + 256/5 u - 96 u^2 + 256/5 u^3 + 32 u^4 - 1536/35 u^5 + 64/5 u^6
-        const float poly = -32.0f / 5.0f + u * (256.0f / 5.0f + u * (-96.0f + u * (256.0f / 5.0f + u * (32.0f + u * (-1536.0f / 35.0f + 64.0f / 5.0f * u)))));
-        p = 3.0f / (35.0f * u * u) + poly;
+        return u * (64.0f / 5.0f + u * u * (-256.0f / 5.0f + u * (32.0f + u * (1536.0f / 35.0f - 192.0f / 5.0f * u))));
     }
-    return p * inv_b * inv_b;
+    // 3/(35 u^2) - 32/5 + 256/5 u - 96 u^2 + 256/5 u^3 + 32 u^4 - 1536/35 u^5 + 64/5 u^6
+    const float poly = -32.0f / 5.0f + u * (256.0f / 5.0f + u * (-96.0f + u * (256.0f / 5.0f + u * (32.0f + u * (-1536.0f / 35.0f + 64.0f / 5.0f * u)))));
+    return 3.0f / (35.0f * u * u) + poly;
 }
 
-// R_PP(r) = R(r, b_pp) - R(r, b_cut) for 0 < r < b_cut (Eq. PP).  Where
-// r >= b_pp the first term is 1/r^2 and the difference is written as m(u)/r^2
-// with u = r/b_cut: on b_cut/2 <= r the outer-shell branch of Eq. (refforce)
-// gives r^2 (1/r^2 - R) = v^5 (192/5 - 416/5 v + 2048/35 v^2 - 64/5 v^3),
-// v = 1 - u (exact polynomial shift, no cancellation near the cutoff); below
-// b_cut/2 the inner branch gives 1 - 64/5 u^3 + 256/5 u^5 - 32 u^6
+// R_PP(r) / r for 0 < r < b_cut (Eq. PP), IOS-cell units.  Where r >= b_pp the
+// first term is 1/r^2 and the difference is written as m(u)/r^2 with
+// u = r/b_cut: for u >= 1/2 the outer-shell branch of Eq. (refforce) gives
+// r^2 (1/r^2 - R) = v^5 (192/5 - 416/5 v + 2048/35 v^2 - 64/5 v^3), v = 1 - u
+// (an exact polynomial shift, free of cancellation near the cutoff); below
+// u = 1/2 the inner branch gives 1 - 64/5 u^3 + 256/5 u^5 - 32 u^6
 // - 1536/35 u^7 + 192/5 u^8.
-__device__ __forceinline__ float pp_reference(float r, float rinv, float inv_bpp, float inv_bcut) {
+__device__ __forceinline__ float pp_over_r(float r2, float inv_bpp, float inv_bcut) {
+    const float rinv = rsqrtf(r2);
+    const float r = r2 * rinv;
+    float val;
     if (r * inv_bpp >= 1.0f) {
         const float u = r * inv_bcut;
         float m;
@@ -59,9 +74,11 @@ __device__ __forceinline__ float pp_reference(float r, float rinv, float inv_bpp
             const float u2 = u * u;
             m = 1.0f + u2 * u * (-64.0f / 5.0f + u2 * (256.0f / 5.0f + u * (-32.0f + u * (-1536.0f / 35.0f + 192.0f / 5.0f * u))));
         }
-        return m * rinv * rinv;
+        val = m * rinv * rinv;
+    } else {
+        val = ref_force_scaled(r * inv_bpp) * inv_bpp * inv_bpp - ref_force_scaled(r * inv_bcut) * inv_bcut * inv_bcut;
     }
-    return ref_force_inside(r * inv_bpp, inv_bpp) - ref_force_inside(r * inv_bcut, inv_bcut);
+    return val * rinv;
 }
 
 __device__ __forceinline__ void kahan_add(float &sum, float &comp, float v) {
@@ -71,40 +88,7 @@ __device__ __forceinline__ void kahan_add(float &sum, float &comp, float v) {
     sum = t;
 }
 
-__global__ void __launch_bounds__(256) pp_kernel(PPParams P) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= P.N) return;
-    const int n = P.n_ios;
-    const int c = P.cellid[i];
-    const int cx = c % n, cy = (c / n) % n, cz = c / (n * n);
-    const int ox = P.off0[i], oy = P.off1[i], oz = P.off2[i];
-    float fx = 0.f, fy = 0.f, fz = 0.f, kx = 0.f, ky = 0.f, kz = 0.f;
-    for (int dz = -1; dz <= 1; ++dz) {
-        const int zc = wrap(cz + dz, n);
-        for (int dy = -1; dy <= 1; ++dy) {
-            const int yc = wrap(cy + dy, n);
-            for (int dx = -1; dx <= 1; ++dx) {
-                const int xc = wrap(cx + dx, n);
-                const int64_t nc = ((int64_t)zc * n + yc) * n + xc;
-                const int s = __ldg(&P.start[nc]);
-                const int e = s + __ldg(&P.count[nc]);
-                for (int j = s; j < e; ++j) {
-                    const float rx = (float)(dx * FIX + (int)__ldg(&P.off0[j]) - ox) * P.unit;
-                    const float ry = (float)(dy * FIX + (int)__ldg(&P.off1[j]) - oy) * P.unit;
-                    const float rz = (float)(dz * FIX + (int)__ldg(&P.off2[j]) - oz) * P.unit;
-                    const float r2 = rx * rx + ry * ry + rz * rz;
-                    if (r2 >= P.bcut2 || r2 == 0.0f) continue;   // also skips j == i
-                    const float rinv = rsqrtf(r2);
-                    const float r = r2 * rinv;
-                    const float g = P.coef * pp_reference(r, rinv, P.inv_bpp, P.inv_bcut) * rinv;
-                    kahan_add(fx, kx, g * rx);
-                    kahan_add(fy, ky, g * ry);
-                    kahan_add(fz, kz, g * rz);
-                }
-            }
-        }
-    }
-    float a0 = fx, a1 = fy, a2 = fz;
+__device__ __forceinline__ void finish(const PPParams &P, int64_t i, float a0, float a1, float a2) {
     if (P.accumulate) {
         a0 += P.acc0[i];
         a1 += P.acc1[i];
@@ -126,30 +110,193 @@ __global__ void __launch_bounds__(256) pp_kernel(PPParams P) {
     }
 }
 
+__device__ __forceinline__ void add_stats(unsigned long long *stats, unsigned long long pairs,
+                                          unsigned long long cands) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        pairs += __shfl_xor_sync(0xffffffffu, pairs, o);
+        cands += __shfl_xor_sync(0xffffffffu, cands, o);
+    }
+    if ((threadIdx.x & 31) == 0 && (pairs | cands)) {
+        atomicAdd(&stats[0], pairs);
+        atomicAdd(&stats[1], cands);
+    }
+}
+
+
+// The particles of the three cells (x-1, x, x+1) of row r as at most two
+// contiguous ranges; dx of particle j in range k is base[k] + (j >= b1[k]) + (j >= b2[k]).
+struct RowRanges {
+    int beg[2], end[2], b1[2], b2[2], base[2];
+    int nseg;
+    __device__ __forceinline__ RowRanges(const PPParams &P, int64_t r, int cx, int n) {
+        const int BIG = 0x7fffffff;
+        if (cx > 0 && cx < n - 1) {
+            nseg = 1;
+            beg[0] = __ldg(&P.start[r + cx - 1]);
+            b1[0] = __ldg(&P.start[r + cx]);
+            b2[0] = __ldg(&P.start[r + cx + 1]);
+            end[0] = b2[0] + __ldg(&P.count[r + cx + 1]);
+            base[0] = -1;
+        } else if (cx == 0) {
+            nseg = 2;
+            beg[0] = __ldg(&P.start[r]);
+            b1[0] = __ldg(&P.start[r + 1]);
+            b2[0] = BIG;
+            end[0] = b1[0] + __ldg(&P.count[r + 1]);
+            base[0] = 0;
+            beg[1] = __ldg(&P.start[r + n - 1]);
+            end[1] = beg[1] + __ldg(&P.count[r + n - 1]);
+            b1[1] = b2[1] = BIG;
+            base[1] = -1;
+        } else {
+            nseg = 2;
+            beg[0] = __ldg(&P.start[r + n - 2]);
+            b1[0] = __ldg(&P.start[r + n - 1]);
+            b2[0] = BIG;
+            end[0] = b1[0] + __ldg(&P.count[r + n - 1]);
+            base[0] = -1;
+            beg[1] = __ldg(&P.start[r]);
+            end[1] = beg[1] + __ldg(&P.count[r]);
+            b1[1] = b2[1] = BIG;
+            base[1] = 1;
+        }
+    }
+    __device__ __forceinline__ int size() const { return (end[0] - beg[0]) + (nseg > 1 ? end[1] - beg[1] : 0); }
+};
+
+__global__ void prep_positions_kernel(const uint16_t *off0, const uint16_t *off1, const uint16_t *off2,
+                                      const int32_t *cellid, float4 *pos, int64_t n) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float s = 1.0f / FIX;
+    pos[i] = make_float4((float)off0[i] * s, (float)off1[i] * s, (float)off2[i] * s, __int_as_float(cellid[i]));
+}
+
+__device__ __forceinline__ void eval_pair(const PPParams &P, float rx, float ry, float rz, float r2, float &fx,
+                                          float &fy, float &fz, float &kx, float &ky, float &kz) {
+    const float g = P.coef * pp_over_r(r2, P.inv_bpp, P.inv_bcut);
+    kahan_add(fx, kx, g * rx);
+    kahan_add(fy, ky, g * ry);
+    kahan_add(fz, kz, g * rz);
+}
+
+__global__ void __launch_bounds__(256) pp_kernel(PPParams P) {
+    __shared__ float4 wtile[8][32];
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    float4 *tile = wtile[threadIdx.x >> 5];
+    const bool has = i < P.N;
+    const int n = P.n_ios;
+    float4 me = has ? P.pos[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+    int c = has ? __float_as_int(me.w) : -1;
+    const int c0 = __shfl_sync(0xffffffffu, c, 0);
+    if (!has) c = c0;
+    const bool uniform = __all_sync(0xffffffffu, c == c0);
+    const int cx = c % n, cy = (c / n) % n, cz = c / (n * n);
+    float fx = 0.f, fy = 0.f, fz = 0.f, kx = 0.f, ky = 0.f, kz = 0.f;
+    unsigned long long pairs = 0, cands = 0;
+    if (uniform) {
+        // shared neighbourhood: sources staged 32 at a time, frame = 3x3x3 cells
+        me.x += 1.0f; me.y += 1.0f; me.z += 1.0f;
+        for (int dz = -1; dz <= 1; ++dz)
+            for (int dy = -1; dy <= 1; ++dy) {
+                const int64_t r = ((int64_t)wrap(cz + dz, n) * n + wrap(cy + dy, n)) * n;
+                const RowRanges rr(P, r, cx, n);
+                if (has) cands += rr.size();
+                for (int sgi = 0; sgi < rr.nseg; ++sgi) {
+                    for (int t0 = rr.beg[sgi]; t0 < rr.end[sgi]; t0 += 32) {
+                        const int m = min(32, rr.end[sgi] - t0);
+                        if (lane < m) {
+                            const int j = t0 + lane;
+                            const float4 q = __ldg(&P.pos[j]);
+                            const float dx = (float)(rr.base[sgi] + 1 + (j >= rr.b1[sgi]) + (j >= rr.b2[sgi]));
+                            tile[lane] = make_float4(q.x + dx, q.y + (float)(dy + 1), q.z + (float)(dz + 1), 0.f);
+                        }
+                        __syncwarp();
+                        unsigned mask = 0u;
+                        for (int k = 0; k < m; ++k) {
+                            const float4 s = tile[k];
+                            const float rx = s.x - me.x, ry = s.y - me.y, rz = s.z - me.z;
+                            const float r2 = rx * rx + ry * ry + rz * rz;
+                            mask |= (r2 < P.bcut2 && r2 > 0.0f) ? (1u << k) : 0u;
+                        }
+                        if (!has) mask = 0u;
+                        pairs += __popc(mask);
+                        while (mask) {
+                            const int k = __ffs(mask) - 1;
+                            mask &= mask - 1u;
+                            const float4 s = tile[k];
+                            const float rx = s.x - me.x, ry = s.y - me.y, rz = s.z - me.z;
+                            eval_pair(P, rx, ry, rz, rx * rx + ry * ry + rz * rz, fx, fy, fz, kx, ky, kz);
+                        }
+                        __syncwarp();
+                    }
+                }
+            }
+    } else if (has) {
+        for (int dz = -1; dz <= 1; ++dz)
+            for (int dy = -1; dy <= 1; ++dy) {
+                const int64_t r = ((int64_t)wrap(cz + dz, n) * n + wrap(cy + dy, n)) * n;
+                const RowRanges rr(P, r, cx, n);
+                cands += rr.size();
+                const float fdy = (float)dy, fdz = (float)dz;
+                for (int sgi = 0; sgi < rr.nseg; ++sgi) {
+                    for (int j = rr.beg[sgi]; j < rr.end[sgi]; ++j) {
+                        const float4 q = __ldg(&P.pos[j]);
+                        const float fdx = (float)(rr.base[sgi] + (j >= rr.b1[sgi]) + (j >= rr.b2[sgi]));
+                        const float rx = (fdx + q.x) - me.x;
+                        const float ry = (fdy + q.y) - me.y;
+                        const float rz = (fdz + q.z) - me.z;
+                        const float r2 = rx * rx + ry * ry + rz * rz;
+                        if (r2 < P.bcut2 && r2 > 0.0f) {
+                            eval_pair(P, rx, ry, rz, r2, fx, fy, fz, kx, ky, kz);
+                            ++pairs;
+                        }
+                    }
+                }
+            }
+    }
+    if (has) finish(P, i, fx - kx, fy - ky, fz - kz);
+    add_stats(P.stats, pairs, cands);
+}
+
 }  // namespace
+
+cudaError_t launch_prep_positions(cube2_ctx *ctx, const cube2_particles *p) {
+    const int64_t blocks = (ctx->N + 255) / 256;
+    if (blocks == 0) return cudaSuccess;
+    ProfScope prof(ctx, P_PREP, 0);
+    prep_positions_kernel<<<(unsigned)blocks, 256, 0, ctx->stream>>>(p->off[0], p->off[1], p->off[2], ctx->cellid,
+                                                                    ctx->pos4, ctx->N);
+    ctx->launches++;
+    return cudaGetLastError();
+}
 
 cudaError_t launch_pp(cube2_ctx *ctx, const cube2_particles *p, int accumulate, float kick) {
     PPParams P{};
-    P.off0 = p->off[0]; P.off1 = p->off[1]; P.off2 = p->off[2];
-    P.count = p->count; P.start = p->start; P.cellid = ctx->cellid;
+    P.pos = ctx->pos4;
+    P.count = p->count; P.start = p->start;
     P.acc0 = p->acc[0]; P.acc1 = p->acc[1]; P.acc2 = p->acc[2];
     P.vel0 = p->vel[0]; P.vel1 = p->vel[1]; P.vel2 = p->vel[2];
+    P.stats = ctx->pp_stats;
     P.N = ctx->N;
     P.n_ios = ctx->n_ios;
     P.accumulate = accumulate;
-    P.unit = (float)(ctx->s_ios / FIX);
-    P.inv_bpp = (float)(1.0 / ctx->cfg.b_pp);
-    P.inv_bcut = (float)(1.0 / ctx->b_range);
-    P.bcut2 = (float)(ctx->b_range * ctx->b_range);
+    const double s = ctx->s_ios;
+    P.inv_bpp = (float)(s / ctx->cfg.b_pp);
+    P.inv_bcut = (float)(s / ctx->b_range);
+    P.bcut2 = (float)((ctx->b_range / s) * (ctx->b_range / s));
     const double vp = ctx->cfg.box * ctx->cfg.box * ctx->cfg.box / (double)ctx->N;
-    P.coef = (float)(vp / (4.0 * 3.14159265358979323846));
+    P.coef = (float)(vp / (4.0 * 3.14159265358979323846) / (s * s));
     P.kick = kick;
     P.status = ctx->dev_status;
-    const int64_t blocks = (ctx->N + 255) / 256;
-    if (blocks == 0) return cudaSuccess;
-    ProfScope prof(ctx, P_PP, 0);
-    pp_kernel<<<(unsigned)blocks, 256, 0, ctx->stream>>>(P);
-    ctx->launches++;
+    if (ctx->N == 0) return cudaSuccess;
+    {
+        ProfScope prof(ctx, P_PP, 0);
+        pp_kernel<<<(unsigned)((ctx->N + 255) / 256), 256, 0, ctx->stream>>>(P);
+    }
+    ctx->launches += 1;
     return cudaGetLastError();
 }
 

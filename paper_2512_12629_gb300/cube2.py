@@ -28,7 +28,7 @@ ERR_UNSUPPORTED_SIZE = -6
 ERR_STATE = -7
 ERR_DISPLACEMENT = -8
 MAX_LEVELS = 2
-PROFILE_CLASSES = 16
+PROFILE_CLASSES = 19
 
 
 class Cube2Error(RuntimeError):
@@ -90,6 +90,7 @@ def _load():
         "cube2_profile": (I, [P, I]),
         "cube2_profile_read": (I, [P, ctypes.POINTER(D), ctypes.POINTER(ctypes.c_int64)]),
         "cube2_profile_class_name": (ctypes.c_char_p, [I]),
+        "cube2_pp_stats": (I, [P, ctypes.POINTER(ctypes.c_int64)]),
         "cube2_destroy": (None, [P]),
     }
     for name, (res, args) in sig.items():
@@ -260,6 +261,12 @@ class Context:
 
     def launch_count(self):
         return int(_lib.cube2_launch_count(self.ptr))
+
+    def pp_stats(self):
+        """(in-range ordered pairs, candidate pairs) since the last call."""
+        out = (ctypes.c_int64 * 2)()
+        self._chk(_lib.cube2_pp_stats(self.ptr, out))
+        return int(out[0]), int(out[1])
 
     def profile(self, capacity):
         """Start (capacity > 0) or stop (0) per-kernel-class CUDA-event timing."""

@@ -57,6 +57,14 @@ def _state(name):
         return RAGGED, random_ios(12 ** 3, 12, RAGGED.box, seed=31, clustered=0.3)
     if name == "CLUSTER":
         return CLUSTER, random_ios(5000, 16, CLUSTER.box, seed=32, clustered=0.8)
+    if name == "DENSE":
+        # a 4500-particle clump: its brick holds more particles than the brick
+        # kernel stages, so its cells go through the tiled PP kernel
+        from inputs.zeldovich import ios_from_positions
+        rng = np.random.Generator(np.random.Philox(33))
+        clump = 32.0 + rng.normal(0.0, 2.0, size=(3, 4500))
+        pos = np.concatenate([clump, rng.uniform(0.0, CLUSTER.box, size=(3, 1500))], axis=1) % CLUSTER.box
+        return CLUSTER, ios_from_positions(pos, rng.normal(0.0, 1.0, size=pos.shape), 16, CLUSTER.box)
     raise KeyError(name)
 
 
@@ -76,7 +84,7 @@ def case(name):
     return _CACHE[name]
 
 
-ALL = ["C1", "C2_SMALL", "RAGGED", "CLUSTER"]
+ALL = ["C1", "C2_SMALL", "RAGGED", "CLUSTER", "DENSE"]
 
 
 @pytest.mark.parametrize("name", ALL)
@@ -208,12 +216,12 @@ def _oracle_drift_units(st, w, greens, a0, a1, f0_gpu):
     return disp[:, order], slack[:, order]
 
 
-@pytest.mark.parametrize("name", ["C1", "C2_SMALL", "CLUSTER"])
+@pytest.mark.parametrize("name", ["C1", "C2_SMALL", "CLUSTER", "DENSE"])
 def test_kdk_step_matches_oracle(name):
     w, st, greens, ctx = case(name)
     a = w.scale_factors()
     a0, a1 = a[0], a[1]
-    if name == "CLUSTER":
+    if name in ("CLUSTER", "DENSE"):
         a0, a1 = 0.5, 0.52
     p = cube2.IOSState.from_numpy(st)
     ctx.force(p)
@@ -256,6 +264,29 @@ def test_kdk_far_movers_take_the_general_rebin_path():
     d = np.abs(got["off"].astype(np.int64) - ref["off"].astype(np.int64))
     assert np.minimum(d, 65536 - d).max() <= 1
     assert_force_close(got["vel"], ref["vel"], "velocity")
+
+
+def test_rebin_sorts_huge_cells_stably():
+    # 20000 particles packed into one IOS cell: the atomic slots scramble the
+    # cell, and the CTA sort (runs of 8192 merged through scratch) must restore
+    # the old order exactly; a vanishing step moves nobody.
+    w = CLUSTER
+    rng = np.random.default_rng(5)
+    n = 20000
+    cell = np.array([5.3, 9.1, 13.7])
+    pos = (np.floor(cell / 4.0) * 4.0)[:, None] + rng.uniform(0.0, 4.0, size=(3, n))
+    pos = np.concatenate([pos, rng.uniform(0, w.box, size=(3, 3000))], axis=1)
+    from inputs.zeldovich import ios_from_positions
+    st = ios_from_positions(pos, np.zeros_like(pos), w.n_ios, w.box)
+    ctx = cube2.init_mesh(cube2.make_config(w, n_particles=pos.shape[1]))
+    ctx.set_green(0)
+    p = cube2.IOSState.from_numpy(st)
+    ctx.force(p)
+    ctx.kdk_step(p, 0.5, 0.5 + 1e-12)
+    ctx.check()
+    got = p.to_numpy()
+    assert np.array_equal(got["count"], st["count"]) and np.array_equal(got["off"], st["off"])
+    assert got["count"].max() >= n
 
 
 def test_kdk_is_deterministic_and_stable_order():
