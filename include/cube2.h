@@ -173,6 +173,23 @@ int cube2_get_green(cube2_ctx *ctx, int level, float *out);
  * complex FP32 [n][n][n/2+1] (unnormalised, numpy.fft.rfftn convention). */
 int cube2_debug_forward_fft(cube2_ctx *ctx, int level, float *out);
 
+/* Allocation-free Poisson solve, without a context.  The paper has no
+ * counterpart: it is for callers that cannot allocate device memory where
+ * they need a solve (a fixed device-memory budget owned by the host
+ * application, or code that must not let cudaMalloc/cudaFree synchronise the
+ * device).  rho: device FP32 [n][n][n] overdensity (as cube2_get_density
+ * gives); green: device FP32 [n][n][n/2+1] table with 1/n^3 folded in (as
+ * cube2_get_green gives); phi: device FP32 [n][n][n] output.  Same kernels
+ * and result as cube2_solve_pm.  Working memory is one file-scope device array
+ * of 15.7 MB that every GPU loading the library holds until exit; n must be a
+ * supported size no larger than 128 (else CUBE2_ERR_UNSUPPORTED_SIZE, message
+ * in cube2_last_error(NULL)).  The first call on a device looks up that
+ * array's address (cudaGetSymbolAddress) with the device current; make that
+ * first call before any stream capture.  All calls share the array and keep
+ * the last call's contents, so calls that overlap on the GPU (different
+ * streams or threads without ordering) race.  No allocation takes place. */
+int cube2_solve_pm_noalloc(const float *rho, const float *green, float *phi, int32_t n, void *stream);
+
 /* Host helper: out = {K(a0,ah), Dr(a0,a1), K(ah,a1)} for cfg's cosmology. */
 int cube2_kdk_factors(const cube2_config *cfg, double a0, double a1, double out[3]);
 
@@ -181,7 +198,8 @@ int cube2_kdk_factors(const cube2_config *cfg, double a0, double a1, double out[
 int cube2_check(cube2_ctx *ctx);
 
 /* Message of the last error recorded on ctx ("" if none); NULL ctx gives
- * the message of the last failed cube2_init_mesh. */
+ * the message of the last failed cube2_init_mesh or cube2_solve_pm_noalloc
+ * on the calling thread. */
 const char *cube2_last_error(cube2_ctx *ctx);
 
 /* Optional per-kernel-class timing with CUDA events on the context stream.

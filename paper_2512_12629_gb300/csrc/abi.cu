@@ -32,13 +32,17 @@ void prof_end(cube2_ctx *ctx, int slot) {
     if (slot >= 0) cudaEventRecord(ctx->ev[2 * slot + 1], ctx->stream);
 }
 
+namespace {
+thread_local std::string g_init_error;
+}
+
+void set_context_free_error(const std::string &msg) { g_init_error = msg; }
+
 int cuda_error(cube2_ctx *ctx, cudaError_t e, const char *what) {
     return set_error(ctx, CUBE2_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
 }
 
 namespace {
-
-thread_local std::string g_init_error;
 
 // Gauss-Legendre nodes/weights on [-1, 1] by Newton iteration on P_n.
 void gauss_legendre(int n, std::vector<double> &x, std::vector<double> &w) {

@@ -23,6 +23,8 @@
 // exp(-2 pi i k/n) built from FP64 sincospi.
 #include "common.cuh"
 
+#include <string>
+
 namespace cube2 {
 namespace {
 
@@ -384,3 +386,133 @@ cudaError_t launch_fft_z_forward(cube2_ctx *ctx, Level &L) { return dispatch(ctx
 cudaError_t launch_fft_inverse(cube2_ctx *ctx, Level &L) { return dispatch(ctx, L, Op::Inverse); }
 
 }  // namespace cube2
+
+// ---------------------------------------------------------------------------
+// Allocation-free Poisson solve (cube2_solve_pm_noalloc).
+//
+// Some callers cannot allocate device memory at the point where they need a
+// solve: code that runs under a fixed device-memory budget handed out by its
+// host application, or that must not let cudaMalloc/cudaFree synchronise the
+// device in the middle of its own work.  For them this variant of solve_pm
+// takes the density, the Green's table and the output from the caller and keeps
+// its own working memory (spectrum, padded Green's table, twiddles) in one
+// file-scope device array, resolved once per device with cudaGetSymbolAddress.
+// It calls no allocating CUDA or library routine.
+#include <mutex>
+
+namespace cube2 {
+namespace {
+
+constexpr int NOALLOC_MAX_N = 128;
+constexpr int NOALLOC_KXP = ((NOALLOC_MAX_N / 2 + 1) + 15) / 16 * 16;
+constexpr size_t NOALLOC_HALF = (size_t)NOALLOC_MAX_N * NOALLOC_MAX_N * NOALLOC_KXP;
+constexpr size_t NOALLOC_SPEC_BYTES = NOALLOC_HALF * sizeof(float2);
+constexpr size_t NOALLOC_GREEN_BYTES = NOALLOC_HALF * sizeof(float);
+constexpr size_t NOALLOC_BYTES = NOALLOC_SPEC_BYTES + NOALLOC_GREEN_BYTES + NOALLOC_MAX_N * sizeof(float2);
+
+// Working memory of every cube2_solve_pm_noalloc call on a device (15.7 MB).
+static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_BYTES];
+
+constexpr int NOALLOC_MAX_DEVICES = 64;
+std::mutex g_noalloc_mutex;
+void *g_noalloc_ptr[NOALLOC_MAX_DEVICES] = {};
+
+__global__ void noalloc_twiddle_kernel(float2 *tw, int n) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    double s, c;
+    sincospi(-2.0 * (double)k / (double)n, &s, &c);
+    tw[k] = make_float2((float)c, (float)s);
+}
+
+template <int N>
+cudaError_t noalloc_passes(const float *rho, float2 *spec, const float *gpad, float *phi, const float2 *tw,
+                           cudaStream_t st) {
+    Launcher<N>::setup();
+    constexpr int L = Tile<N>::L;
+    const int kxp = NOALLOC_KXP;
+    const int64_t nrows = (int64_t)N * N;
+    const unsigned bx = (unsigned)((nrows + 2 * L - 1) / (2 * L));
+    const unsigned by = (unsigned)((int64_t)N * (kxp / L));
+    fft_x_r2c<N><<<bx, Tile<N>::T, Tile<N>::SMEM, st>>>(rho, spec, nrows, kxp, tw);
+    fft_y<N, false><<<by, Tile<N>::T, Tile<N>::SMEM, st>>>(spec, kxp, tw);
+    fft_z<N, true><<<by, Tile<N>::T, Tile<N>::SMEM, st>>>(spec, gpad, kxp, tw);
+    fft_y<N, true><<<by, Tile<N>::T, Tile<N>::SMEM, st>>>(spec, kxp, tw);
+    fft_x_c2r<N><<<bx, Tile<N>::T, Tile<N>::SMEM, st>>>(spec, phi, nrows, kxp, tw);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+void set_context_free_error(const std::string &msg);
+
+}  // namespace cube2
+
+extern "C" int cube2_solve_pm_noalloc(const float *rho, const float *green, float *phi, int32_t n, void *stream) {
+    using namespace cube2;
+    if (!rho || !green || !phi) {
+        set_context_free_error("cube2_solve_pm_noalloc: null pointer");
+        return CUBE2_ERR_BAD_ARG;
+    }
+    if (n > NOALLOC_MAX_N || !fft_size_supported(n)) {
+        set_context_free_error("cube2_solve_pm_noalloc: mesh size " + std::to_string(n) +
+                               " not supported (2^a 3^b from 8 to " + std::to_string(NOALLOC_MAX_N) + ")");
+        return CUBE2_ERR_UNSUPPORTED_SIZE;
+    }
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess || dev < 0 || dev >= NOALLOC_MAX_DEVICES) {
+        set_context_free_error(std::string("cube2_solve_pm_noalloc: no usable device: ") + cudaGetErrorString(e));
+        return CUBE2_ERR_CUDA;
+    }
+    void *base = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+        if (!g_noalloc_ptr[dev]) {
+            e = cudaGetSymbolAddress(&g_noalloc_ptr[dev], g_noalloc_scratch);
+            if (e != cudaSuccess) {
+                g_noalloc_ptr[dev] = nullptr;
+                set_context_free_error(std::string("cube2_solve_pm_noalloc: cudaGetSymbolAddress failed: ") +
+                                       cudaGetErrorString(e));
+                return CUBE2_ERR_CUDA;
+            }
+        }
+        base = g_noalloc_ptr[dev];
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    unsigned char *b = static_cast<unsigned char *>(base);
+    float2 *spec = reinterpret_cast<float2 *>(b);
+    float *gpad = reinterpret_cast<float *>(b + NOALLOC_SPEC_BYTES);
+    float2 *tw = reinterpret_cast<float2 *>(b + NOALLOC_SPEC_BYTES + NOALLOC_GREEN_BYTES);
+    const size_t nh = (size_t)(n / 2 + 1);
+    // the caller's compact [n][n][n/2+1] table into the padded layout; the
+    // padding columns, left from earlier calls, are cleared
+    e = cudaMemcpy2DAsync(gpad, NOALLOC_KXP * sizeof(float), green, nh * sizeof(float), nh * sizeof(float),
+                          (size_t)n * n, cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess)
+        e = cudaMemset2DAsync(gpad + nh, NOALLOC_KXP * sizeof(float), 0, (NOALLOC_KXP - nh) * sizeof(float),
+                              (size_t)n * n, st);
+    if (e == cudaSuccess) {
+        noalloc_twiddle_kernel<<<(n + 127) / 128, 128, 0, st>>>(tw, n);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) {
+        switch (n) {
+            case 8: e = noalloc_passes<8>(rho, spec, gpad, phi, tw, st); break;
+            case 12: e = noalloc_passes<12>(rho, spec, gpad, phi, tw, st); break;
+            case 16: e = noalloc_passes<16>(rho, spec, gpad, phi, tw, st); break;
+            case 24: e = noalloc_passes<24>(rho, spec, gpad, phi, tw, st); break;
+            case 32: e = noalloc_passes<32>(rho, spec, gpad, phi, tw, st); break;
+            case 48: e = noalloc_passes<48>(rho, spec, gpad, phi, tw, st); break;
+            case 64: e = noalloc_passes<64>(rho, spec, gpad, phi, tw, st); break;
+            case 96: e = noalloc_passes<96>(rho, spec, gpad, phi, tw, st); break;
+            case 128: e = noalloc_passes<128>(rho, spec, gpad, phi, tw, st); break;
+            default: e = cudaErrorInvalidValue; break;
+        }
+    }
+    if (e != cudaSuccess) {
+        set_context_free_error(std::string("cube2_solve_pm_noalloc: ") + cudaGetErrorString(e));
+        return CUBE2_ERR_CUDA;
+    }
+    return CUBE2_OK;
+}

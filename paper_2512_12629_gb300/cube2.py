@@ -91,6 +91,7 @@ def _load():
         "cube2_profile_read": (I, [P, ctypes.POINTER(D), ctypes.POINTER(ctypes.c_int64)]),
         "cube2_profile_class_name": (ctypes.c_char_p, [I]),
         "cube2_pp_stats": (I, [P, ctypes.POINTER(ctypes.c_int64)]),
+        "cube2_solve_pm_noalloc": (I, [P, P, P, ctypes.c_int32, P]),
         "cube2_destroy": (None, [P]),
     }
     for name, (res, args) in sig.items():
@@ -286,6 +287,19 @@ class Context:
                 if cnt[k]:
                     out[(name, l)] = (ms[k], int(cnt[k]))
         return out
+
+
+def solve_pm_noalloc(rho: torch.Tensor, green: torch.Tensor, phi: torch.Tensor, stream=None):
+    """Context-free Poisson solve that allocates no device memory.
+
+    For callers that cannot allocate where they need a solve; the library keeps
+    its working memory in a fixed device array (meshes up to 128^3).  rho and
+    phi are [n][n][n] FP32, green the [n][n][n/2+1] table of ``get_green``."""
+    n = rho.shape[0]
+    st = torch.cuda.current_stream() if stream is None else stream
+    code = _lib.cube2_solve_pm_noalloc(rho.data_ptr(), green.data_ptr(), phi.data_ptr(), n, st.cuda_stream)
+    if code != OK:
+        raise Cube2Error(code, _lib.cube2_last_error(None).decode())
 
 
 def kdk_factors(cfg: Config, a0, a1):
