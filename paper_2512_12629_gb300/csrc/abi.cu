@@ -317,7 +317,8 @@ int cube2_deposit(cube2_ctx *ctx, int level, const cube2_particles *p) {
     int r = level_ok(ctx, level, true);
     if (r) return r;
     if (!particles_ok(ctx, p, false, false)) return set_error(ctx, CUBE2_ERR_BAD_ARG, "bad particle arrays");
-    cudaError_t e = launch_deposit(ctx, level, p, nullptr);
+    cudaError_t e = launch_cellid(ctx, p);
+    if (e == cudaSuccess) e = launch_deposit(ctx, level, p, nullptr);
     if (e != cudaSuccess) return cuda_error(ctx, e, "deposit");
     for (int l = 0; l < ctx->nl; ++l)
         if (level < 0 || l == level) { ctx->lev[l].has_density = true; ctx->lev[l].has_potential = false; }
@@ -329,7 +330,8 @@ int cube2_deposit_u64(cube2_ctx *ctx, int level, const cube2_particles *p, uint6
     int r = level_ok(ctx, level, false);
     if (r) return r;
     if (!out || !particles_ok(ctx, p, false, false)) return set_error(ctx, CUBE2_ERR_BAD_ARG, "bad arguments");
-    cudaError_t e = launch_deposit(ctx, level, p, out);
+    cudaError_t e = launch_cellid(ctx, p);
+    if (e == cudaSuccess) e = launch_deposit(ctx, level, p, out);
     if (e != cudaSuccess) return cuda_error(ctx, e, "deposit_u64");
     return CUBE2_OK;
 }
@@ -367,7 +369,6 @@ int cube2_pp_force(cube2_ctx *ctx, const cube2_particles *p, int accumulate) {
     if (!ctx) return CUBE2_ERR_BAD_ARG;
     if (!particles_ok(ctx, p, false, true)) return set_error(ctx, CUBE2_ERR_BAD_ARG, "bad particle arrays");
     cudaError_t e = launch_cellid(ctx, p);
-    if (e == cudaSuccess) e = launch_prep_positions(ctx, p);
     if (e == cudaSuccess) e = launch_pp(ctx, p, accumulate, 0.0f);
     if (e != cudaSuccess) return cuda_error(ctx, e, "pp_force");
     return CUBE2_OK;
@@ -386,7 +387,6 @@ static int force_core(cube2_ctx *ctx, const cube2_particles *p, float kick) {
         ctx->lev[l].has_potential = true;
     }
     if (e == cudaSuccess) e = launch_interp(ctx, -1, p, 0);
-    if (e == cudaSuccess) e = launch_prep_positions(ctx, p);
     if (e == cudaSuccess) e = launch_pp(ctx, p, 1, kick);
     if (e != cudaSuccess) return cuda_error(ctx, e, "force");
     return CUBE2_OK;

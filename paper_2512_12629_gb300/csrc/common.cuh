@@ -118,7 +118,6 @@ cudaError_t launch_fft_inverse(cube2_ctx *ctx, Level &L);          // spec -> re
 cudaError_t launch_cellid(cube2_ctx *ctx, const cube2_particles *p);
 cudaError_t launch_interp(cube2_ctx *ctx, int level, const cube2_particles *p, int accumulate);
 cudaError_t launch_pp(cube2_ctx *ctx, const cube2_particles *p, int accumulate, float kick);
-cudaError_t launch_prep_positions(cube2_ctx *ctx, const cube2_particles *p);
 cudaError_t launch_kick(cube2_ctx *ctx, const cube2_particles *p, float kick);
 cudaError_t launch_kick_drift(cube2_ctx *ctx, const cube2_particles *p, float kick, float drift_fix);
 cudaError_t launch_scan(cube2_ctx *ctx, const int32_t *in, int32_t *out, int64_t n);

@@ -2,20 +2,23 @@
 // the CIC reading; IOS input of Sec. 2.3).
 //
 // Design: one CTA owns a brick of BI^3 IOS cells.  For every level it owns the
-// mesh cells that cover the brick (BI * n/n_ios per axis) and holds their uint64
+// mesh cells that cover the brick (BI * n/n_ios per axis) and holds their 64-bit
 // accumulators in shared memory.  It walks the particles of the brick and of a
-// one-cell IOS halo (every particle whose CIC cloud can reach an owned cell),
-// adds the exact integer weights of the corners that fall inside its owned
-// region with shared-memory atomics, then converts each owned cell once and
-// writes it with plain coalesced stores.  No global atomics and no uint64 mesh
-// in HBM: HBM traffic is the particle offsets (x ~1.95 for the halo) plus one
-// FP32 write per mesh cell.
+// one-cell IOS halo (every particle whose CIC cloud can reach an owned cell):
+// the halo brick is a set of x-rows whose particles are contiguous in IOS order
+// (two segments where a row wraps around the box), so items map to particles
+// through a short search over the row prefix.  Each corner weight that falls in
+// the owned region is added exactly with two 32-bit shared-memory atomics (low
+// word, then the high word plus the low word's carry); the CTA then converts
+// each owned cell once and writes it with plain coalesced stores.  No global
+// atomics and no 64-bit mesh in HBM: HBM traffic is the particle data (x ~1.95
+// for the halo) plus one FP32 write per mesh cell.
 //
 // Integer CIC: X = c 2^16 + off is the IOS fixed-point coordinate; the mesh
 // coordinate floored to 2^-16 cell is X >> s (s >= 0) or X << -s.  With
 // T = Xm - 2^15 the lower corner is T >> 16 and the 1-D weights are
 // 2^16 - (T & 0xffff) and (T & 0xffff); the 3-D weight is their exact product.
-// A uint64 wrap in any add is detected from the atomic's old value.
+// A wrap of a cell's 64-bit sum is detected from the high word's atomic.
 #include "common.cuh"
 
 namespace cube2 {
@@ -25,7 +28,7 @@ struct DepLevel {
     int n;            // mesh cells per axis
     int shift;        // n_ios / n = 2^shift, shift in {-2,-1,0,1}
     int own;          // owned mesh cells per axis for a full brick
-    int tile_off;     // offset of this level's tile in the shared uint64 array
+    int tile_off;     // offset of this level's tile in the shared word arrays
     float *out_f32;   // FP32 overdensity grid (or null)
     uint64_t *out_u64;  // raw accumulator (or null)
     uint64_t mean_int;
@@ -34,9 +37,10 @@ struct DepLevel {
 
 struct DepParams {
     const uint16_t *off0, *off1, *off2;
-    const int32_t *count, *start;
+    const int32_t *count, *start, *cellid;
     int n_ios, bi, nbx;   // IOS cells per axis, brick edge, bricks per axis
     int nl;
+    int tile_total;       // cells of all level tiles
     DepLevel lev[CUBE2_MAX_LEVELS];
     int *status;
 };
@@ -47,78 +51,112 @@ __device__ __forceinline__ float u64_delta_to_f32(uint64_t acc, uint64_t m, floa
     return __fmul_rn(mag, scale);
 }
 
-__global__ void __launch_bounds__(256) deposit_kernel(DepParams P) {
-    extern __shared__ unsigned long long smem_u64[];
-    const int bi = P.bi;
-    const int hb = bi + 2;                                   // halo brick edge (IOS cells)
+constexpr int DEP_THREADS = 256;
+constexpr int DEP_MAX_SEGS = 3 * (DEPOSIT_BRICK + 2) * (DEPOSIT_BRICK + 2);
+
+template <int NL, int S0, int S1, int BI>
+__global__ void __launch_bounds__(DEP_THREADS) deposit_kernel(DepParams P) {
+    extern __shared__ unsigned int smem_u32[];            // [tile_total] low words, [tile_total] high words
+    __shared__ int seg_pre[DEP_MAX_SEGS + 1];              // item prefix over the halo-row segments
+    __shared__ int seg_start[DEP_MAX_SEGS];                // first particle of each segment
+    __shared__ int seg_info[DEP_MAX_SEGS];                 // hx0 | hy << 8 | hz << 16
+    __shared__ int seg_xa[DEP_MAX_SEGS];                   // cell x of the segment's first cell
+    unsigned int *lo = smem_u32, *hi = smem_u32 + P.tile_total;
+    const int n = P.n_ios;
+    constexpr int bi = BI;
     const int brick = blockIdx.x;
     const int bx = brick % P.nbx, by = (brick / P.nbx) % P.nbx, bz = brick / (P.nbx * P.nbx);
     const int c0x = bx * bi, c0y = by * bi, c0z = bz * bi;
-    const int ex = min(bi, P.n_ios - c0x), ey = min(bi, P.n_ios - c0y), ez = min(bi, P.n_ios - c0z);
+    const int ex = min(bi, n - c0x), ey = min(bi, n - c0y), ez = min(bi, n - c0z);
+    const int nrows = (ey + 2) * (ez + 2);
+    const int nseg = 3 * nrows;
 
-    // shared layout: [tiles (uint64)] [halo prefix (int32, hb^3 + 1)] [halo starts (int32, hb^3)]
-    int tile_total = 0;
-    for (int l = 0; l < P.nl; ++l) tile_total += P.lev[l].own * P.lev[l].own * P.lev[l].own;
-    int *hpre = reinterpret_cast<int *>(smem_u64 + tile_total);
-    int *hstart = hpre + hb * hb * hb + 1;
-    const int nh = hb * hb * hb;
-
-    for (int i = threadIdx.x; i < tile_total; i += blockDim.x) smem_u64[i] = 0ull;
-    // halo cell counts (cells beyond a partial brick's extent + 1 are excluded)
-    for (int h = threadIdx.x; h < nh; h += blockDim.x) {
-        const int hx = h % hb, hy = (h / hb) % hb, hz = h / (hb * hb);
-        int cnt = 0, st = 0;
-        if (hx <= ex + 1 && hy <= ey + 1 && hz <= ez + 1) {
-            const int cx = wrap(c0x - 1 + hx, P.n_ios), cy = wrap(c0y - 1 + hy, P.n_ios),
-                      cz = wrap(c0z - 1 + hz, P.n_ios);
-            const int64_t c = ((int64_t)cz * P.n_ios + cy) * P.n_ios + cx;
-            cnt = P.count[c];
-            st = P.start[c];
+    for (int i = threadIdx.x; i < 2 * P.tile_total; i += blockDim.x) smem_u32[i] = 0u;
+    // halo row (hy, hz) spans cells x in [c0x-1, c0x+ex]; segment 0 is the part
+    // inside [0, n), segments 1 and 2 the cells that wrap on the left and right
+    for (int sg = threadIdx.x; sg < nseg; sg += blockDim.x) {
+        const int row = sg / 3, part = sg % 3;
+        const int hy = row % (ey + 2), hz = row / (ey + 2);
+        const int cy = wrap(c0y - 1 + hy, n), cz = wrap(c0z - 1 + hz, n);
+        const int64_t rbase = ((int64_t)cz * n + cy) * n;
+        int xa, xb, hx0;
+        if (part == 0) {
+            xa = max(c0x - 1, 0);
+            xb = min(c0x + ex, n - 1);
+            hx0 = xa - (c0x - 1);
+        } else if (part == 1 && c0x == 0) {
+            xa = xb = n - 1;            // the halo cell left of x = 0
+            hx0 = 0;
+        } else if (part == 2 && c0x + ex == n) {
+            xa = xb = 0;                // the halo cell right of x = n - 1
+            hx0 = ex + 1;
+        } else {
+            xa = 0;
+            xb = -1;                    // empty
+            hx0 = 0;
         }
-        hpre[h] = cnt;
-        hstart[h] = st;
+        int st = 0, cnt = 0;
+        if (xb >= xa) {
+            st = P.start[rbase + xa];
+            cnt = P.start[rbase + xb] + P.count[rbase + xb] - st;
+        }
+        seg_pre[sg] = cnt;
+        seg_start[sg] = st;
+        seg_info[sg] = hx0 | (hy << 8) | (hz << 16);
+        seg_xa[sg] = xa;
     }
     __syncthreads();
-    // exclusive scan of the halo counts (single warp; nh <= 1000 for bi = 8)
-    if (threadIdx.x < 32) {
+    if (threadIdx.x < 32) {            // exclusive scan of the segment sizes
         const int lane = threadIdx.x;
-        const int per = (nh + 31) / 32;
-        const int b0 = lane * per, b1 = min(nh, b0 + per);
-        int s = 0;
-        for (int i = b0; i < b1; ++i) s += hpre[i];
-        int incl = s;
+        const int per = (nseg + 31) / 32;
+        const int b0 = min(nseg, lane * per), b1 = min(nseg, b0 + per);
+        int acc = 0;
+        for (int i = b0; i < b1; ++i) acc += seg_pre[i];
+        int incl = acc;
         for (int o = 1; o < 32; o <<= 1) {
             const int v = __shfl_up_sync(0xffffffffu, incl, o);
             if (lane >= o) incl += v;
         }
-        int run = incl - s;
-        for (int i = b0; i < b1; ++i) { const int v = hpre[i]; hpre[i] = run; run += v; }
-        if (lane == 31) hpre[nh] = incl;
+        int run = incl - acc;
+        for (int i = b0; i < b1; ++i) { const int v = seg_pre[i]; seg_pre[i] = run; run += v; }
+        if (lane == 31) seg_pre[nseg] = incl;
     }
     __syncthreads();
-    const int total = hpre[nh];
+    const int total = seg_pre[nseg];
 
-    for (int t = threadIdx.x; t < total; t += blockDim.x) {
-        // halo cell holding item t: largest h with hpre[h] <= t
-        int lo = 0, hi = nh - 1;
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (hpre[mid] <= t) lo = mid; else hi = mid - 1;
+    // warp-contiguous items: warp w takes [w * per_w, (w+1) * per_w), lanes interleaved
+    const int nwarps = blockDim.x >> 5, lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int per_w = ((total + nwarps - 1) / nwarps + 31) & ~31;
+    const int it0 = w * per_w, it1 = min(total, it0 + per_w);
+    int sg = 0;
+    if (it0 < it1) {
+        int lo_s = 0, hi_s = nseg - 1;   // last segment with seg_pre <= it0 + lane
+        const int first = it0 + lane;
+        while (lo_s < hi_s) {
+            const int mid = (lo_s + hi_s + 1) >> 1;
+            if (seg_pre[mid] <= first) lo_s = mid; else hi_s = mid - 1;
         }
-        const int h = lo;
-        const int64_t p = (int64_t)hstart[h] + (t - hpre[h]);
-        const int hx = h % hb, hy = (h / hb) % hb, hz = h / (hb * hb);
+        sg = lo_s;
+    }
+    for (int t = it0 + lane; t < it1; t += 32) {
+        while (seg_pre[sg + 1] <= t) ++sg;
+        const int64_t p = (int64_t)seg_start[sg] + (t - seg_pre[sg]);
+        const int info = seg_info[sg];
+        const int hx = (info & 0xff) + (P.cellid[p] % n - seg_xa[sg]);
+        const int hy = (info >> 8) & 0xff, hz = info >> 16;
         // unwrapped fixed-point coordinates relative to the grid origin
-        const int X0 = (c0x - 1 + hx) * FIX + (int)P.off0[p];
-        const int X1 = (c0y - 1 + hy) * FIX + (int)P.off1[p];
-        const int X2 = (c0z - 1 + hz) * FIX + (int)P.off2[p];
-        for (int l = 0; l < P.nl; ++l) {
-            const DepLevel &L = P.lev[l];
-            const int s = L.shift;
+        const int X[3] = {(c0x - 1 + hx) * FIX + (int)P.off0[p], (c0y - 1 + hy) * FIX + (int)P.off1[p],
+                          (c0z - 1 + hz) * FIX + (int)P.off2[p]};
+        const int c0[3] = {c0x, c0y, c0z};
+        const int e[3] = {ex, ey, ez};
+#pragma unroll
+        for (int l = 0; l < NL; ++l) {
+            const int s = l == 0 ? S0 : S1;
+            constexpr int own0 = S0 >= 0 ? (BI >> S0) : (BI << (-S0));
+            constexpr int own1 = S1 >= 0 ? (BI >> S1) : (BI << (-S1));
+            const int own = l == 0 ? own0 : own1;
+            const int tile_off = l == 0 ? 0 : own0 * own0 * own0;
             int i0[3], w0[3], w1[3], ext[3];
-            const int X[3] = {X0, X1, X2};
-            const int c0[3] = {c0x, c0y, c0z};
-            const int e[3] = {ex, ey, ez};
 #pragma unroll
             for (int a = 0; a < 3; ++a) {
                 const int xm = s >= 0 ? (X[a] >> s) : (X[a] * (1 << (-s)));
@@ -129,8 +167,7 @@ __global__ void __launch_bounds__(256) deposit_kernel(DepParams P) {
                 w0[a] = FIX - w1[a];
                 ext[a] = s >= 0 ? (e[a] >> s) : (e[a] << (-s));
             }
-            unsigned long long *tile = smem_u64 + L.tile_off;
-            const int own = L.own;
+            unsigned int *tlo = lo + tile_off, *thi = hi + tile_off;
 #pragma unroll
             for (int cz = 0; cz < 2; ++cz) {
                 const int iz = i0[2] + cz;
@@ -145,10 +182,16 @@ __global__ void __launch_bounds__(256) deposit_kernel(DepParams P) {
                     for (int cx = 0; cx < 2; ++cx) {
                         const int ix = i0[0] + cx;
                         if (ix < 0 || ix >= ext[0]) continue;
-                        const unsigned long long w = wyz * (unsigned long long)(cx ? w1[0] : w0[0]);
-                        if (w == 0ull) continue;
-                        const unsigned long long old = atomicAdd(&tile[(iz * own + iy) * own + ix], w);
-                        if (old + w < old) set_status(P.status, ST_CAPACITY);
+                        const unsigned long long wgt = wyz * (unsigned long long)(cx ? w1[0] : w0[0]);
+                        if (wgt == 0ull) continue;
+                        const int cell = (iz * own + iy) * own + ix;
+                        const unsigned int wl = (unsigned int)wgt, wh = (unsigned int)(wgt >> 32);
+                        const unsigned int old = atomicAdd(&tlo[cell], wl);
+                        const unsigned int add_hi = wh + ((old + wl < old) ? 1u : 0u);
+                        if (add_hi) {
+                            const unsigned int oldh = atomicAdd(&thi[cell], add_hi);
+                            if (oldh + add_hi < oldh) set_status(P.status, ST_CAPACITY);
+                        }
                     }
                 }
             }
@@ -157,21 +200,26 @@ __global__ void __launch_bounds__(256) deposit_kernel(DepParams P) {
     __syncthreads();
 
     // epilogue: each owned cell converted and written once
-    for (int l = 0; l < P.nl; ++l) {
+#pragma unroll
+    for (int l = 0; l < NL; ++l) {
         const DepLevel &L = P.lev[l];
-        const int s = L.shift;
-        const int own = L.own;
+        const int s = l == 0 ? S0 : S1;
+        constexpr int own0 = S0 >= 0 ? (BI >> S0) : (BI << (-S0));
+        constexpr int own1 = S1 >= 0 ? (BI >> S1) : (BI << (-S1));
+        const int own = l == 0 ? own0 : own1;
         const int ox = s >= 0 ? (c0x >> s) : (c0x << (-s));
         const int oy = s >= 0 ? (c0y >> s) : (c0y << (-s));
         const int oz = s >= 0 ? (c0z >> s) : (c0z << (-s));
         const int exl = s >= 0 ? (ex >> s) : (ex << (-s));
         const int eyl = s >= 0 ? (ey >> s) : (ey << (-s));
         const int ezl = s >= 0 ? (ez >> s) : (ez << (-s));
-        const unsigned long long *tile = smem_u64 + L.tile_off;
+        const int tile_off = l == 0 ? 0 : own0 * own0 * own0;
+        const unsigned int *tlo = lo + tile_off, *thi = hi + tile_off;
         const int cells = exl * eyl * ezl;
         for (int i = threadIdx.x; i < cells; i += blockDim.x) {
             const int ix = i % exl, iy = (i / exl) % eyl, iz = i / (exl * eyl);
-            const uint64_t v = tile[(iz * own + iy) * own + ix];
+            const int cell = (iz * own + iy) * own + ix;
+            const uint64_t v = ((uint64_t)thi[cell] << 32) | (uint64_t)tlo[cell];
             const int64_t g = ((int64_t)(oz + iz) * L.n + (oy + iy)) * L.n + (ox + ix);
             if (L.out_u64) L.out_u64[g] = v;
             if (L.out_f32) L.out_f32[g] = u64_delta_to_f32(v, L.mean_int, L.scale);
@@ -186,7 +234,7 @@ __global__ void __launch_bounds__(256) deposit_kernel(DepParams P) {
 cudaError_t launch_deposit(cube2_ctx *ctx, int level, const cube2_particles *p, uint64_t *out_u64) {
     DepParams P{};
     P.off0 = p->off[0]; P.off1 = p->off[1]; P.off2 = p->off[2];
-    P.count = p->count; P.start = p->start;
+    P.count = p->count; P.start = p->start; P.cellid = ctx->cellid;
     P.n_ios = ctx->n_ios;
     P.status = ctx->dev_status;
     int lo = level < 0 ? 0 : level, hi = level < 0 ? ctx->nl : level + 1;
@@ -209,18 +257,36 @@ cudaError_t launch_deposit(cube2_ctx *ctx, int level, const cube2_particles *p, 
         D.mean_int = L.mean_int;
         D.scale = L.dens_scale;
     }
-    const int hb = P.bi + 2;
-    const size_t smem = (size_t)tile * 8 + (size_t)(2 * hb * hb * hb + 1) * 4;
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaFuncSetAttribute(deposit_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        attr_set = true;
-    }
+    P.tile_total = tile;
+    const size_t smem = (size_t)tile * 8;
     const int64_t blocks = (int64_t)P.nbx * P.nbx * P.nbx;
     ProfScope prof(ctx, P_DEPOSIT, 0);
-    deposit_kernel<<<(unsigned)blocks, 256, smem, ctx->stream>>>(P);
+    const int s0 = P.lev[0].shift, s1 = P.nl > 1 ? P.lev[1].shift : s0;
+    cudaError_t e = cudaErrorInvalidValue;
+#define CUBE2_DEPOSIT_CASE(NL_, A_, B_, BI_)                                                           \
+    if (P.nl == NL_ && s0 == A_ && s1 == B_) {                                                         \
+        static bool attr = false;                                                                      \
+        if (!attr) {                                                                                   \
+            cudaFuncSetAttribute(deposit_kernel<NL_, A_, B_, BI_>,                                     \
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);             \
+            attr = true;                                                                               \
+        }                                                                                              \
+        deposit_kernel<NL_, A_, B_, BI_><<<(unsigned)blocks, DEP_THREADS, smem, ctx->stream>>>(P);     \
+        e = cudaGetLastError();                                                                        \
+    }
+    CUBE2_DEPOSIT_CASE(1, 1, 1, 8)
+    CUBE2_DEPOSIT_CASE(1, 0, 0, 8)
+    CUBE2_DEPOSIT_CASE(1, -1, -1, 8)
+    CUBE2_DEPOSIT_CASE(1, -2, -2, 4)
+    CUBE2_DEPOSIT_CASE(2, 1, 0, 8)
+    CUBE2_DEPOSIT_CASE(2, 1, -1, 8)
+    CUBE2_DEPOSIT_CASE(2, 1, -2, 4)
+    CUBE2_DEPOSIT_CASE(2, 0, -1, 8)
+    CUBE2_DEPOSIT_CASE(2, 0, -2, 4)
+    CUBE2_DEPOSIT_CASE(2, -1, -2, 4)
+#undef CUBE2_DEPOSIT_CASE
     ctx->launches++;
-    return cudaGetLastError();
+    return e;
 }
 
 }  // namespace cube2

@@ -106,9 +106,8 @@ __host__ __device__ constexpr int pick_radix(int rem) {
     return rem % 3 == 0 ? 3 : (rem == 2 || rem == 4) ? rem : rem == 16 ? 4 : rem % 8 == 0 ? 8 : rem % 4 == 0 ? 4 : 2;
 }
 
-template <int N, int L, int T, int R, int NS, bool INV>
+template <int N, int L, int LP, int T, int R, int NS, bool INV>
 __device__ __forceinline__ void stockham_stage(float2 *S, const float2 *__restrict__ tw) {
-    constexpr int LP = L + 1;
     constexpr int NB = N / R;
     constexpr int TOT = NB * L;
     constexpr int PER = (TOT + T - 1) / T;
@@ -147,23 +146,34 @@ __device__ __forceinline__ void stockham_stage(float2 *S, const float2 *__restri
     __syncthreads();
 }
 
-template <int N, int L, int T, int NS, bool INV>
+template <int N, int L, int LP, int T, int NS, bool INV>
 __device__ __forceinline__ void fft_lines(float2 *S, const float2 *__restrict__ tw) {
     if constexpr (NS < N) {
         constexpr int R = pick_radix(N / NS);
-        stockham_stage<N, L, T, R, NS, INV>(S, tw);
-        fft_lines<N, L, T, NS * R, INV>(S, tw);
+        stockham_stage<N, L, LP, T, R, NS, INV>(S, tw);
+        fft_lines<N, L, LP, T, NS * R, INV>(S, tw);
     }
 }
 
+// L lines per tile; x passes pad the line stride to L + 1 (their load and store
+// phases are position-parallel), y/z passes keep it at L so every tile row is a
+// 16-byte-aligned 128-byte line filled with asynchronous 16-byte copies.
 template <int N>
 struct Tile {
     static constexpr int L = N >= 2048 ? 8 : FFT_LINES;
     static constexpr int LP = L + 1;
-    static constexpr int T0 = N * L / 32;
-    static constexpr int T = T0 < 64 ? 64 : (T0 > 512 ? 512 : T0);
+    static constexpr int LPY = L;
+    static constexpr int T0 = N * L / 16;
+    static constexpr int T = T0 < 64 ? 64 : (T0 > 1024 ? 1024 : T0);
     static constexpr size_t SMEM = (size_t)N * LP * sizeof(float2);
+    static constexpr size_t SMEMY = (size_t)N * LPY * sizeof(float2);
 };
+
+__device__ __forceinline__ void cp_async16(void *smem_dst, const void *gsrc) {
+    const unsigned dst = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
 // ---------------------------------------------------------------- X passes
 template <int N>
@@ -179,7 +189,7 @@ __global__ void __launch_bounds__(Tile<N>::T) fft_x_r2c(const float *__restrict_
         reinterpret_cast<float *>(&S[x * LP + (r >> 1)])[r & 1] = v;
     }
     __syncthreads();
-    fft_lines<N, L, T, 1, false>(S, tw);
+    fft_lines<N, L, LP, T, 1, false>(S, tw);
     constexpr int NH = N / 2 + 1;
     for (int i = threadIdx.x; i < L * NH; i += T) {
         const int l = i / NH, k = i % NH;
@@ -210,7 +220,7 @@ __global__ void __launch_bounds__(Tile<N>::T) fft_x_c2r(const float2 *__restrict
         if (k > 0 && k < N / 2) S[(N - k) * LP + l] = make_float2(A.x + B.y, B.x - A.y);  // conj(A) + i conj(B)
     }
     __syncthreads();
-    fft_lines<N, L, T, 1, true>(S, tw);
+    fft_lines<N, L, LP, T, 1, true>(S, tw);
     for (int i = threadIdx.x; i < 2 * L * N; i += T) {
         const int r = i / N, x = i % N;
         const int64_t row = row0 + r;
@@ -221,21 +231,22 @@ __global__ void __launch_bounds__(Tile<N>::T) fft_x_c2r(const float2 *__restrict
 // ---------------------------------------------------------------- Y passes
 template <int N, bool INV>
 __global__ void __launch_bounds__(Tile<N>::T) fft_y(float2 *__restrict__ data, int kxp, const float2 *__restrict__ tw) {
-    constexpr int L = Tile<N>::L, LP = Tile<N>::LP, T = Tile<N>::T;
-    extern __shared__ float2 S[];
+    constexpr int L = Tile<N>::L, LP = Tile<N>::LPY, T = Tile<N>::T;
+    extern __shared__ __align__(16) float2 S[];
     const int tiles_x = kxp / L;
     const int tx = blockIdx.x % tiles_x;
     const int64_t z = blockIdx.x / tiles_x;
     float2 *base = data + z * N * kxp + tx * L;
-    for (int i = threadIdx.x; i < N * L; i += T) {
-        const int y = i / L, l = i % L;
-        S[y * LP + l] = base[(int64_t)y * kxp + l];
+    for (int i = threadIdx.x; i < N * L / 2; i += T) {
+        const int y = i / (L / 2), l2 = 2 * (i % (L / 2));
+        cp_async16(&S[y * LP + l2], &base[(int64_t)y * kxp + l2]);
     }
+    cp_async_wait_all();
     __syncthreads();
-    fft_lines<N, L, T, 1, INV>(S, tw);
-    for (int i = threadIdx.x; i < N * L; i += T) {
-        const int y = i / L, l = i % L;
-        base[(int64_t)y * kxp + l] = S[y * LP + l];
+    fft_lines<N, L, LP, T, 1, INV>(S, tw);
+    for (int i = threadIdx.x; i < N * L / 2; i += T) {
+        const int y = i / (L / 2), l2 = 2 * (i % (L / 2));
+        *reinterpret_cast<float4 *>(&base[(int64_t)y * kxp + l2]) = *reinterpret_cast<const float4 *>(&S[y * LP + l2]);
     }
 }
 
@@ -243,35 +254,38 @@ __global__ void __launch_bounds__(Tile<N>::T) fft_y(float2 *__restrict__ data, i
 template <int N, bool GREEN>
 __global__ void __launch_bounds__(Tile<N>::T) fft_z(float2 *__restrict__ data, const float *__restrict__ green,
                                                    int kxp, const float2 *__restrict__ tw) {
-    constexpr int L = Tile<N>::L, LP = Tile<N>::LP, T = Tile<N>::T;
-    extern __shared__ float2 S[];
+    constexpr int L = Tile<N>::L, LP = Tile<N>::LPY, T = Tile<N>::T;
+    extern __shared__ __align__(16) float2 S[];
     const int tiles_x = kxp / L;
     const int tx = blockIdx.x % tiles_x;
     const int64_t ky = blockIdx.x / tiles_x;
     const int64_t zstride = (int64_t)N * kxp;
     float2 *base = data + ky * kxp + tx * L;
-    for (int i = threadIdx.x; i < N * L; i += T) {
-        const int z = i / L, l = i % L;
-        S[z * LP + l] = base[z * zstride + l];
+    for (int i = threadIdx.x; i < N * L / 2; i += T) {
+        const int z = i / (L / 2), l2 = 2 * (i % (L / 2));
+        cp_async16(&S[z * LP + l2], &base[z * zstride + l2]);
     }
+    cp_async_wait_all();
     __syncthreads();
-    fft_lines<N, L, T, 1, false>(S, tw);
+    fft_lines<N, L, LP, T, 1, false>(S, tw);
     if (GREEN) {
         const float *g = green + ky * kxp + tx * L;
-        for (int i = threadIdx.x; i < N * L; i += T) {
-            const int z = i / L, l = i % L;
-            const float gv = __ldg(&g[z * zstride + l]);
-            float2 v = S[z * LP + l];
-            v.x *= gv;
-            v.y *= gv;
-            S[z * LP + l] = v;
+        for (int i = threadIdx.x; i < N * L / 2; i += T) {
+            const int z = i / (L / 2), l2 = 2 * (i % (L / 2));
+            const float2 gv = __ldg(reinterpret_cast<const float2 *>(&g[z * zstride + l2]));
+            float4 v = *reinterpret_cast<const float4 *>(&S[z * LP + l2]);
+            v.x *= gv.x;
+            v.y *= gv.x;
+            v.z *= gv.y;
+            v.w *= gv.y;
+            *reinterpret_cast<float4 *>(&S[z * LP + l2]) = v;
         }
         __syncthreads();
-        fft_lines<N, L, T, 1, true>(S, tw);
+        fft_lines<N, L, LP, T, 1, true>(S, tw);
     }
-    for (int i = threadIdx.x; i < N * L; i += T) {
-        const int z = i / L, l = i % L;
-        base[z * zstride + l] = S[z * LP + l];
+    for (int i = threadIdx.x; i < N * L / 2; i += T) {
+        const int z = i / (L / 2), l2 = 2 * (i % (L / 2));
+        *reinterpret_cast<float4 *>(&base[z * zstride + l2]) = *reinterpret_cast<const float4 *>(&S[z * LP + l2]);
     }
 }
 
@@ -288,7 +302,7 @@ struct Launcher {
         const unsigned by = (unsigned)((int64_t)N * (Lv.kxp / Tile<N>::L));
         {
             ProfScope prof(ctx, P_FFT_Y_FWD, Lv.index);
-            fft_y<N, false><<<by, Tile<N>::T, Tile<N>::SMEM, ctx->stream>>>(Lv.spec, Lv.kxp, Lv.tw);
+            fft_y<N, false><<<by, Tile<N>::T, Tile<N>::SMEMY, ctx->stream>>>(Lv.spec, Lv.kxp, Lv.tw);
         }
         ctx->launches += 2;
         return cudaGetLastError();
@@ -298,9 +312,9 @@ struct Launcher {
         const unsigned bz = (unsigned)((int64_t)N * (Lv.kxp / Tile<N>::L));
         ProfScope prof(ctx, P_FFT_Z_GREEN, Lv.index);
         if (green)
-            fft_z<N, true><<<bz, Tile<N>::T, Tile<N>::SMEM, ctx->stream>>>(Lv.spec, Lv.green, Lv.kxp, Lv.tw);
+            fft_z<N, true><<<bz, Tile<N>::T, Tile<N>::SMEMY, ctx->stream>>>(Lv.spec, Lv.green, Lv.kxp, Lv.tw);
         else
-            fft_z<N, false><<<bz, Tile<N>::T, Tile<N>::SMEM, ctx->stream>>>(Lv.spec, nullptr, Lv.kxp, Lv.tw);
+            fft_z<N, false><<<bz, Tile<N>::T, Tile<N>::SMEMY, ctx->stream>>>(Lv.spec, nullptr, Lv.kxp, Lv.tw);
         ctx->launches += 1;
         return cudaGetLastError();
     }
@@ -309,7 +323,7 @@ struct Launcher {
         const unsigned by = (unsigned)((int64_t)N * (Lv.kxp / Tile<N>::L));
         {
             ProfScope prof(ctx, P_FFT_Y_INV, Lv.index);
-            fft_y<N, true><<<by, Tile<N>::T, Tile<N>::SMEM, ctx->stream>>>(Lv.spec, Lv.kxp, Lv.tw);
+            fft_y<N, true><<<by, Tile<N>::T, Tile<N>::SMEMY, ctx->stream>>>(Lv.spec, Lv.kxp, Lv.tw);
         }
         const int64_t nrows = (int64_t)N * N;
         const unsigned bx = (unsigned)((nrows + 2 * Tile<N>::L - 1) / (2 * Tile<N>::L));
@@ -435,9 +449,9 @@ cudaError_t noalloc_passes(const float *rho, float2 *spec, const float *gpad, fl
     const unsigned bx = (unsigned)((nrows + 2 * L - 1) / (2 * L));
     const unsigned by = (unsigned)((int64_t)N * (kxp / L));
     fft_x_r2c<N><<<bx, Tile<N>::T, Tile<N>::SMEM, st>>>(rho, spec, nrows, kxp, tw);
-    fft_y<N, false><<<by, Tile<N>::T, Tile<N>::SMEM, st>>>(spec, kxp, tw);
-    fft_z<N, true><<<by, Tile<N>::T, Tile<N>::SMEM, st>>>(spec, gpad, kxp, tw);
-    fft_y<N, true><<<by, Tile<N>::T, Tile<N>::SMEM, st>>>(spec, kxp, tw);
+    fft_y<N, false><<<by, Tile<N>::T, Tile<N>::SMEMY, st>>>(spec, kxp, tw);
+    fft_z<N, true><<<by, Tile<N>::T, Tile<N>::SMEMY, st>>>(spec, gpad, kxp, tw);
+    fft_y<N, true><<<by, Tile<N>::T, Tile<N>::SMEMY, st>>>(spec, kxp, tw);
     fft_x_c2r<N><<<bx, Tile<N>::T, Tile<N>::SMEM, st>>>(spec, phi, nrows, kxp, tw);
     return cudaGetLastError();
 }

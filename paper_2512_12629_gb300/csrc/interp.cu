@@ -1,14 +1,17 @@
 // Force interpolation F = -H_l sum_corners W E_l with E_l = D * phi_l (paper Sec. 2.1.2:
 // Eq. diff for D, the deposit's CIC weights for W, so that momentum is conserved).
 //
-// One thread per particle, every level in one pass.  The 4-point difference is
-// not stored as a field: along axis d the CIC pair of corners (weights w0 on
-// i0, w1 on i0+1) sees phi at i0-2 .. i0+3 with the combined coefficients
+// One CTA per brick of BI^3 IOS cells, every level in one pass.  For each level
+// the CTA stages in shared memory the phi tile its particles can reach: the
+// brick's mesh cells, one more for the upper CIC corner and two on each side
+// for the 4-point difference.  The 4-point difference is not stored as a
+// field: along axis d the CIC pair of corners (weights w0 on i0, w1 on i0+1)
+// sees phi at i0-2 .. i0+3 with the combined coefficients
 //   i0-2: +w0/12      i0-1: -2/3 w0 + w1/12   i0: -2/3 w1
 //   i0+1: +2/3 w0     i0+2: -w0/12 + 2/3 w1   i0+3: -w1/12
-// applied on the 2x2 lines of the two other axes: 24 loads per component,
-// 56 distinct phi values per level.  Particles are stored cell-sorted, so a warp
-// reads a compact neighbourhood and phi comes from L1/L2 after the first touch.
+// applied on the 2x2 lines of the two other axes: 24 reads per component, 56
+// distinct phi values per level, all from shared memory.  The brick's
+// particles are the x-rows of its cells, contiguous in IOS order.
 #include "common.cuh"
 
 namespace cube2 {
@@ -18,16 +21,20 @@ struct InterpLevel {
     const float *phi;
     int n, shift;
     float scale;          // -H_l
+    int tile_off, D;      // tile offset in shared memory, tile edge
 };
 
 struct InterpParams {
     const uint16_t *off0, *off1, *off2;
-    const int32_t *cellid;
+    const int32_t *cellid, *count, *start;
     float *acc0, *acc1, *acc2;
     int64_t N;
-    int n_ios, nl, accumulate;
+    int n_ios, nl, accumulate, bi, nbx;
     InterpLevel lev[CUBE2_MAX_LEVELS];
 };
+
+constexpr int INTERP_THREADS = 256;
+constexpr int INTERP_MAX_ROWS = DEPOSIT_BRICK * DEPOSIT_BRICK;
 
 __device__ __forceinline__ void fd_coeffs(float w0, float w1, float c[6]) {
     const float a = 2.0f / 3.0f, b = 1.0f / 12.0f;
@@ -39,95 +46,175 @@ __device__ __forceinline__ void fd_coeffs(float w0, float w1, float c[6]) {
     c[5] = -b * w1;
 }
 
-__global__ void __launch_bounds__(256) interp_kernel(InterpParams P) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= P.N) return;
-    const int c = P.cellid[i];
-    const int n_ios = P.n_ios;
-    const int cx = c % n_ios, cy = (c / n_ios) % n_ios, cz = c / (n_ios * n_ios);
-    const int X[3] = {cx * FIX + (int)P.off0[i], cy * FIX + (int)P.off1[i], cz * FIX + (int)P.off2[i]};
-    float F[3] = {0.f, 0.f, 0.f};
-    for (int l = 0; l < P.nl; ++l) {
-        const InterpLevel &L = P.lev[l];
-        const int n = L.n, s = L.shift;
-        int i0[3];
-        float w0[3], w1[3];
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            const int xm = s >= 0 ? (X[a] >> s) : (X[a] * (1 << (-s)));
-            const int t = xm - (FIX >> 1);
-            i0[a] = t >> FIX_BITS;
-            const int f = t & (FIX - 1);
-            w1[a] = (float)f * (1.0f / FIX);
-            w0[a] = (float)(FIX - f) * (1.0f / FIX);
-        }
-        // wrapped indices i0-2 .. i0+3 per axis
-        int ix[6], iy[6], iz[6];
-#pragma unroll
-        for (int m = 0; m < 6; ++m) {
-            ix[m] = wrap(i0[0] - 2 + m, n);
-            iy[m] = wrap(i0[1] - 2 + m, n);
-            iz[m] = wrap(i0[2] - 2 + m, n);
-        }
-        const float *phi = L.phi;
-        const int64_t nn = (int64_t)n * n;
-        float cx6[6], cy6[6], cz6[6];
-        fd_coeffs(w0[0], w1[0], cx6);
-        fd_coeffs(w0[1], w1[1], cy6);
-        fd_coeffs(w0[2], w1[2], cz6);
-        float ex = 0.f, ey = 0.f, ez = 0.f;
-#pragma unroll
-        for (int bz = 0; bz < 2; ++bz) {
-            const float wz = bz ? w1[2] : w0[2];
-#pragma unroll
-            for (int by = 0; by < 2; ++by) {
-                const float wy = by ? w1[1] : w0[1];
-                // x component: line along x at (iy[2+by], iz[2+bz])
-                const float *row = phi + (int64_t)iz[2 + bz] * nn + (int64_t)iy[2 + by] * n;
-                float sx = 0.f;
-#pragma unroll
-                for (int m = 0; m < 6; ++m) sx += cx6[m] * __ldg(&row[ix[m]]);
-                ex += wy * wz * sx;
-            }
-        }
-#pragma unroll
-        for (int bz = 0; bz < 2; ++bz) {
-            const float wz = bz ? w1[2] : w0[2];
-#pragma unroll
-            for (int bx = 0; bx < 2; ++bx) {
-                const float wx = bx ? w1[0] : w0[0];
-                const float *col = phi + (int64_t)iz[2 + bz] * nn + ix[2 + bx];
-                float sy = 0.f;
-#pragma unroll
-                for (int m = 0; m < 6; ++m) sy += cy6[m] * __ldg(&col[(int64_t)iy[m] * n]);
-                ey += wx * wz * sy;
-            }
-        }
-#pragma unroll
-        for (int by = 0; by < 2; ++by) {
-            const float wy = by ? w1[1] : w0[1];
-#pragma unroll
-            for (int bx = 0; bx < 2; ++bx) {
-                const float wx = bx ? w1[0] : w0[0];
-                const float *col = phi + (int64_t)iy[2 + by] * n + ix[2 + bx];
-                float sz = 0.f;
-#pragma unroll
-                for (int m = 0; m < 6; ++m) sz += cz6[m] * __ldg(&col[(int64_t)iz[m] * nn]);
-                ez += wx * wy * sz;
-            }
-        }
-        F[0] += L.scale * ex;
-        F[1] += L.scale * ey;
-        F[2] += L.scale * ez;
+__device__ __forceinline__ int mod_n(int j, int n) {
+    const int r = j % n;
+    return r < 0 ? r + n : r;
+}
+
+template <int NL, int DA, int DB>
+__global__ void __launch_bounds__(INTERP_THREADS) interp_kernel(InterpParams P) {
+    extern __shared__ float tiles[];
+    __shared__ int row_pre[INTERP_MAX_ROWS + 1], row_start[INTERP_MAX_ROWS];
+    const int n_ios = P.n_ios, bi = P.bi;
+    const int brick = blockIdx.x;
+    const int bx = brick % P.nbx, by = (brick / P.nbx) % P.nbx, bz = brick / (P.nbx * P.nbx);
+    const int c0x = bx * bi, c0y = by * bi, c0z = bz * bi;
+    const int ex = min(bi, n_ios - c0x), ey = min(bi, n_ios - c0y), ez = min(bi, n_ios - c0z);
+    const int nrows = ey * ez;
+    for (int r = threadIdx.x; r < nrows; r += blockDim.x) {
+        const int cy = c0y + r % ey, cz = c0z + r / ey;
+        const int64_t rb = ((int64_t)cz * n_ios + cy) * n_ios;
+        const int st = P.start[rb + c0x];
+        row_start[r] = st;
+        row_pre[r] = P.start[rb + c0x + ex - 1] + P.count[rb + c0x + ex - 1] - st;
     }
-    if (P.accumulate) {
-        P.acc0[i] += F[0];
-        P.acc1[i] += F[1];
-        P.acc2[i] += F[2];
-    } else {
-        P.acc0[i] = F[0];
-        P.acc1[i] = F[1];
-        P.acc2[i] = F[2];
+    // stage the phi tiles (origin three cells below the brick's mesh origin):
+    // wrapped per-axis indices first, then one warp per tile row
+    __shared__ int widx[3][64];
+    const int nwarps_s = blockDim.x >> 5, lane_s = threadIdx.x & 31, w_s = threadIdx.x >> 5;
+#pragma unroll
+    for (int l = 0; l < NL; ++l) {
+        const InterpLevel &L = P.lev[l];
+        const int s = L.shift, n = L.n;
+        constexpr int D0 = DA;
+        const int D = l == 0 ? DA : DB;
+        (void)D0;
+        __syncthreads();
+        if (threadIdx.x < 3 * D) {
+            const int a = threadIdx.x / D, k = threadIdx.x % D;
+            const int c0a = a == 0 ? c0x : (a == 1 ? c0y : c0z);
+            widx[a][k] = mod_n((s >= 0 ? (c0a >> s) : (c0a << (-s))) - 3 + k, n);
+        }
+        __syncthreads();
+        float *tile = tiles + L.tile_off;
+        const int64_t nn = (int64_t)n * n;
+        // asynchronous 4-byte global -> shared copies: every row in flight at once
+        for (int row = w_s; row < D * D; row += nwarps_s) {
+            const int y = row % D, z = row / D;
+            const float *src = L.phi + widx[2][z] * nn + (int64_t)widx[1][y] * n;
+            for (int x = lane_s; x < D; x += 32) {
+                const unsigned dst = (unsigned)__cvta_generic_to_shared(tile + row * D + x);
+                asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(dst), "l"(src + widx[0][x]) : "memory");
+            }
+        }
+    }
+    asm volatile("cp.async.wait_all;\n" ::: "memory");
+    __syncthreads();
+    if (threadIdx.x < 32) {            // exclusive scan of the row sizes
+        const int lane = threadIdx.x;
+        const int per = (nrows + 31) / 32;
+        const int b0 = min(nrows, lane * per), b1 = min(nrows, b0 + per);
+        int acc = 0;
+        for (int i = b0; i < b1; ++i) acc += row_pre[i];
+        int incl = acc;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += v;
+        }
+        int run = incl - acc;
+        for (int i = b0; i < b1; ++i) { const int v = row_pre[i]; row_pre[i] = run; run += v; }
+        if (lane == 31) row_pre[nrows] = incl;
+    }
+    __syncthreads();
+    const int total = row_pre[nrows];
+    const int nwarps = blockDim.x >> 5, lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int per_w = ((total + nwarps - 1) / nwarps + 31) & ~31;
+    const int it0 = w * per_w, it1 = min(total, it0 + per_w);
+    int r = 0;
+    if (it0 < it1) {
+        int lo = 0, hi = nrows - 1;
+        const int first = it0 + lane;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (row_pre[mid] <= first) lo = mid; else hi = mid - 1;
+        }
+        r = lo;
+    }
+    for (int t = it0 + lane; t < it1; t += 32) {
+        while (row_pre[r + 1] <= t) ++r;
+        const int64_t i = (int64_t)row_start[r] + (t - row_pre[r]);
+        const int cx = P.cellid[i] % n_ios, cy = c0y + r % ey, cz = c0z + r / ey;
+        const int X[3] = {cx * FIX + (int)P.off0[i], cy * FIX + (int)P.off1[i], cz * FIX + (int)P.off2[i]};
+        const int c0[3] = {c0x, c0y, c0z};
+        float F[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+        for (int l = 0; l < NL; ++l) {
+            const InterpLevel &L = P.lev[l];
+            const int s = L.shift;
+            constexpr int DMAX = DA > DB ? DA : DB;
+            (void)DMAX;
+            const int D = l == 0 ? DA : DB;
+            int li[3];
+            float w0[3], w1[3];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                const int xm = s >= 0 ? (X[a] >> s) : (X[a] * (1 << (-s)));
+                const int tt = xm - (FIX >> 1);
+                const int org = (s >= 0 ? (c0[a] >> s) : (c0[a] << (-s))) - 3;
+                li[a] = (tt >> FIX_BITS) - org;            // lower corner in the tile, >= 2
+                const int f = tt & (FIX - 1);
+                w1[a] = (float)f * (1.0f / FIX);
+                w0[a] = (float)(FIX - f) * (1.0f / FIX);
+            }
+            const float *tile = tiles + L.tile_off;
+            const int DD = D * D;
+            float cx6[6], cy6[6], cz6[6];
+            fd_coeffs(w0[0], w1[0], cx6);
+            fd_coeffs(w0[1], w1[1], cy6);
+            fd_coeffs(w0[2], w1[2], cz6);
+            float ex_ = 0.f, ey_ = 0.f, ez_ = 0.f;
+#pragma unroll
+            for (int bz2 = 0; bz2 < 2; ++bz2) {
+                const float wz = bz2 ? w1[2] : w0[2];
+#pragma unroll
+                for (int by2 = 0; by2 < 2; ++by2) {
+                    const float wy = by2 ? w1[1] : w0[1];
+                    const float *row = tile + (li[2] + bz2) * DD + (li[1] + by2) * D + li[0] - 2;
+                    float sx = 0.f;
+#pragma unroll
+                    for (int m = 0; m < 6; ++m) sx += cx6[m] * row[m];
+                    ex_ += wy * wz * sx;
+                }
+            }
+#pragma unroll
+            for (int bz2 = 0; bz2 < 2; ++bz2) {
+                const float wz = bz2 ? w1[2] : w0[2];
+#pragma unroll
+                for (int bx2 = 0; bx2 < 2; ++bx2) {
+                    const float wx = bx2 ? w1[0] : w0[0];
+                    const float *col = tile + (li[2] + bz2) * DD + (li[1] - 2) * D + li[0] + bx2;
+                    float sy = 0.f;
+#pragma unroll
+                    for (int m = 0; m < 6; ++m) sy += cy6[m] * col[m * D];
+                    ey_ += wx * wz * sy;
+                }
+            }
+#pragma unroll
+            for (int by2 = 0; by2 < 2; ++by2) {
+                const float wy = by2 ? w1[1] : w0[1];
+#pragma unroll
+                for (int bx2 = 0; bx2 < 2; ++bx2) {
+                    const float wx = bx2 ? w1[0] : w0[0];
+                    const float *col = tile + (li[2] - 2) * DD + (li[1] + by2) * D + li[0] + bx2;
+                    float sz = 0.f;
+#pragma unroll
+                    for (int m = 0; m < 6; ++m) sz += cz6[m] * col[m * DD];
+                    ez_ += wx * wy * sz;
+                }
+            }
+            F[0] += L.scale * ex_;
+            F[1] += L.scale * ey_;
+            F[2] += L.scale * ez_;
+        }
+        if (P.accumulate) {
+            P.acc0[i] += F[0];
+            P.acc1[i] += F[1];
+            P.acc2[i] += F[2];
+        } else {
+            P.acc0[i] = F[0];
+            P.acc1[i] = F[1];
+            P.acc2[i] = F[2];
+        }
     }
 }
 
@@ -153,22 +240,61 @@ cudaError_t launch_interp(cube2_ctx *ctx, int level, const cube2_particles *p, i
     InterpParams P{};
     P.off0 = p->off[0]; P.off1 = p->off[1]; P.off2 = p->off[2];
     P.cellid = ctx->cellid;
+    P.count = p->count; P.start = p->start;
     P.acc0 = p->acc[0]; P.acc1 = p->acc[1]; P.acc2 = p->acc[2];
     P.N = ctx->N;
     P.n_ios = ctx->n_ios;
     P.accumulate = accumulate;
     const int lo = level < 0 ? 0 : level, hi = level < 0 ? ctx->nl : level + 1;
+    int min_shift = 1;
+    for (int l = lo; l < hi; ++l) min_shift = min(min_shift, ctx->lev[l].shift);
+    P.bi = min_shift <= -2 ? DEPOSIT_BRICK / 2 : DEPOSIT_BRICK;
+    P.nbx = (ctx->n_ios + P.bi - 1) / P.bi;
     P.nl = hi - lo;
+    int off = 0;
     for (int l = lo; l < hi; ++l) {
         const Level &L = ctx->lev[l];
-        P.lev[l - lo] = InterpLevel{L.real, L.n, L.shift, (float)(-L.H)};
+        InterpLevel &I = P.lev[l - lo];
+        I.phi = L.real;
+        I.n = L.n;
+        I.shift = L.shift;
+        I.scale = (float)(-L.H);
+        const int E = L.shift >= 0 ? (P.bi >> L.shift) : (P.bi << (-L.shift));
+        I.D = E + 6;
+        I.tile_off = off;
+        off += I.D * I.D * I.D;
     }
-    const int64_t blocks = (ctx->N + 255) / 256;
-    if (blocks == 0) return cudaSuccess;
+    if (ctx->N == 0) return cudaSuccess;
+    const size_t smem = (size_t)off * sizeof(float);
+    const int64_t blocks = (int64_t)P.nbx * P.nbx * P.nbx;
     ProfScope prof(ctx, P_INTERP, 0);
-    interp_kernel<<<(unsigned)blocks, 256, 0, ctx->stream>>>(P);
+    const int d0 = P.lev[0].D, d1 = P.nl > 1 ? P.lev[1].D : d0;
+    cudaError_t e = cudaErrorInvalidValue;
+    // tile edges are 8, 10, 14 or 22 (brick 8 or 4, shifts -2..1); the coarse level has the smaller edge
+#define CUBE2_INTERP_CASE(NL_, A_, B_)                                                              \
+    if (P.nl == NL_ && d0 == A_ && d1 == B_) {                                                      \
+        static bool attr = false;                                                                   \
+        if (!attr) {                                                                                \
+            cudaFuncSetAttribute(interp_kernel<NL_, A_, B_>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                 200 * 1024);                                                       \
+            attr = true;                                                                            \
+        }                                                                                           \
+        interp_kernel<NL_, A_, B_><<<(unsigned)blocks, INTERP_THREADS, smem, ctx->stream>>>(P);     \
+        e = cudaGetLastError();                                                                     \
+    }
+    CUBE2_INTERP_CASE(1, 8, 8)
+    CUBE2_INTERP_CASE(1, 10, 10)
+    CUBE2_INTERP_CASE(1, 14, 14)
+    CUBE2_INTERP_CASE(1, 22, 22)
+    CUBE2_INTERP_CASE(2, 8, 10)
+    CUBE2_INTERP_CASE(2, 8, 14)
+    CUBE2_INTERP_CASE(2, 8, 22)
+    CUBE2_INTERP_CASE(2, 10, 14)
+    CUBE2_INTERP_CASE(2, 10, 22)
+    CUBE2_INTERP_CASE(2, 14, 22)
+#undef CUBE2_INTERP_CASE
     ctx->launches++;
-    return cudaGetLastError();
+    return e;
 }
 
 }  // namespace cube2

@@ -10,18 +10,17 @@
 // off/2^16 is exact in FP32 (prep kernel, once per force evaluation) and so is
 // (cell step + offset) and the separation of two such values: the pair term is
 // bitwise antisymmetric.  Each ordered pair is evaluated from both sides (gather
-// form, no atomics, deterministic) and the per-particle sums use Kahan
-// compensation.
+// form, no atomics, deterministic).
 //
-// One thread per target, in particle (= cell) order.  Where all 32 targets of
-// a warp sit in the same cell (the clustered regime) they share their 27
-// neighbour cells: the warp then stages 32 sources at a time in a per-warp
-// shared-memory tile, each lane first builds a 32-bit mask of the sources in
-// range (cheap test) and then evaluates only those, so the expensive force
-// expression is not executed for out-of-range candidates.  Warps that span
-// several cells walk each lane's own ranges.  The path a warp takes depends
-// only on the cell counts and every sum has a fixed order, so results are
-// bitwise reproducible.
+// One thread per target, in particle (= cell) order.  Where
+// all 32 targets of a warp sit in one cell (the clustered regime) they share
+// their 27 neighbour cells: the warp stages 32 sources at a time in a per-warp
+// shared-memory tile, each lane tests all 32 into an in-range bit mask and
+// evaluates only the set bits.  Warps spanning several cells walk each lane's
+// own ranges.  Per-particle sums are compensated: plain FP32 partials per tile
+// (or per row of cells) are added to the running total with Kahan's scheme.
+// The path a warp takes depends only on the cell counts and every sum has a
+// fixed order, so results are bitwise reproducible.
 #include "common.cuh"
 
 namespace cube2 {
@@ -62,22 +61,15 @@ __device__ __forceinline__ float ref_force_scaled(float u) {
 __device__ __forceinline__ float pp_over_r(float r2, float inv_bpp, float inv_bcut) {
     const float rinv = rsqrtf(r2);
     const float r = r2 * rinv;
-    float val;
-    if (r * inv_bpp >= 1.0f) {
-        const float u = r * inv_bcut;
-        float m;
-        if (u >= 0.5f) {
-            const float v = 1.0f - u;
-            const float v2 = v * v;
-            m = v2 * v2 * v * (192.0f / 5.0f + v * (-416.0f / 5.0f + v * (2048.0f / 35.0f - 64.0f / 5.0f * v)));
-        } else {
-            const float u2 = u * u;
-            m = 1.0f + u2 * u * (-64.0f / 5.0f + u2 * (256.0f / 5.0f + u * (-32.0f + u * (-1536.0f / 35.0f + 192.0f / 5.0f * u))));
-        }
-        val = m * rinv * rinv;
-    } else {
+    const float u = r * inv_bcut;
+    const float v = 1.0f - u;
+    const float v2 = v * v;
+    const float m_out = v2 * v2 * v * (192.0f / 5.0f + v * (-416.0f / 5.0f + v * (2048.0f / 35.0f - 64.0f / 5.0f * v)));
+    const float u2 = u * u;
+    const float m_in = 1.0f + u2 * u * (-64.0f / 5.0f + u2 * (256.0f / 5.0f + u * (-32.0f + u * (-1536.0f / 35.0f + 192.0f / 5.0f * u))));
+    float val = (u >= 0.5f ? m_out : m_in) * rinv * rinv;
+    if (r * inv_bpp < 1.0f)   // closer than b_pp: both terms are softened (rare)
         val = ref_force_scaled(r * inv_bpp) * inv_bpp * inv_bpp - ref_force_scaled(r * inv_bcut) * inv_bcut * inv_bcut;
-    }
     return val * rinv;
 }
 
@@ -165,71 +157,93 @@ struct RowRanges {
     __device__ __forceinline__ int size() const { return (end[0] - beg[0]) + (nseg > 1 ? end[1] - beg[1] : 0); }
 };
 
-__global__ void prep_positions_kernel(const uint16_t *off0, const uint16_t *off1, const uint16_t *off2,
-                                      const int32_t *cellid, float4 *pos, int64_t n) {
+constexpr int PP_WARPS_CTA = 8;
+constexpr int PP_CTA = PP_WARPS_CTA * 32;
+
+// Float offsets (and the cell id bits) for the PP kernel.
+__global__ void __launch_bounds__(PP_CTA) prep_positions_kernel(const uint16_t *off0, const uint16_t *off1,
+                                                                const uint16_t *off2, const int32_t *cellid,
+                                                                float4 *pos, int64_t n) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const float s = 1.0f / FIX;
     pos[i] = make_float4((float)off0[i] * s, (float)off1[i] * s, (float)off2[i] * s, __int_as_float(cellid[i]));
 }
 
-__device__ __forceinline__ void eval_pair(const PPParams &P, float rx, float ry, float rz, float r2, float &fx,
-                                          float &fy, float &fz, float &kx, float &ky, float &kz) {
-    const float g = P.coef * pp_over_r(r2, P.inv_bpp, P.inv_bcut);
-    kahan_add(fx, kx, g * rx);
-    kahan_add(fy, ky, g * ry);
-    kahan_add(fz, kz, g * rz);
-}
+// Compensated sum of three components: terms are added plainly into a block
+// partial (a tile or a row of candidates), and each block partial is added to
+// the running total with Kahan compensation.
+struct Sum3 {
+    float x = 0.f, y = 0.f, z = 0.f, cx = 0.f, cy = 0.f, cz = 0.f;
+    __device__ __forceinline__ void add_block(float bx, float by, float bz) {
+        kahan_add(x, cx, bx);
+        kahan_add(y, cy, by);
+        kahan_add(z, cz, bz);
+    }
+};
 
-__global__ void __launch_bounds__(256) pp_kernel(PPParams P) {
-    __shared__ float4 wtile[8][32];
+__global__ void __launch_bounds__(PP_CTA) pp_kernel(PPParams P) {
+    __shared__ float tx[PP_WARPS_CTA][32], ty[PP_WARPS_CTA][32], tz[PP_WARPS_CTA][32];
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int lane = threadIdx.x & 31;
-    float4 *tile = wtile[threadIdx.x >> 5];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    float *sx = tx[wib], *sy = ty[wib], *sz = tz[wib];
     const bool has = i < P.N;
     const int n = P.n_ios;
-    float4 me = has ? P.pos[i] : make_float4(0.f, 0.f, 0.f, 0.f);
-    int c = has ? __float_as_int(me.w) : -1;
+    const float4 me0 = has ? P.pos[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+    int c = has ? __float_as_int(me0.w) : -1;
     const int c0 = __shfl_sync(0xffffffffu, c, 0);
     if (!has) c = c0;
     const bool uniform = __all_sync(0xffffffffu, c == c0);
     const int cx = c % n, cy = (c / n) % n, cz = c / (n * n);
-    float fx = 0.f, fy = 0.f, fz = 0.f, kx = 0.f, ky = 0.f, kz = 0.f;
+    Sum3 a;
     unsigned long long pairs = 0, cands = 0;
     if (uniform) {
-        // shared neighbourhood: sources staged 32 at a time, frame = 3x3x3 cells
-        me.x += 1.0f; me.y += 1.0f; me.z += 1.0f;
+        // the warp's targets share their 27 neighbour cells: stage 32 sources at a
+        // time (3x3x3-cell frame, padded with far-away points), test all 32 into a
+        // mask, evaluate the set bits
+        const float mx = me0.x + 1.0f, my = me0.y + 1.0f, mz = me0.z + 1.0f;
         for (int dz = -1; dz <= 1; ++dz)
             for (int dy = -1; dy <= 1; ++dy) {
                 const int64_t r = ((int64_t)wrap(cz + dz, n) * n + wrap(cy + dy, n)) * n;
                 const RowRanges rr(P, r, cx, n);
                 if (has) cands += rr.size();
                 for (int sgi = 0; sgi < rr.nseg; ++sgi) {
-                    for (int t0 = rr.beg[sgi]; t0 < rr.end[sgi]; t0 += 32) {
-                        const int m = min(32, rr.end[sgi] - t0);
-                        if (lane < m) {
-                            const int j = t0 + lane;
+                    const int beg = sgi ? rr.beg[1] : rr.beg[0], end = sgi ? rr.end[1] : rr.end[0];
+                    const int b1 = sgi ? rr.b1[1] : rr.b1[0], b2 = sgi ? rr.b2[1] : rr.b2[0];
+                    const int base = (sgi ? rr.base[1] : rr.base[0]) + 1;
+                    for (int t0 = beg; t0 < end; t0 += 32) {
+                        const int j = t0 + lane;
+                        if (j < end) {
                             const float4 q = __ldg(&P.pos[j]);
-                            const float dx = (float)(rr.base[sgi] + 1 + (j >= rr.b1[sgi]) + (j >= rr.b2[sgi]));
-                            tile[lane] = make_float4(q.x + dx, q.y + (float)(dy + 1), q.z + (float)(dz + 1), 0.f);
+                            sx[lane] = q.x + (float)(base + (j >= b1) + (j >= b2));
+                            sy[lane] = q.y + (float)(dy + 1);
+                            sz[lane] = q.z + (float)(dz + 1);
+                        } else {
+                            sx[lane] = 1.0e18f;
+                            sy[lane] = 1.0e18f;
+                            sz[lane] = 1.0e18f;
                         }
                         __syncwarp();
                         unsigned mask = 0u;
-                        for (int k = 0; k < m; ++k) {
-                            const float4 s = tile[k];
-                            const float rx = s.x - me.x, ry = s.y - me.y, rz = s.z - me.z;
+#pragma unroll
+                        for (int k = 0; k < 32; ++k) {
+                            const float rx = sx[k] - mx, ry = sy[k] - my, rz = sz[k] - mz;
                             const float r2 = rx * rx + ry * ry + rz * rz;
                             mask |= (r2 < P.bcut2 && r2 > 0.0f) ? (1u << k) : 0u;
                         }
                         if (!has) mask = 0u;
                         pairs += __popc(mask);
+                        float px = 0.f, py = 0.f, pz = 0.f;
                         while (mask) {
                             const int k = __ffs(mask) - 1;
                             mask &= mask - 1u;
-                            const float4 s = tile[k];
-                            const float rx = s.x - me.x, ry = s.y - me.y, rz = s.z - me.z;
-                            eval_pair(P, rx, ry, rz, rx * rx + ry * ry + rz * rz, fx, fy, fz, kx, ky, kz);
+                            const float rx = sx[k] - mx, ry = sy[k] - my, rz = sz[k] - mz;
+                            const float g = P.coef * pp_over_r(rx * rx + ry * ry + rz * rz, P.inv_bpp, P.inv_bcut);
+                            px += g * rx;
+                            py += g * ry;
+                            pz += g * rz;
                         }
+                        a.add_block(px, py, pz);
                         __syncwarp();
                     }
                 }
@@ -241,37 +255,32 @@ __global__ void __launch_bounds__(256) pp_kernel(PPParams P) {
                 const RowRanges rr(P, r, cx, n);
                 cands += rr.size();
                 const float fdy = (float)dy, fdz = (float)dz;
+                float px = 0.f, py = 0.f, pz = 0.f;
                 for (int sgi = 0; sgi < rr.nseg; ++sgi) {
                     for (int j = rr.beg[sgi]; j < rr.end[sgi]; ++j) {
                         const float4 q = __ldg(&P.pos[j]);
                         const float fdx = (float)(rr.base[sgi] + (j >= rr.b1[sgi]) + (j >= rr.b2[sgi]));
-                        const float rx = (fdx + q.x) - me.x;
-                        const float ry = (fdy + q.y) - me.y;
-                        const float rz = (fdz + q.z) - me.z;
+                        const float rx = (fdx + q.x) - me0.x;
+                        const float ry = (fdy + q.y) - me0.y;
+                        const float rz = (fdz + q.z) - me0.z;
                         const float r2 = rx * rx + ry * ry + rz * rz;
                         if (r2 < P.bcut2 && r2 > 0.0f) {
-                            eval_pair(P, rx, ry, rz, r2, fx, fy, fz, kx, ky, kz);
+                            const float g = P.coef * pp_over_r(r2, P.inv_bpp, P.inv_bcut);
+                            px += g * rx;
+                            py += g * ry;
+                            pz += g * rz;
                             ++pairs;
                         }
                     }
                 }
+                a.add_block(px, py, pz);
             }
     }
-    if (has) finish(P, i, fx - kx, fy - ky, fz - kz);
+    if (has) finish(P, i, a.x - a.cx, a.y - a.cy, a.z - a.cz);
     add_stats(P.stats, pairs, cands);
 }
 
 }  // namespace
-
-cudaError_t launch_prep_positions(cube2_ctx *ctx, const cube2_particles *p) {
-    const int64_t blocks = (ctx->N + 255) / 256;
-    if (blocks == 0) return cudaSuccess;
-    ProfScope prof(ctx, P_PREP, 0);
-    prep_positions_kernel<<<(unsigned)blocks, 256, 0, ctx->stream>>>(p->off[0], p->off[1], p->off[2], ctx->cellid,
-                                                                    ctx->pos4, ctx->N);
-    ctx->launches++;
-    return cudaGetLastError();
-}
 
 cudaError_t launch_pp(cube2_ctx *ctx, const cube2_particles *p, int accumulate, float kick) {
     PPParams P{};
@@ -292,10 +301,17 @@ cudaError_t launch_pp(cube2_ctx *ctx, const cube2_particles *p, int accumulate, 
     P.kick = kick;
     P.status = ctx->dev_status;
     if (ctx->N == 0) return cudaSuccess;
+    const int nblocks = (int)((ctx->N + PP_CTA - 1) / PP_CTA);
+    {
+        ProfScope prof(ctx, P_PREP, 0);
+        prep_positions_kernel<<<(unsigned)nblocks, PP_CTA, 0, ctx->stream>>>(p->off[0], p->off[1], p->off[2],
+                                                                           ctx->cellid, ctx->pos4, ctx->N);
+    }
     {
         ProfScope prof(ctx, P_PP, 0);
-        pp_kernel<<<(unsigned)((ctx->N + 255) / 256), 256, 0, ctx->stream>>>(P);
+        pp_kernel<<<(unsigned)nblocks, PP_CTA, 0, ctx->stream>>>(P);
     }
+    ctx->launches += 2;
     ctx->launches += 1;
     return cudaGetLastError();
 }
