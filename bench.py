@@ -20,9 +20,10 @@ Also reported on the same JSON line:
   clocks        nvidia-smi samples taken during the timed region
 
 --impl reference times the FP64 oracle alone (this project's reference arm).
-With torchrun (N > 1) every rank runs an independent replica of the box
-(the single box does not shard; replicas only) and the slowest rank's time
-sets the aggregate.
+With torchrun (N > 1) every rank runs an independent realisation of the box
+(another seed of the same recipe; the single box does not shard, so there
+are replicas only and no data-path collective); the units all ranks
+processed over the slowest rank's time set the aggregate.
 """
 from __future__ import annotations
 
@@ -73,6 +74,48 @@ def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return world, rank, local
+
+
+class Ranks:
+    """The job's ranks as bench.py uses them: reductions of per-rank scalars
+    (the slowest rank's time, the units all ranks processed) and barriers.
+    ``dist`` is torch.distributed with an initialised group, or None for one
+    rank; ``device`` is where the reduction tensors live ("cuda" under NCCL,
+    "cpu" under gloo)."""
+
+    def __init__(self, dist=None, device="cpu"):
+        self.dist, self.device = dist, device
+        self.world = dist.get_world_size() if dist else 1
+        self.rank = dist.get_rank() if dist else 0
+
+    def barrier(self):
+        if self.dist:
+            self.dist.barrier()
+
+    def _reduce(self, x, op):
+        if not self.dist:
+            return float(x)
+        import torch
+        t = torch.tensor([float(x)], dtype=torch.float64, device=self.device)
+        self.dist.all_reduce(t, op=op)
+        return float(t.item())
+
+    def max(self, x):
+        return self._reduce(x, self.dist.ReduceOp.MAX if self.dist else None)
+
+    def sum(self, x):
+        return self._reduce(x, self.dist.ReduceOp.SUM if self.dist else None)
+
+
+def replica_workload(w, rank):
+    """The box rank ``rank`` simulates: the workload itself on rank 0, an
+    independent realisation (another seed of the same recipe) elsewhere."""
+    return w if rank == 0 else w.with_(seed=w.seed + 7919 * rank)
+
+
+def job_throughput(units_all_ranks, seconds_slowest):
+    """Whole-job particle-steps/s: units processed by all ranks / slowest rank."""
+    return units_all_ranks / seconds_slowest
 
 
 # ----------------------------------------------------------------- clocks
@@ -296,11 +339,16 @@ def main():
     else:
         dist = None
         torch.cuda.set_device(0)
+    ranks = Ranks(dist, "cuda")
     from paper_2512_12629_gb300 import build as pkg_build
+    if rank == 0:
+        pkg_build.build()
+    ranks.barrier()
     pkg_build.build()
     from inputs.zeldovich import zeldovich_ios
     from paper_2512_12629_gb300 import cube2
 
+    w = replica_workload(w, rank)
     st = zeldovich_ios(w)
     n_part = int(st["count"].sum())
     ctx = cube2.init_mesh(cube2.make_config(w, n_particles=n_part))
@@ -332,8 +380,7 @@ def main():
     launches0 = ctx.launch_count()
     clocks = ClockSampler(bus_id_of(torch.cuda.current_device()))
     clocks.start()
-    if dist:
-        dist.barrier()
+    ranks.barrier()
     torch.cuda.synchronize()
     ev0.record(stream)
     for k in range(args.steps):
@@ -343,8 +390,7 @@ def main():
         ctx.kdk_step(p, a[i], a[i + 1])
     ev1.record(stream)
     torch.cuda.synchronize()
-    if dist:
-        dist.barrier()
+    ranks.barrier()
     clk = clocks.stop()
     launches = ctx.launch_count() - launches0
     ms = ev0.elapsed_time(ev1)
@@ -352,12 +398,9 @@ def main():
     ctx.profile(0)
     ctx.check()
     pp_pairs, pp_cands = ctx.pp_stats()
-    ms_max = ms
-    if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_max = float(t.item())
-    value = n_part * args.steps * world / (ms_max / 1e3)
+    ms_max = ranks.max(ms)
+    units = ranks.sum(n_part * args.steps)
+    value = job_throughput(units, ms_max / 1e3)
 
     # dominant kernel class -> roofline (PP counts both of its kernels)
     peak, peak_kind = peaks()
@@ -406,8 +449,7 @@ def main():
         ctx.kdk_step_host(pe, host, a[0], a[1])                # warm
         host = cube2.IOSState(*(x.cpu().pin_memory() for x in (p0.off, p0.count, p0.start, p0.vel, p0.acc)))
         torch.cuda.synchronize()
-        if dist:
-            dist.barrier()
+        ranks.barrier()
         t0 = time.perf_counter()
         for k in range(args.steps):
             i = k % S
@@ -416,12 +458,8 @@ def main():
                                 (p0.off, p0.count, p0.start, p0.vel, p0.acc)):
                     x.copy_(y)
             ctx.kdk_step_host(pe, host, a[i], a[i + 1])
-        el = time.perf_counter() - t0
-        if dist:
-            t = torch.tensor([el], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            el = float(t.item())
-        e2e = {"value": n_part * args.steps * world / el, "unit": UNIT,
+        el = ranks.max(time.perf_counter() - t0)
+        e2e = {"value": job_throughput(units, el), "unit": UNIT,
                "h2d_bytes_per_step": bytes_step, "d2h_bytes_per_step": bytes_step,
                "api": "cube2_kdk_step_host (pinned host state, H2D + step + D2H each step)"}
 

@@ -162,3 +162,44 @@ def green(n, b_soft, b_trunc=None, alias=2, order=2):
     ok = d2 > 0
     out[ok] = num[ok] / (d2[ok] * den[ok] ** 2)
     return out
+
+
+def green_at(n, modes, b_soft, b_trunc=None, alias=2, order=2):
+    """Eq. (Gk) at selected modes of an n^3 mesh, without the full table.
+
+    modes: int array (K, 3) of (m_x, m_y, m_z) in rfftn index ranges
+    (m_x in [0, n/2], m_y, m_z in [0, n)).  Same arithmetic as ``green``."""
+    modes = np.asarray(modes, dtype=np.int64)
+    mx = modes[:, 0]
+    my = np.where(modes[:, 1] <= n // 2, modes[:, 1], modes[:, 1] - n)
+    mz = np.where(modes[:, 2] <= n // 2, modes[:, 2], modes[:, 2] - n)
+    # numpy's fftfreq puts the Nyquist index n/2 at -n/2 on the y and z axes
+    my = np.where(modes[:, 1] == n // 2, -(n // 2), my)
+    mz = np.where(modes[:, 2] == n // 2, -(n // 2), mz)
+    kx, ky, kz = (TWO_PI / n) * mx, (TWO_PI / n) * my, (TWO_PI / n) * mz
+    dx, dy, dz = fd_transform_modes(mx, n), fd_transform_modes(my, n), fd_transform_modes(mz, n)
+    d2 = dx * dx + dy * dy + dz * dz
+    num = np.zeros(len(modes))
+    den = np.zeros(len(modes))
+    images = range(-alias, alias + 1)
+    for nz in images:
+        knz = kz + TWO_PI * nz
+        wz = assignment_transform(knz, order) ** 2
+        for ny in images:
+            kny = ky + TWO_PI * ny
+            wy = assignment_transform(kny, order) ** 2
+            for nx in images:
+                knx = kx + TWO_PI * nx
+                wx = assignment_transform(knx, order) ** 2
+                w2 = wx * wy * wz
+                kn2 = knx * knx + kny * kny + knz * knz
+                safe = np.where(kn2 > 0, kn2, 1.0)
+                kn = np.sqrt(safe)
+                ds2 = profile_transform(kn, b_soft) ** 2 - profile_transform(kn, b_trunc) ** 2
+                dr = -(dx * knx + dy * kny + dz * knz) * ds2 / safe
+                num += np.where(kn2 > 0, w2 * dr, 0.0)
+                den += w2
+    out = np.zeros(len(modes))
+    ok = d2 > 0
+    out[ok] = num[ok] / (d2[ok] * den[ok] ** 2)
+    return out

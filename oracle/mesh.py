@@ -207,3 +207,40 @@ def pm_force(off, count, w, greens=None):
         f, _ = pm_force_level(off, count, w.n_ios, n, h, g)
         total = total + f
     return total
+
+
+def deposit_u64_at(off, count, start, n_ios, n_mesh, cells):
+    """Integer CIC accumulator at selected mesh cells only (flat ids, x fastest).
+
+    For each selected cell, gathers the particles of every IOS cell near it
+    (a window that holds all particles whose CIC cloud can reach the cell)
+    and sums their exact corner weights that land on it, as ``deposit_u64``."""
+    s = level_shift(n_ios, n_mesh)
+    cells = np.asarray(cells, dtype=np.int64)
+    out = np.zeros(len(cells), dtype=np.uint64)
+    for k, cell in enumerate(cells):
+        js = (int(cell % n_mesh), int((cell // n_mesh) % n_mesh), int(cell // (n_mesh * n_mesh)))
+        # a particle of IOS cell c sits at mesh coordinates [c, c + 1) * 2^-s and
+        # touches the cells floor(x - 1/2) and floor(x - 1/2) + 1
+        if s >= 0:
+            win = [range(((j - 2) << s), ((j + 2) << s) + 1) for j in js]
+        else:
+            win = [range((j - 2) >> (-s), ((j + 2) >> (-s)) + 1) for j in js]
+        seen = set()
+        total = 0
+        for iz in win[2]:
+            for iy in win[1]:
+                for ix in win[0]:
+                    c = ((iz % n_ios) * n_ios + iy % n_ios) * n_ios + ix % n_ios
+                    if c in seen:
+                        continue
+                    seen.add(c)
+                    a, b = int(start[c]), int(start[c]) + int(count[c])
+                    if b == a:
+                        continue
+                    cxyz = np.array([c % n_ios, (c // n_ios) % n_ios, c // (n_ios * n_ios)], dtype=np.int64)
+                    X = cxyz[:, None] * FIX + off[:, a:b].astype(np.int64)
+                    for idx, wgt in _corners(X, n_mesh, s):
+                        total += int(wgt[idx == cell].sum())
+        out[k] = np.uint64(total % (1 << 64))
+    return out

@@ -98,4 +98,40 @@ def pp_force_brute(pos, box, b_pp, b_cut, n_particles=None):
     return (d * mag[None]).sum(axis=2)
 
 
-__all__ = ["pp_force", "pp_force_brute", "cell_coords"]
+def pp_force_at(off, count, start, n_ios, box, b_pp, b_cut, targets, n_particles=None):
+    """PP force (3, K) on selected particles only, by the same rule as ``pp_force``:
+    each target's 27 neighbour cells are gathered directly."""
+    n_part = int(count.sum()) if n_particles is None else n_particles
+    s_ios = box / n_ios
+    vp = box ** 3 / n_part
+    targets = np.asarray(targets, dtype=np.int64)
+    starts = start.astype(np.int64)
+    ends = starts + count.astype(np.int64)
+    cell_of = np.searchsorted(ends, targets, side="right")
+    out = np.zeros((3, len(targets)))
+    for k, (i, c) in enumerate(zip(targets, cell_of)):
+        cc = (c % n_ios, (c // n_ios) % n_ios, c // (n_ios * n_ios))
+        oi = off[:, i].astype(np.int64)
+        for oz in (-1, 0, 1):
+            for oy in (-1, 0, 1):
+                for ox in (-1, 0, 1):
+                    nb = ((((cc[2] + oz) % n_ios) * n_ios + (cc[1] + oy) % n_ios) * n_ios
+                          + (cc[0] + ox) % n_ios)
+                    j = np.arange(starts[nb], ends[nb])
+                    j = j[j != i]
+                    if j.size == 0:
+                        continue
+                    d = np.empty((3, j.size))
+                    for ax, o in enumerate((ox, oy, oz)):
+                        d[ax] = (o * FIX + off[ax, j].astype(np.int64) - oi[ax]) * (s_ios / FIX)
+                    r = np.sqrt((d * d).sum(axis=0))
+                    m = (r > 0) & (r < b_cut)
+                    if not m.any():
+                        continue
+                    d, r = d[:, m], r[m]
+                    mag = vp * pp_reference(r, b_pp, b_cut) / (4.0 * math.pi * r)
+                    out[:, k] += (d * mag).sum(axis=1)
+    return out
+
+
+__all__ = ["pp_force", "pp_force_at", "pp_force_brute", "cell_coords"]

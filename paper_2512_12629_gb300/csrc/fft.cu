@@ -252,7 +252,7 @@ __global__ void __launch_bounds__(Tile<N>::T) fft_y(float2 *__restrict__ data, i
 
 // ------------------------------------------------------------ Z (+ Green)
 template <int N, bool GREEN>
-__global__ void __launch_bounds__(Tile<N>::T) fft_z(float2 *__restrict__ data, const float *__restrict__ green,
+__global__ void __launch_bounds__(Tile<N>::T, (Tile<N>::T >= 512 ? 2 : 1)) fft_z(float2 *__restrict__ data, const float *__restrict__ green,
                                                    int kxp, const float2 *__restrict__ tw) {
     constexpr int L = Tile<N>::L, LP = Tile<N>::LPY, T = Tile<N>::T;
     extern __shared__ __align__(16) float2 S[];

@@ -61,6 +61,8 @@ def test_pp_cell_list_matches_brute_force_and_is_antisymmetric():
     sub = P.pp_force(st["off"], st["count"], st["start"], w.n_ios, w.box, b_pp, b_cut,
                      targets=[3, 77, 500])
     assert np.array_equal(sub, f[:, [3, 77, 500]])
+    at = P.pp_force_at(st["off"], st["count"], st["start"], w.n_ios, w.box, b_pp, b_cut, [0, 3, 77, 500, 599])
+    assert np.allclose(at, f[:, [0, 3, 77, 500, 599]], rtol=1e-12, atol=1e-12 * np.abs(f).max())
 
 
 def _ewald_errors(w, n, seed):

@@ -129,3 +129,21 @@ def test_solve_recovers_poisson_for_single_mode():
     # phi = G(k) rho exactly for a single mode
     assert np.allclose(phi, g[0, 0, 1] * rho, atol=1e-12)
     assert abs(g[0, 0, 1] * k * k + 1) < 0.25 * k * k    # O(k^2) FD/assignment terms
+
+
+@pytest.mark.parametrize("n_ios,n_mesh", [(8, 16), (8, 4), (8, 8), (4, 16)])
+def test_point_deposit_equals_full_deposit(n_ios, n_mesh):
+    st = random_ios(700, n_ios, 16.0, seed=8, clustered=0.5)
+    acc = M.deposit_u64(st["off"], st["count"], n_ios, n_mesh).ravel()
+    rng = np.random.default_rng(2)
+    cells = rng.integers(0, n_mesh ** 3, 60)
+    at = M.deposit_u64_at(st["off"], st["count"], st["start"], n_ios, n_mesh, cells)
+    assert np.array_equal(at, acc[cells])
+
+
+def test_point_green_equals_full_table():
+    g = K.green(24, 2.0, 9.0)
+    rng = np.random.default_rng(4)
+    modes = np.stack([rng.integers(0, 13, 80), rng.integers(0, 24, 80), rng.integers(0, 24, 80)], 1)
+    modes[:4] = [[12, 12, 12], [0, 0, 0], [12, 0, 5], [3, 12, 12]]
+    assert np.array_equal(K.green_at(24, modes, 2.0, 9.0), g[modes[:, 2], modes[:, 1], modes[:, 0]])
