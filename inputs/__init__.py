@@ -2,4 +2,4 @@
 
 Holds workload records and the Zel'dovich initial-condition generator only;
 none of the force method's arithmetic lives here."""
-from .workloads import C1, C2, C2_SMALL, C3, C5, WORKLOADS, Level, Workload  # noqa: F401
+from .workloads import C1, C2, C2_MID, C2_SMALL, C3, C5, WORKLOADS, Level, Workload  # noqa: F401

@@ -84,6 +84,12 @@ C2 = Workload(
 C2_SMALL = C2.with_(name="pm2-64c-32x128mesh", n_p=64, box=64.0, n_ios=64,
                     levels=(Level(32, 3.5), Level(128, 2.0)), seed=12)
 
+# Same recipe as C2 at 27/64 of the volume (192^3 particles, 96^3 + 384^3
+# meshes, the same IOS/mesh ratios): every array larger than L2, a working
+# set of about 1.5 GB; the size used for multi-pass profiler captures.
+C2_MID = C2.with_(name="pm2-192c-96x384mesh", n_p=192, box=192.0, n_ios=192,
+                  levels=(Level(96, 3.5), Level(384, 2.0)), seed=22)
+
 # Differentiation workload: 128^3 particles, 128 Mpc/h, one 256^3 level,
 # 10 KDK steps z = 9 -> 0.
 C3 = Workload(
@@ -100,4 +106,4 @@ C5 = Workload(
     z_init=49.0, z_final=0.0, n_steps=1, seed=5, displace_to_a=1.0,
 )
 
-WORKLOADS = {w.name: w for w in (C1, C2, C2_SMALL, C3, C5)}
+WORKLOADS = {w.name: w for w in (C1, C2, C2_SMALL, C2_MID, C3, C5)}

@@ -312,7 +312,6 @@ cudaError_t launch_pp(cube2_ctx *ctx, const cube2_particles *p, int accumulate, 
         pp_kernel<<<(unsigned)nblocks, PP_CTA, 0, ctx->stream>>>(P);
     }
     ctx->launches += 2;
-    ctx->launches += 1;
     return cudaGetLastError();
 }
 
