@@ -2,9 +2,8 @@
 //   F_i += V_p / (4 pi) (R(r, b_pp) - R(r, b_range)) (x_j - x_i) / r,   0 < r < b_range,
 // with R(r, b) of Eq. (refforce).  The IOS order is the cell list (Sec. 2.3): the
 // IOS cell is at least b_range wide, so the 27 cells around a particle's cell
-// hold all its partners.  The three cells of one (dz, dy) row are adjacent in
-// memory, so the 27 cells are walked as 9 contiguous particle ranges (two where
-// the row wraps around the box).
+// hold all its partners.  The cells of one (dz, dy) row are adjacent in memory,
+// so a run of cells along x is one contiguous particle range.
 //
 // Arithmetic is carried out in IOS-cell units.  A particle's in-cell offset
 // off/2^16 is exact in FP32 (prep kernel, once per force evaluation) and so is
@@ -12,15 +11,18 @@
 // bitwise antisymmetric.  Each ordered pair is evaluated from both sides (gather
 // form, no atomics, deterministic).
 //
-// One thread per target, in particle (= cell) order.  Where
-// all 32 targets of a warp sit in one cell (the clustered regime) they share
-// their 27 neighbour cells: the warp stages 32 sources at a time in a per-warp
-// shared-memory tile, each lane tests all 32 into an in-range bit mask and
-// evaluates only the set bits.  Warps spanning several cells walk each lane's
-// own ranges.  Per-particle sums are compensated: plain FP32 partials per tile
-// (or per row of cells) are added to the running total with Kahan's scheme.
-// The path a warp takes depends only on the cell counts and every sum has a
-// fixed order, so results are bitwise reproducible.
+// One thread per target, in particle (= cell) order.  A warp whose 32 targets
+// lie in one row of cells, at most PP_WMAX + 1 cells wide (every dense region),
+// shares one source stream: the particles of cells xa-1 .. xb+1 in the 9 rows
+// around it.  It stages 64 sources at a time in shared memory; each lane tests
+// all 64 (sign of r^2 - b_cut^2 shifted into a bit mask, 8 instructions per
+// candidate) and evaluates only the set bits with a branch-free far-pair
+// formula; pairs closer than b_pp take a separate, rarely entered loop.
+// Other warps (sparse regions) walk each lane's own 27 cells.
+// Per-particle sums are compensated: plain FP32 partials per batch are added to
+// the running total with Kahan's scheme.  The path a warp takes depends only
+// on the cell layout and every sum has a fixed order, so results are bitwise
+// reproducible.
 #include "common.cuh"
 
 namespace cube2 {
@@ -34,7 +36,7 @@ struct PPParams {
     unsigned long long *stats;  // [2]: in-range ordered pairs, candidates
     int64_t N;
     int n_ios, accumulate;
-    float inv_bpp, inv_bcut, bcut2;   // IOS-cell units
+    float inv_bpp, inv_bcut, bcut2, bpp2;   // IOS-cell units
     float coef;                       // V_p / (4 pi s_ios^2)
     float kick;                       // 0: no kick; else v += kick * acc after the sum
     int *status;
@@ -49,28 +51,6 @@ __device__ __forceinline__ float ref_force_scaled(float u) {
     // 3/(35 u^2) - 32/5 + 256/5 u - 96 u^2 + 256/5 u^3 + 32 u^4 - 1536/35 u^5 + 64/5 u^6
     const float poly = -32.0f / 5.0f + u * (256.0f / 5.0f + u * (-96.0f + u * (256.0f / 5.0f + u * (32.0f + u * (-1536.0f / 35.0f + 64.0f / 5.0f * u)))));
     return 3.0f / (35.0f * u * u) + poly;
-}
-
-// R_PP(r) / r for 0 < r < b_cut (Eq. PP), IOS-cell units.  Where r >= b_pp the
-// first term is 1/r^2 and the difference is written as m(u)/r^2 with
-// u = r/b_cut: for u >= 1/2 the outer-shell branch of Eq. (refforce) gives
-// r^2 (1/r^2 - R) = v^5 (192/5 - 416/5 v + 2048/35 v^2 - 64/5 v^3), v = 1 - u
-// (an exact polynomial shift, free of cancellation near the cutoff); below
-// u = 1/2 the inner branch gives 1 - 64/5 u^3 + 256/5 u^5 - 32 u^6
-// - 1536/35 u^7 + 192/5 u^8.
-__device__ __forceinline__ float pp_over_r(float r2, float inv_bpp, float inv_bcut) {
-    const float rinv = rsqrtf(r2);
-    const float r = r2 * rinv;
-    const float u = r * inv_bcut;
-    const float v = 1.0f - u;
-    const float v2 = v * v;
-    const float m_out = v2 * v2 * v * (192.0f / 5.0f + v * (-416.0f / 5.0f + v * (2048.0f / 35.0f - 64.0f / 5.0f * v)));
-    const float u2 = u * u;
-    const float m_in = 1.0f + u2 * u * (-64.0f / 5.0f + u2 * (256.0f / 5.0f + u * (-32.0f + u * (-1536.0f / 35.0f + 192.0f / 5.0f * u))));
-    float val = (u >= 0.5f ? m_out : m_in) * rinv * rinv;
-    if (r * inv_bpp < 1.0f)   // closer than b_pp: both terms are softened (rare)
-        val = ref_force_scaled(r * inv_bpp) * inv_bpp * inv_bpp - ref_force_scaled(r * inv_bcut) * inv_bcut * inv_bcut;
-    return val * rinv;
 }
 
 __device__ __forceinline__ void kahan_add(float &sum, float &comp, float v) {
@@ -182,100 +162,235 @@ struct Sum3 {
     }
 };
 
-__global__ void __launch_bounds__(PP_CTA) pp_kernel(PPParams P) {
-    __shared__ float tx[PP_WARPS_CTA][32], ty[PP_WARPS_CTA][32], tz[PP_WARPS_CTA][32];
+// Far-pair factor R_PP(r)/r for b_pp <= r < b_cut (Eq. PP), IOS-cell units,
+// branch-free.  Where r >= b_pp the first term of R_PP is 1/r^2 and the
+// difference is written as m(u)/r^2 with u = r/b_cut: for u >= 1/2 the
+// outer-shell branch of Eq. (refforce) gives r^2 (1/r^2 - R) =
+// v^5 (192/5 - 416/5 v + 2048/35 v^2 - 64/5 v^3), v = 1 - u (an exact
+// polynomial shift, free of cancellation near the cutoff); below u = 1/2 the
+// inner branch gives 1 - 64/5 u^3 + 256/5 u^5 - 32 u^6 - 1536/35 u^7 + 192/5 u^8.
+// Pairs closer than b_pp (and r = 0) get 0 here; close_pair() handles them.
+__device__ __forceinline__ float far_pair(float r2, float inv_bcut, float bpp2) {
+    const float rinv = rsqrtf(r2);
+    const float u = r2 * rinv * inv_bcut;
+    const float v = 1.0f - u;
+    const float v2 = v * v;
+    const float m_out = v2 * v2 * v * (192.0f / 5.0f + v * (-416.0f / 5.0f + v * (2048.0f / 35.0f - 64.0f / 5.0f * v)));
+    const float u2 = u * u;
+    const float m_in = 1.0f + u2 * u * (-64.0f / 5.0f + u2 * (256.0f / 5.0f + u * (-32.0f + u * (-1536.0f / 35.0f + 192.0f / 5.0f * u))));
+    const float g = (u >= 0.5f ? m_out : m_in) * (rinv * rinv * rinv);
+    return r2 >= bpp2 ? g : 0.0f;
+}
+
+// R_PP(r)/r for 0 < r < b_pp: both terms of Eq. PP are softened.
+__device__ __forceinline__ float close_pair(float r2, float inv_bpp, float inv_bcut) {
+    const float rinv = rsqrtf(r2);
+    const float r = r2 * rinv;
+    return (ref_force_scaled(r * inv_bpp) * inv_bpp * inv_bpp - ref_force_scaled(r * inv_bcut) * inv_bcut * inv_bcut) *
+           rinv;
+}
+
+// Sources of a warp whose 32 targets lie in one row of cells, x in [xa, xb]:
+// for each of the 9 (dz, dy) rows, the cells xa-1 .. xb+1 as a main range and
+// at most one wrapped cell, flattened into one stream.  Stream position p of
+// segment s is particle beg[s] + p - cum[s]; its x coordinate in the warp's
+// frame (cell xa at 0) is (cell id - adj[s]) + off_x.
+constexpr int PP_SEGS = 18;
+struct WarpSegs {
+    int beg[PP_SEGS];
+    int adj[PP_SEGS];
+    int cum[PP_SEGS + 2];
+};
+
+// Union width limit (cells beyond the first) for the shared-stream path.
+#ifndef PP_WMAX
+#define PP_WMAX 8
+#endif
+
+struct PPShared {
+    float4 buf[PP_WARPS_CTA][64];             // staged sources of the union path
+    WarpSegs seg[PP_WARPS_CTA];
+};
+
+// Stage stream position p (far-away point past the end).  s: the lane's
+// running segment index (positions a lane stages only increase).
+__device__ __forceinline__ float4 stage_source(const PPParams &P, const WarpSegs &W, int p, int &s) {
+    if (p >= W.cum[PP_SEGS]) return make_float4(1.0e18f, 1.0e18f, 1.0e18f, 0.0f);
+    while (p >= W.cum[s + 1]) ++s;
+    const float4 q = __ldg(&P.pos[W.beg[s] + (p - W.cum[s])]);
+    const int row = s >> 1;   // (dz + 1) * 3 + (dy + 1)
+    return make_float4((float)(__float_as_int(q.w) - W.adj[s]) + q.x, q.y + (float)(row % 3), q.z + (float)(row / 3),
+                       0.0f);
+}
+
+// Candidate test of 32 staged sources: bit (31 - k) set where source k is
+// closer than b_cut (sign of r^2 - b_cut^2, shifted in).
+__device__ __forceinline__ unsigned test32(const float4 *S, float mx, float my, float mz, float bcut2) {
+    unsigned m = 0u;
+#pragma unroll
+    for (int k = 0; k < 32; ++k) {
+        const float4 q = S[k];
+        const float rx = q.x - mx, ry = q.y - my, rz = q.z - mz;
+        const float d = fmaf(rx, rx, fmaf(ry, ry, fmaf(rz, rz, -bcut2)));
+        m = __funnelshift_l(__float_as_uint(d), m, 1);
+    }
+    return m;
+}
+
+__device__ void union_path(const PPParams &P, WarpSegs &W, float4 *S, int64_t i, bool has, int c0, int xa, int xb,
+                           float4 me, Sum3 &a, unsigned long long &pairs, unsigned long long &cands) {
+    const int lane = threadIdx.x & 31;
+    const int n = P.n_ios;
+    const int cz = c0 / (n * n), cy = (c0 / n) % n;
+    // segment table: lane 2*row + which
+    int len = 0;
+    if (lane < PP_SEGS) {
+        const int row = lane >> 1, which = lane & 1;
+        const int dz = row / 3 - 1, dy = row % 3 - 1;
+        const int rb = (wrap(cz + dz, n) * n + wrap(cy + dy, n)) * n;
+        int beg = 0, adj = rb + xa;
+        if (which == 0) {
+            const int lo = xa > 0 ? xa - 1 : 0, hi = xb < n - 1 ? xb + 1 : n - 1;
+            beg = __ldg(&P.start[rb + lo]);
+            len = __ldg(&P.start[rb + hi]) + __ldg(&P.count[rb + hi]) - beg;
+        } else if (xa == 0) {
+            beg = __ldg(&P.start[rb + n - 1]);
+            len = __ldg(&P.count[rb + n - 1]);
+            adj += n;
+        } else if (xb == n - 1) {
+            beg = __ldg(&P.start[rb]);
+            len = __ldg(&P.count[rb]);
+            adj -= n;
+        }
+        W.beg[lane] = beg;
+        W.adj[lane] = adj;
+    }
+    int incl = len;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+    }
+    if (lane < PP_SEGS) W.cum[lane + 1] = incl;
+    if (lane == 0) W.cum[0] = 0;
+    if (lane == PP_SEGS) W.cum[PP_SEGS + 1] = 0x7fffffff;
+    __syncwarp();
+    const int total = W.cum[PP_SEGS];
+    // own particle's stream position (row (0, 0) main segment is s = 8)
+    const int pself = has ? W.cum[8] + (int)(i - W.beg[8]) : -1000;
+    const int cx = (has ? __float_as_int(me.w) : c0) % n;
+    const float mx = (float)(cx - xa) + me.x, my = me.y + 1.0f, mz = me.z + 1.0f;
+    if (has) cands += (unsigned long long)total;
+    const float bcut2 = P.bcut2, bpp2 = P.bpp2, ibc = P.inv_bcut, ibp = P.inv_bpp;
+    int sa = 0, sb = 0;
+    for (int b0 = 0; b0 < total; b0 += 64) {
+        S[lane] = stage_source(P, W, b0 + lane, sa);
+        S[32 + lane] = stage_source(P, W, b0 + 32 + lane, sb);
+        __syncwarp();
+        unsigned long long m = ((unsigned long long)test32(S, mx, my, mz, bcut2) << 32) |
+                               test32(S + 32, mx, my, mz, bcut2);
+        const int ts = pself - b0;
+        if (ts >= 0 && ts < 64) m &= ~(1ull << (63 - ts));
+        if (!has) m = 0ull;
+        pairs += __popcll(m);
+        const unsigned long long m0 = m;
+        float px = 0.f, py = 0.f, pz = 0.f;
+        bool close = false;
+        while (m) {
+            const int k = __clzll(m);
+            m ^= 1ull << (63 - k);
+            const float4 q = S[k];
+            const float rx = q.x - mx, ry = q.y - my, rz = q.z - mz;
+            const float r2 = rx * rx + ry * ry + rz * rz;
+            const float g = far_pair(r2, ibc, bpp2);
+            close |= r2 < bpp2;
+            px = fmaf(g, rx, px);
+            py = fmaf(g, ry, py);
+            pz = fmaf(g, rz, pz);
+        }
+        if (__any_sync(0xffffffffu, close)) {
+            m = close ? m0 : 0ull;
+            while (m) {
+                const int k = __clzll(m);
+                m ^= 1ull << (63 - k);
+                const float4 q = S[k];
+                const float rx = q.x - mx, ry = q.y - my, rz = q.z - mz;
+                const float r2 = rx * rx + ry * ry + rz * rz;
+                if (r2 < bpp2) {
+                    if (r2 > 0.0f) {
+                        const float g = close_pair(r2, ibp, ibc);
+                        px = fmaf(g, rx, px);
+                        py = fmaf(g, ry, py);
+                        pz = fmaf(g, rz, pz);
+                    } else {
+                        --pairs;   // coincident particles: no pair force
+                    }
+                }
+            }
+        }
+        a.add_block(P.coef * px, P.coef * py, P.coef * pz);
+        __syncwarp();
+    }
+}
+
+// Warps whose targets span several rows or a wide x range (sparse regions):
+// each lane walks its own 27 cells as 9 row ranges and evaluates the pairs in
+// range as it meets them.  Plain nested loops keep the loads pipelined.
+__device__ void lane_path(const PPParams &P, bool has, int c, float4 me, Sum3 &a,
+                                    unsigned long long &pairs, unsigned long long &cands) {
+    if (!has) return;
+    const int n = P.n_ios;
+    const int cx = c % n, cy = (c / n) % n, cz = c / (n * n);
+    const float bcut2 = P.bcut2, bpp2 = P.bpp2, ibc = P.inv_bcut, ibp = P.inv_bpp;
+    for (int dz = -1; dz <= 1; ++dz)
+        for (int dy = -1; dy <= 1; ++dy) {
+            const int64_t r = ((int64_t)wrap(cz + dz, n) * n + wrap(cy + dy, n)) * n;
+            const RowRanges rr(P, r, cx, n);
+            cands += rr.size();
+            const float fdy = (float)dy, fdz = (float)dz;
+            float px = 0.f, py = 0.f, pz = 0.f;
+            for (int sgi = 0; sgi < rr.nseg; ++sgi) {
+                for (int j = rr.beg[sgi]; j < rr.end[sgi]; ++j) {
+                    const float4 q = __ldg(&P.pos[j]);
+                    const float fdx = (float)(rr.base[sgi] + (j >= rr.b1[sgi]) + (j >= rr.b2[sgi]));
+                    const float rx = (fdx + q.x) - me.x;
+                    const float ry = (fdy + q.y) - me.y;
+                    const float rz = (fdz + q.z) - me.z;
+                    const float r2 = rx * rx + ry * ry + rz * rz;
+                    if (r2 < bcut2 && r2 > 0.0f) {
+                        const float g = r2 >= bpp2 ? far_pair(r2, ibc, bpp2) : close_pair(r2, ibp, ibc);
+                        px = fmaf(g, rx, px);
+                        py = fmaf(g, ry, py);
+                        pz = fmaf(g, rz, pz);
+                        ++pairs;
+                    }
+                }
+            }
+            a.add_block(P.coef * px, P.coef * py, P.coef * pz);
+        }
+}
+
+__global__ void __launch_bounds__(PP_CTA, 3) pp_kernel(PPParams P) {
+    __shared__ PPShared sh;
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    float *sx = tx[wib], *sy = ty[wib], *sz = tz[wib];
+    const int wib = threadIdx.x >> 5;
     const bool has = i < P.N;
     const int n = P.n_ios;
-    const float4 me0 = has ? P.pos[i] : make_float4(0.f, 0.f, 0.f, 0.f);
-    int c = has ? __float_as_int(me0.w) : -1;
+    const float4 me = has ? P.pos[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+    int c = has ? __float_as_int(me.w) : -1;
     const int c0 = __shfl_sync(0xffffffffu, c, 0);
     if (!has) c = c0;
-    const bool uniform = __all_sync(0xffffffffu, c == c0);
-    const int cx = c % n, cy = (c / n) % n, cz = c / (n * n);
+    // cells are non-decreasing along the warp (padding lanes repeat lane 0's):
+    // lane 0 and the largest cell bound its extent
+    const int c31 = __reduce_max_sync(0xffffffffu, c);
+    const int xa = c0 % n, xb = c31 % n;
+    const bool one_row = (c0 / n) == (c31 / n) && xb - xa <= PP_WMAX && xb - xa + 3 <= n;
     Sum3 a;
     unsigned long long pairs = 0, cands = 0;
-    if (uniform) {
-        // the warp's targets share their 27 neighbour cells: stage 32 sources at a
-        // time (3x3x3-cell frame, padded with far-away points), test all 32 into a
-        // mask, evaluate the set bits
-        const float mx = me0.x + 1.0f, my = me0.y + 1.0f, mz = me0.z + 1.0f;
-        for (int dz = -1; dz <= 1; ++dz)
-            for (int dy = -1; dy <= 1; ++dy) {
-                const int64_t r = ((int64_t)wrap(cz + dz, n) * n + wrap(cy + dy, n)) * n;
-                const RowRanges rr(P, r, cx, n);
-                if (has) cands += rr.size();
-                for (int sgi = 0; sgi < rr.nseg; ++sgi) {
-                    const int beg = sgi ? rr.beg[1] : rr.beg[0], end = sgi ? rr.end[1] : rr.end[0];
-                    const int b1 = sgi ? rr.b1[1] : rr.b1[0], b2 = sgi ? rr.b2[1] : rr.b2[0];
-                    const int base = (sgi ? rr.base[1] : rr.base[0]) + 1;
-                    for (int t0 = beg; t0 < end; t0 += 32) {
-                        const int j = t0 + lane;
-                        if (j < end) {
-                            const float4 q = __ldg(&P.pos[j]);
-                            sx[lane] = q.x + (float)(base + (j >= b1) + (j >= b2));
-                            sy[lane] = q.y + (float)(dy + 1);
-                            sz[lane] = q.z + (float)(dz + 1);
-                        } else {
-                            sx[lane] = 1.0e18f;
-                            sy[lane] = 1.0e18f;
-                            sz[lane] = 1.0e18f;
-                        }
-                        __syncwarp();
-                        unsigned mask = 0u;
-#pragma unroll
-                        for (int k = 0; k < 32; ++k) {
-                            const float rx = sx[k] - mx, ry = sy[k] - my, rz = sz[k] - mz;
-                            const float r2 = rx * rx + ry * ry + rz * rz;
-                            mask |= (r2 < P.bcut2 && r2 > 0.0f) ? (1u << k) : 0u;
-                        }
-                        if (!has) mask = 0u;
-                        pairs += __popc(mask);
-                        float px = 0.f, py = 0.f, pz = 0.f;
-                        while (mask) {
-                            const int k = __ffs(mask) - 1;
-                            mask &= mask - 1u;
-                            const float rx = sx[k] - mx, ry = sy[k] - my, rz = sz[k] - mz;
-                            const float g = P.coef * pp_over_r(rx * rx + ry * ry + rz * rz, P.inv_bpp, P.inv_bcut);
-                            px += g * rx;
-                            py += g * ry;
-                            pz += g * rz;
-                        }
-                        a.add_block(px, py, pz);
-                        __syncwarp();
-                    }
-                }
-            }
-    } else if (has) {
-        for (int dz = -1; dz <= 1; ++dz)
-            for (int dy = -1; dy <= 1; ++dy) {
-                const int64_t r = ((int64_t)wrap(cz + dz, n) * n + wrap(cy + dy, n)) * n;
-                const RowRanges rr(P, r, cx, n);
-                cands += rr.size();
-                const float fdy = (float)dy, fdz = (float)dz;
-                float px = 0.f, py = 0.f, pz = 0.f;
-                for (int sgi = 0; sgi < rr.nseg; ++sgi) {
-                    for (int j = rr.beg[sgi]; j < rr.end[sgi]; ++j) {
-                        const float4 q = __ldg(&P.pos[j]);
-                        const float fdx = (float)(rr.base[sgi] + (j >= rr.b1[sgi]) + (j >= rr.b2[sgi]));
-                        const float rx = (fdx + q.x) - me0.x;
-                        const float ry = (fdy + q.y) - me0.y;
-                        const float rz = (fdz + q.z) - me0.z;
-                        const float r2 = rx * rx + ry * ry + rz * rz;
-                        if (r2 < P.bcut2 && r2 > 0.0f) {
-                            const float g = P.coef * pp_over_r(r2, P.inv_bpp, P.inv_bcut);
-                            px += g * rx;
-                            py += g * ry;
-                            pz += g * rz;
-                            ++pairs;
-                        }
-                    }
-                }
-                a.add_block(px, py, pz);
-            }
-    }
+    if (one_row)
+        union_path(P, sh.seg[wib], sh.buf[wib], i, has, c0, xa, xb, me, a, pairs, cands);
+    else
+        lane_path(P, has, c, me, a, pairs, cands);
     if (has) finish(P, i, a.x - a.cx, a.y - a.cy, a.z - a.cz);
     add_stats(P.stats, pairs, cands);
 }
@@ -296,6 +411,7 @@ cudaError_t launch_pp(cube2_ctx *ctx, const cube2_particles *p, int accumulate, 
     P.inv_bpp = (float)(s / ctx->cfg.b_pp);
     P.inv_bcut = (float)(s / ctx->b_range);
     P.bcut2 = (float)((ctx->b_range / s) * (ctx->b_range / s));
+    P.bpp2 = (float)((ctx->cfg.b_pp / s) * (ctx->cfg.b_pp / s));
     const double vp = ctx->cfg.box * ctx->cfg.box * ctx->cfg.box / (double)ctx->N;
     P.coef = (float)(vp / (4.0 * 3.14159265358979323846) / (s * s));
     P.kick = kick;
