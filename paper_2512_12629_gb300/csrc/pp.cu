@@ -12,7 +12,7 @@
 // form, no atomics, deterministic).
 //
 // One thread per target, in particle (= cell) order.  A warp whose 32 targets
-// lie in one row of cells, at most PP_WMAX + 1 cells wide (every dense region),
+// lie in one row of cells, narrow enough (every dense region; see PP_WMAX),
 // shares one source stream: the particles of cells xa-1 .. xb+1 in the 9 rows
 // around it.  It stages 64 sources at a time in shared memory; each lane tests
 // all 64 (sign of r^2 - b_cut^2 shifted into a bit mask, 8 instructions per
@@ -202,14 +202,22 @@ struct WarpSegs {
     int cum[PP_SEGS + 2];
 };
 
-// Union width limit (cells beyond the first) for the shared-stream path.
+// Widest warp (cells beyond the first) that takes the shared-stream path: its
+// lanes test (w + 3) / 3 times their own candidates, still cheaper than the
+// per-lane walk up to about w = 16 over the 256^3 run.
 #ifndef PP_WMAX
-#define PP_WMAX 8
+#define PP_WMAX 16
 #endif
 
+struct PPWarpShared {
+    struct {
+        float4 buf[64];   // staged sources of the union path
+        WarpSegs seg;
+    } u;
+};
+
 struct PPShared {
-    float4 buf[PP_WARPS_CTA][64];             // staged sources of the union path
-    WarpSegs seg[PP_WARPS_CTA];
+    PPWarpShared w[PP_WARPS_CTA];
 };
 
 // Stage stream position p (far-away point past the end).  s: the lane's
@@ -237,8 +245,8 @@ __device__ __forceinline__ unsigned test32(const float4 *S, float mx, float my, 
     return m;
 }
 
-__device__ void union_path(const PPParams &P, WarpSegs &W, float4 *S, int64_t i, bool has, int c0, int xa, int xb,
-                           float4 me, Sum3 &a, unsigned long long &pairs, unsigned long long &cands) {
+// Build the warp's segment table; returns the stream length.
+__device__ int build_segments(const PPParams &P, WarpSegs &W, int c0, int xa, int xb) {
     const int lane = threadIdx.x & 31;
     const int n = P.n_ios;
     const int cz = c0 / (n * n), cy = (c0 / n) % n;
@@ -275,6 +283,13 @@ __device__ void union_path(const PPParams &P, WarpSegs &W, float4 *S, int64_t i,
     if (lane == 0) W.cum[0] = 0;
     if (lane == PP_SEGS) W.cum[PP_SEGS + 1] = 0x7fffffff;
     __syncwarp();
+    return W.cum[PP_SEGS];
+}
+
+__device__ void union_path(const PPParams &P, const WarpSegs &W, float4 *S, int64_t i, bool has, int c0, int xa,
+                           float4 me, Sum3 &a, unsigned long long &pairs, unsigned long long &cands) {
+    const int lane = threadIdx.x & 31;
+    const int n = P.n_ios;
     const int total = W.cum[PP_SEGS];
     // own particle's stream position (row (0, 0) main segment is s = 8)
     const int pself = has ? W.cum[8] + (int)(i - W.beg[8]) : -1000;
@@ -293,38 +308,35 @@ __device__ void union_path(const PPParams &P, WarpSegs &W, float4 *S, int64_t i,
         if (ts >= 0 && ts < 64) m &= ~(1ull << (63 - ts));
         if (!has) m = 0ull;
         pairs += __popcll(m);
-        const unsigned long long m0 = m;
         float px = 0.f, py = 0.f, pz = 0.f;
-        bool close = false;
+        unsigned long long cm = 0ull;   // pairs closer than b_pp
         while (m) {
             const int k = __clzll(m);
-            m ^= 1ull << (63 - k);
+            const unsigned long long bit = 1ull << (63 - k);
+            m ^= bit;
             const float4 q = S[k];
             const float rx = q.x - mx, ry = q.y - my, rz = q.z - mz;
             const float r2 = rx * rx + ry * ry + rz * rz;
             const float g = far_pair(r2, ibc, bpp2);
-            close |= r2 < bpp2;
+            if (r2 < bpp2) cm |= bit;
             px = fmaf(g, rx, px);
             py = fmaf(g, ry, py);
             pz = fmaf(g, rz, pz);
         }
-        if (__any_sync(0xffffffffu, close)) {
-            m = close ? m0 : 0ull;
-            while (m) {
-                const int k = __clzll(m);
-                m ^= 1ull << (63 - k);
+        if (__any_sync(0xffffffffu, cm != 0ull)) {
+            while (cm) {
+                const int k = __clzll(cm);
+                cm ^= 1ull << (63 - k);
                 const float4 q = S[k];
                 const float rx = q.x - mx, ry = q.y - my, rz = q.z - mz;
                 const float r2 = rx * rx + ry * ry + rz * rz;
-                if (r2 < bpp2) {
-                    if (r2 > 0.0f) {
-                        const float g = close_pair(r2, ibp, ibc);
-                        px = fmaf(g, rx, px);
-                        py = fmaf(g, ry, py);
-                        pz = fmaf(g, rz, pz);
-                    } else {
-                        --pairs;   // coincident particles: no pair force
-                    }
+                if (r2 > 0.0f) {
+                    const float g = close_pair(r2, ibp, ibc);
+                    px = fmaf(g, rx, px);
+                    py = fmaf(g, ry, py);
+                    pz = fmaf(g, rz, pz);
+                } else {
+                    --pairs;   // coincident particles: no pair force
                 }
             }
         }
@@ -384,11 +396,13 @@ __global__ void __launch_bounds__(PP_CTA, 3) pp_kernel(PPParams P) {
     // lane 0 and the largest cell bound its extent
     const int c31 = __reduce_max_sync(0xffffffffu, c);
     const int xa = c0 % n, xb = c31 % n;
+    // warps inside one row, at most PP_WMAX + 1 cells wide, share a source stream
     const bool one_row = (c0 / n) == (c31 / n) && xb - xa <= PP_WMAX && xb - xa + 3 <= n;
+    if (one_row) build_segments(P, sh.w[wib].u.seg, c0, xa, xb);
     Sum3 a;
     unsigned long long pairs = 0, cands = 0;
     if (one_row)
-        union_path(P, sh.seg[wib], sh.buf[wib], i, has, c0, xa, xb, me, a, pairs, cands);
+        union_path(P, sh.w[wib].u.seg, sh.w[wib].u.buf, i, has, c0, xa, me, a, pairs, cands);
     else
         lane_path(P, has, c, me, a, pairs, cands);
     if (has) finish(P, i, a.x - a.cx, a.y - a.cy, a.z - a.cz);
