@@ -57,6 +57,7 @@ def parse_args():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="budget of the oracle sample")
+    ap.add_argument("--streams", type=int, default=16, help="graph branches of the ensemble workload")
     return ap.parse_args()
 
 
@@ -111,6 +112,16 @@ def replica_workload(w, rank):
     """The box rank ``rank`` simulates: the workload itself on rank 0, an
     independent realisation (another seed of the same recipe) elsewhere."""
     return w if rank == 0 else w.with_(seed=w.seed + 7919 * rank)
+
+
+def ensemble_share(ws, world, rank):
+    """Indices of the ensemble boxes rank ``rank`` simulates: the boxes are
+    split over the ranks by the library's LPT placement of its per-box cost
+    estimate (largest first, to the least loaded rank)."""
+    from paper_2512_12629_gb300 import cube2
+    costs = [cube2.config_cost(cube2.make_config(w)) for w in ws]
+    bins = cube2.lpt_partition(costs, world)
+    return [i for i, b in enumerate(bins) if b == rank]
 
 
 def job_throughput(units_all_ranks, seconds_slowest):
@@ -322,8 +333,123 @@ def workload_config(w):
 
 
 # ------------------------------------------------------------------ main
+ENSEMBLE = "c4-ensemble-64x20"
+
+
+def run_ensemble(args):
+    """The 64-box ensemble (inputs.workloads.c4_ensemble): every box's 20 KDK
+    steps recorded as one CUDA graph; a step of this bench is one launch of
+    that graph (64 boxes x 20 steps), timed with CUDA events after the
+    particle states are reset to the initial conditions.  The same work issued
+    box by box without the graph is timed beside it."""
+    import numpy as np
+    import torch
+    from inputs.workloads import c4_ensemble
+    from inputs.zeldovich import zeldovich_ios
+    world, rank, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        dist = None
+        torch.cuda.set_device(0)
+    ranks = Ranks(dist, "cuda")
+    from paper_2512_12629_gb300 import build as pkg_build
+    if rank == 0:
+        pkg_build.build()
+    ranks.barrier()
+    pkg_build.build()
+    from paper_2512_12629_gb300 import cube2
+    ws = c4_ensemble()
+    mine = [ws[i] for i in ensemble_share(ws, world, rank)]
+    ctxs, states, ics = [], [], []
+    for w in mine:
+        st = zeldovich_ios(w)
+        ctx = cube2.init_mesh(cube2.make_config(w, n_particles=int(st["count"].sum())))
+        ctx.set_green(0)
+        p = cube2.IOSState.from_numpy(st)
+        ctx.force(p)
+        ctxs.append(ctx)
+        states.append(p)
+        ics.append(p.clone())
+    for c in ctxs:
+        c.check()
+    torch.cuda.synchronize()
+    sched = np.array([w.scale_factors() for w in mine])
+    ens = cube2.Ensemble(ctxs, states, sched, n_streams=args.streams)
+    kernels, psteps = ens.info()
+    stream = torch.cuda.current_stream()
+
+    def reset():
+        for p, q in zip(states, ics):
+            for x, y in zip((p.off, p.count, p.start, p.vel, p.acc), (q.off, q.count, q.start, q.vel, q.acc)):
+                x.copy_(y, non_blocking=True)
+
+    for _ in range(args.warmup):
+        reset()
+        ens.launch(stream)
+    torch.cuda.synchronize()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    clocks = ClockSampler(bus_id_of(torch.cuda.current_device()))
+    clocks.start()
+    ranks.barrier()
+    for e0, e1 in evs:
+        reset()
+        e0.record(stream)
+        ens.launch(stream)
+        e1.record(stream)
+    torch.cuda.synchronize()
+    ranks.barrier()
+    clk = clocks.stop()
+    ms = sum(e0.elapsed_time(e1) for e0, e1 in evs)
+    for c in ctxs:
+        c.check()
+    # the same steps issued box by box on each box's own stream, no graph
+    seq = []
+    for _ in range(max(1, min(args.steps, 3))):
+        reset()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for c, p, a in zip(ctxs, states, sched):
+            for k in range(len(a) - 1):
+                c.kdk_step(p, a[k], a[k + 1])
+        torch.cuda.synchronize()
+        seq.append(time.perf_counter() - t0)
+    seq_s = ranks.max(min(seq))
+    ms_max = ranks.max(ms)
+    units = ranks.sum(psteps * args.steps)
+    value = job_throughput(units, ms_max / 1e3)
+    seq_value = job_throughput(ranks.sum(psteps), seq_s)
+    ens.close()
+    if rank == 0:
+        line = {
+            "metric": "ensemble particle-steps/sec (64 independent boxes x 20 KDK steps, one CUDA graph)",
+            "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded Zel'dovich ICs, BBKS spectrum)",
+            "config": {"workload": ENSEMBLE, "boxes": len(ws), "boxes_this_rank": len(mine),
+                       "particles": int(sum(w.n_particles for w in ws)), "kdk_steps_per_box": ws[0].n_steps,
+                       "graph_branches": args.streams, "placement": "LPT by cube2_config_cost",
+                       "step": "one graph launch = every box's 20 steps; states reset to the ICs before each",
+                       "l2": "inputs larger than L2 (~1 GB of particles and meshes)", "parallelism": "boxes split over ranks"},
+            "sequential": {"value": seq_value, "unit": UNIT,
+                           "what": "same steps launched box by box from Python, no graph, wall clock"},
+            "gpu_launches": kernels * args.steps, "clocks": clk,
+        }
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
 def main():
     args = parse_args()
+    if args.workload == ENSEMBLE:
+        if args.impl == "reference":
+            print(json.dumps({"impl": "reference", "unavailable": "the ensemble workload has no oracle arm"}))
+            return
+        run_ensemble(args)
+        return
     from inputs.workloads import WORKLOADS
     w = WORKLOADS[args.workload]
     if args.impl == "reference":

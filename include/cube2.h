@@ -218,8 +218,9 @@ const char *cube2_profile_class_name(int cls);
 
 /* PP work counters accumulated since the last call: out[0] = ordered pairs
  * closer than the PP range that were evaluated, out[1] = candidate pairs
- * examined (particles in the 27 cells around each target).  Synchronises the
- * stream and resets the counters. */
+ * tested (per target: the shared source stream of its warp where the warp
+ * has one, else the particles of its 27 cells).  Synchronises the stream and
+ * resets the counters. */
 int cube2_pp_stats(cube2_ctx *ctx, int64_t out[2]);
 
 /* Number of kernel launches this context has issued (for launch accounting). */
@@ -227,6 +228,48 @@ int64_t cube2_launch_count(cube2_ctx *ctx);
 
 /* Free every buffer the context owns.  Synchronises its stream first. */
 void cube2_destroy(cube2_ctx *ctx);
+
+/* ---- Ensembles of independent boxes -------------------------------------
+ * Many small simulations on one GPU, and their split over GPUs.  Placement
+ * follows the load balancing of paper Sec. 2.2.3 (Fig. balance): tasks in
+ * decreasing cost order, each to the least loaded worker. */
+
+/* Longest-processing-time-first placement: sort the n costs (finite, >= 0)
+ * in decreasing order (ties keep index order) and give each, in that order,
+ * to the bin with the smallest load so far (lowest index on ties).  Writes
+ * bin_of[i] in [0, bins).  Host only; CUBE2_ERR_BAD_ARG on bad input. */
+int cube2_lpt_partition(const double *cost, int n, int bins, int *bin_of);
+
+/* Work estimate of one KDK step of a box with configuration cfg (arbitrary
+ * units): FFT n^3 log2(n^3) over every PM level plus 64 per particle
+ * (cfg->n_particles).  Host only, no device needed. */
+int cube2_config_cost(const cube2_config *cfg, double *cost);
+
+typedef struct cube2_ensemble cube2_ensemble;
+
+/* Record n_steps KDK steps of each of n_boxes boxes into one CUDA graph.
+ * ctxs[b] / parts[b]: a distinct context and its particle set, on one device,
+ * with current forces (cube2_force, or a previous step) and profiling off.
+ * a: [n_boxes][n_steps + 1] row-major scale factors, increasing per box.
+ * Boxes go to min(n_streams, n_boxes) concurrent graph branches by
+ * cube2_lpt_partition of cube2_config_cost (1 <= n_streams <= 64); a branch runs
+ * its boxes one after another, largest first.  Synchronises every box's
+ * stream, then records; no kernel runs until cube2_ensemble_launch.  On
+ * failure nothing is kept and *out is NULL. */
+int cube2_ensemble_create(cube2_ensemble **out, cube2_ctx *const *ctxs, cube2_particles *const *parts,
+                          int n_boxes, const double *a, int n_steps, int n_streams);
+
+/* Run the recorded steps once on `stream` (a cudaStream_t; NULL = default
+ * stream).  Each launch advances every box by its n_steps from whatever state
+ * its particle arrays hold.  Synchronise `stream` before reading results or
+ * calling cube2_check on a box. */
+int cube2_ensemble_launch(cube2_ensemble *ens, void *stream);
+
+/* out[0] = kernel nodes in the graph, out[1] = particle-steps per launch. */
+int cube2_ensemble_info(const cube2_ensemble *ens, int64_t out[2]);
+
+/* Wait for the graph's last launch on its streams and free it. */
+void cube2_ensemble_destroy(cube2_ensemble *ens);
 
 #ifdef __cplusplus
 }

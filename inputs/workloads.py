@@ -13,6 +13,7 @@ transfer function and Zel'dovich initial conditions.  The paper's own runs
 """
 from __future__ import annotations
 
+import numpy as np
 from dataclasses import dataclass, field, replace
 
 
@@ -105,5 +106,21 @@ C5 = Workload(
     levels=(Level(512, 3.5), Level(2048, 2.0)), b_pp=0.1 * 1000.0 / 1024,
     z_init=49.0, z_final=0.0, n_steps=1, seed=5, displace_to_a=1.0,
 )
+
+def c4_ensemble(n_boxes=64, seed=100, n_steps=20, sizes=(32, 48, 64, 96)):
+    """Ensemble of independent boxes at C1's resolution: box b has
+    n_p ~ U(sizes) particles per side, L = 2 n_p Mpc/h, one PM level of
+    2 n_p cells (2-cell softening = the IOS cell), n_p^3 IOS cells,
+    sigma_8 ~ U(0.7, 0.9), seed ``seed + b``, n_steps constant-Delta-a KDK
+    steps from z = 49 to 0.  Sizes and sigma_8 come from one Philox stream
+    seeded with ``seed``."""
+    rng = np.random.Generator(np.random.Philox(seed))
+    n_ps = rng.choice(np.asarray(sizes), size=n_boxes)
+    s8 = rng.uniform(0.7, 0.9, size=n_boxes)
+    return [Workload(name=f"c4-box{b}-n{int(n)}", n_p=int(n), box=2.0 * int(n), n_ios=int(n),
+                     levels=(Level(2 * int(n), 2.0),), b_pp=0.2, z_init=49.0, z_final=0.0,
+                     n_steps=n_steps, seed=seed + b, sigma8=float(sg))
+            for b, (n, sg) in enumerate(zip(n_ps, s8))]
+
 
 WORKLOADS = {w.name: w for w in (C1, C2, C2_SMALL, C2_MID, C3, C5)}

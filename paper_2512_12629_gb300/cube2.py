@@ -92,6 +92,12 @@ def _load():
         "cube2_profile_class_name": (ctypes.c_char_p, [I]),
         "cube2_pp_stats": (I, [P, ctypes.POINTER(ctypes.c_int64)]),
         "cube2_solve_pm_noalloc": (I, [P, P, P, ctypes.c_int32, P]),
+        "cube2_lpt_partition": (I, [ctypes.POINTER(D), I, I, ctypes.POINTER(I)]),
+        "cube2_config_cost": (I, [ctypes.POINTER(Config), ctypes.POINTER(D)]),
+        "cube2_ensemble_create": (I, [ctypes.POINTER(P), P, P, I, ctypes.POINTER(D), I, I]),
+        "cube2_ensemble_launch": (I, [P, P]),
+        "cube2_ensemble_info": (I, [P, ctypes.POINTER(ctypes.c_int64)]),
+        "cube2_ensemble_destroy": (None, [P]),
         "cube2_destroy": (None, [P]),
     }
     for name, (res, args) in sig.items():
@@ -300,6 +306,76 @@ def solve_pm_noalloc(rho: torch.Tensor, green: torch.Tensor, phi: torch.Tensor, 
     code = _lib.cube2_solve_pm_noalloc(rho.data_ptr(), green.data_ptr(), phi.data_ptr(), n, st.cuda_stream)
     if code != OK:
         raise Cube2Error(code, _lib.cube2_last_error(None).decode())
+
+
+def config_cost(cfg: Config):
+    """Work estimate of one KDK step of a box (cube2_config_cost); host only."""
+    out = ctypes.c_double()
+    code = _lib.cube2_config_cost(ctypes.byref(cfg), ctypes.byref(out))
+    if code != OK:
+        raise Cube2Error(code, "config_cost")
+    return out.value
+
+
+def lpt_partition(costs, bins):
+    """Bin of each task by cube2_lpt_partition (largest cost first, to the least loaded bin)."""
+    c = np.ascontiguousarray(costs, dtype=np.float64)
+    out = np.zeros(len(c), dtype=np.int32)
+    code = _lib.cube2_lpt_partition(c.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), len(c), int(bins),
+                                    out.ctypes.data_as(ctypes.POINTER(ctypes.c_int)))
+    if code != OK:
+        raise Cube2Error(code, "lpt_partition")
+    return out
+
+
+class Ensemble:
+    """n_steps KDK steps of many boxes recorded as one CUDA graph (cube2_ensemble_*).
+
+    ctxs / states: one Context and IOSState per box, forces current.  a: array
+    (n_boxes, n_steps + 1) of scale factors.  The states' tensors are used in
+    place by every launch and must stay alive (this object keeps them)."""
+
+    def __init__(self, ctxs, states, a, n_streams=8):
+        a = np.ascontiguousarray(a, dtype=np.float64)
+        nb, ns = a.shape[0], a.shape[1] - 1
+        if nb != len(ctxs) or nb != len(states):
+            raise ValueError("one context, state and schedule per box")
+        self.ctxs, self.states = list(ctxs), list(states)
+        self._structs = [st.struct() for st in self.states]
+        cp = (ctypes.c_void_p * nb)(*[c.ptr.value for c in self.ctxs])
+        pp = (ctypes.c_void_p * nb)(*[ctypes.addressof(x) for x in self._structs])
+        ptr = ctypes.c_void_p()
+        code = _lib.cube2_ensemble_create(ctypes.byref(ptr), cp, pp, nb,
+                                          a.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), ns, int(n_streams))
+        if code != OK:
+            msgs = [_lib.cube2_last_error(c.ptr).decode() for c in self.ctxs]
+            raise Cube2Error(code, "; ".join(m for m in msgs if m) or "ensemble_create")
+        self.ptr = ptr
+
+    def launch(self, stream=None):
+        st = torch.cuda.current_stream() if stream is None else stream
+        code = _lib.cube2_ensemble_launch(self.ptr, ctypes.c_void_p(st.cuda_stream))
+        if code != OK:
+            raise Cube2Error(code, "ensemble_launch")
+
+    def info(self):
+        """(kernel nodes in the graph, particle-steps per launch)."""
+        out = (ctypes.c_int64 * 2)()
+        code = _lib.cube2_ensemble_info(self.ptr, out)
+        if code != OK:
+            raise Cube2Error(code, "ensemble_info")
+        return int(out[0]), int(out[1])
+
+    def close(self):
+        if getattr(self, "ptr", None):
+            _lib.cube2_ensemble_destroy(self.ptr)
+            self.ptr = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def kdk_factors(cfg: Config, a0, a1):

@@ -13,6 +13,7 @@ import torch.multiprocessing as mp
 
 import bench
 from inputs import C1
+from inputs.workloads import c4_ensemble
 from inputs.zeldovich import zeldovich_ios
 
 
@@ -35,8 +36,9 @@ def _rank_main(rank, world, port, out):
         value = bench.job_throughput(total, slow / 1e3)
         w = bench.replica_workload(C1, rank)
         st = zeldovich_ios(w.with_(n_p=8, n_ios=8))
+        share = bench.ensemble_share(c4_ensemble(), world, rank)
         out.put((rank, ranks.world, ranks.rank, slow, total, value, w.seed,
-                 st["off"].tobytes()))
+                 st["off"].tobytes(), share))
     finally:
         dist.destroy_process_group()
 
@@ -52,7 +54,7 @@ def test_two_gloo_ranks_reduce_like_the_gpu_job():
     for p in procs:
         p.join(timeout=60)
         assert p.exitcode == 0
-    (r0, w0, k0, slow0, tot0, v0, seed0, off0), (r1, w1, k1, slow1, tot1, v1, seed1, off1) = res
+    (r0, w0, k0, slow0, tot0, v0, seed0, off0, sh0), (r1, w1, k1, slow1, tot1, v1, seed1, off1, sh1) = res
     assert (w0, w1, k0, k1) == (2, 2, 0, 1)
     # every rank sees the slowest time and the sum of the units
     assert slow0 == slow1 == 20.0 and tot0 == tot1 == 2000.0
@@ -60,6 +62,13 @@ def test_two_gloo_ranks_reduce_like_the_gpu_job():
     # rank 0 runs the workload itself, rank 1 another realisation of it
     assert seed0 == C1.seed and seed1 != seed0
     assert off0 != off1
+    # the ensemble's boxes split over the two ranks: disjoint, complete, balanced
+    ws = c4_ensemble()
+    assert sorted(sh0 + sh1) == list(range(len(ws))) and not set(sh0) & set(sh1)
+    from paper_2512_12629_gb300 import cube2
+    cost = [cube2.config_cost(cube2.make_config(w)) for w in ws]
+    l0, l1 = sum(cost[i] for i in sh0), sum(cost[i] for i in sh1)
+    assert abs(l0 - l1) <= max(cost)
 
 
 def test_single_rank_reductions_are_identity():

@@ -57,6 +57,11 @@ def _state(name):
         return RAGGED, random_ios(12 ** 3, 12, RAGGED.box, seed=31, clustered=0.3)
     if name == "CLUSTER":
         return CLUSTER, random_ios(5000, 16, CLUSTER.box, seed=32, clustered=0.8)
+    if name == "C4_24":
+        # an ensemble box with a radix-3 mesh: 24^3 particles, 48^3 mesh
+        from inputs.workloads import c4_ensemble
+        w = c4_ensemble(n_boxes=1, seed=41, sizes=(24,))[0]
+        return w, zeldovich_ios(w)
     if name == "DENSE":
         # a 4500-particle clump: its brick holds more particles than the brick
         # kernel stages, so its cells go through the tiled PP kernel
@@ -84,7 +89,7 @@ def case(name):
     return _CACHE[name]
 
 
-ALL = ["C1", "C2_SMALL", "RAGGED", "CLUSTER", "DENSE"]
+ALL = ["C1", "C2_SMALL", "RAGGED", "CLUSTER", "DENSE", "C4_24"]
 
 
 @pytest.mark.parametrize("name", ALL)
