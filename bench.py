@@ -222,11 +222,12 @@ def algorithmic_bytes(w, n_part, cls, level):
     return table[cls]
 
 
-# FP32 operations of one in-range PP pair (separation 6, r^2 5, rsqrt and
-# range logic 6, the R_PP polynomial and scaling 12, force components 3,
-# Kahan updates 12) and of one candidate test (separation and r^2 11)
-PP_FLOPS_PAIR = 44
-PP_FLOPS_CANDIDATE = 11
+# FP32 operations (an FMA counts 2) of one in-range PP pair: separation 3,
+# r^2 5, rsqrt and u = r/b, v = 1 - u 4, the two shell polynomials of R_PP with
+# their powers 24, the 1/r^3 scaling 3, accumulation of the three components 6;
+# and of one candidate test: separation 3 and r^2 - b^2 6
+PP_FLOPS_PAIR = 45
+PP_FLOPS_CANDIDATE = 9
 
 
 def fp32_peak_tflops(sm_mhz):
@@ -544,7 +545,7 @@ def main():
         fpk = fp32_peak_tflops(mhz)
         flops = pp_pairs * PP_FLOPS_PAIR / dcount
         achieved = flops / (per_launch_ms / 1e3) / 1e12
-        roofline = {"bound": "alu", "kernel": "pp (sparse + dense kernels)", "achieved": achieved, "peak": fpk,
+        roofline = {"bound": "alu", "kernel": "pp_kernel (shared-stream and per-lane paths)", "achieved": achieved, "peak": fpk,
                     "unit": "TFLOP/s", "frac": achieved / fpk,
                     "peak_source": f"derived: 152 SMs x 128 FP32 lanes x 2 x {mhz:.0f} MHz",
                     "algorithmic_flops_per_launch": flops,
