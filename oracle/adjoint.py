@@ -1,0 +1,151 @@
+"""FP64 oracle: vector-Jacobian products of the PM + PP force (adjoint building blocks).
+
+TEST INFRASTRUCTURE ONLY.  Imported by tests/ only; never by the product path.
+
+The force of Sec. 2.1 as a function of continuous particle positions x
+(Mpc/h, shape (3, N)); the IOS quantisation of Sec. 2.3 is treated as the
+identity, so positions enter as plain numbers.  For a PM level with n^3 cells
+of size H, positions in mesh cells are u = x / H and, with the conventions of
+``oracle.mesh`` (cell c spans [c, c+1), CIC W(u, c) = prod_d w(u_d - c_d - 1/2),
+w(t) = max(0, 1 - |t|)):
+
+    rho(c) = (n^3 / N) sum_i W(u_i, c)             assignment (Eq. filter, CIC reading)
+    phi    = G * rho                                Poisson solve with the Eq. (Gk) table
+    E_d    = D_d * phi                              4-point difference (Eq. diff)
+    F_i    = -H sum_c W(u_i, c) E(c)                interpolation, F = -grad u
+
+and the PP term (Eq. PP) is F_i = sum_{j != i} g(r_ij) (x_j - x_i) with
+g(r) = V_p R_PP(r) / (4 pi r), r < b_cut, minimum image.
+
+For a cotangent v (3, N) the vector-Jacobian product w_i = d<v, F(x)>/dx_i is
+(chain rule; G is even and D_d odd, so the transpose of D_d * G * is
+-G * D_d *):
+
+    PM:  w_i = -sum_c grad_u W(u_i, c) (E(c) . v_i) + sum_c grad_u W(u_i, c) psi(c),
+         psi = G * s,   s = (n^3 / N) sum_d D_d * mu_d,   mu_d(c) = sum_j W(u_j, c) v_{j,d}
+    PP:  w_i = sum_{j != i} A_ij (v_j - v_i),   A = g I + (g'(r) / r) d d^T,   d = x_j - x_i.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+from .kernels import pp_reference, reference_force_derivative
+from .mesh import fd_gradient, level_params, solve_potential
+
+
+def cic_corners(u, n):
+    """The 8 CIC corners of positions u (3, N) in mesh cells: a list of
+    (flat cell index, weight W, gradient of W with respect to u (3, N))."""
+    t = u - 0.5
+    i0 = np.floor(t).astype(np.int64)
+    f = t - i0
+    w = [1.0 - f, f]                       # weights of the lower / upper corner per axis
+    dw = [-np.ones_like(f), np.ones_like(f)]
+    out = []
+    for cz in (0, 1):
+        for cy in (0, 1):
+            for cx in (0, 1):
+                c = (cx, cy, cz)
+                idx = (((i0[2] + cz) % n) * n + (i0[1] + cy) % n) * n + (i0[0] + cx) % n
+                wd = [w[c[d]][d] for d in range(3)]
+                W = wd[0] * wd[1] * wd[2]
+                grad = np.stack([dw[c[0]][0] * wd[1] * wd[2], wd[0] * dw[c[1]][1] * wd[2],
+                                 wd[0] * wd[1] * dw[c[2]][2]])
+                out.append((idx, W, grad))
+    return out
+
+
+def _deposit(corners, vals, n):
+    """sum over particles of W * vals onto the mesh ([z][y][x])."""
+    m = np.zeros(n ** 3)
+    for idx, W, _ in corners:
+        np.add.at(m, idx, W * vals)
+    return m.reshape(n, n, n)
+
+
+def pm_force_level(x, box, n, n_particles, g):
+    """F (3, N) of one PM level at continuous positions x."""
+    h = box / n
+    corners = cic_corners(x / h, n)
+    rho = _deposit(corners, np.ones(x.shape[1]), n) * (n ** 3 / n_particles)
+    e = fd_gradient(solve_potential(rho, g)).reshape(3, -1)
+    f = np.zeros_like(x)
+    for idx, W, _ in corners:
+        f -= h * W * e[:, idx]
+    return f
+
+
+def pm_vjp_level(x, v, box, n, n_particles, g):
+    """d<v, F_level(x)>/dx (3, N)."""
+    h = box / n
+    corners = cic_corners(x / h, n)
+    rho = _deposit(corners, np.ones(x.shape[1]), n) * (n ** 3 / n_particles)
+    e = fd_gradient(solve_potential(rho, g)).reshape(3, -1)
+    mu = np.stack([_deposit(corners, v[d], n) for d in range(3)])
+    # s = (n^3/N) sum_d D_d * mu_d: component d of fd_gradient(mu_d) is D_d * mu_d
+    s = sum(fd_gradient(mu[d])[d] for d in range(3)) * (n ** 3 / n_particles)
+    psi = solve_potential(s, g).reshape(-1)
+    w = np.zeros_like(x)
+    for idx, _W, grad in corners:
+        ev = (e[:, idx] * v).sum(axis=0)
+        w += grad * (psi[idx] - ev)
+    return w
+
+
+def _pairs(x, box, b_cut):
+    """All ordered pairs (i, j), i != j, closer than b_cut (minimum image):
+    indices and separations d = x_j - x_i (3, P)."""
+    n = x.shape[1]
+    d = x[:, None, :] - x[:, :, None]            # d[:, i, j] = x_j - x_i
+    d -= box * np.rint(d / box)
+    r = np.sqrt((d * d).sum(axis=0))
+    i, j = np.nonzero((r > 0) & (r < b_cut))
+    return i, j, d[:, i, j], r[i, j]
+
+
+def pp_force(x, box, n_particles, b_pp, b_cut):
+    """PP force (3, N) at continuous positions, all pairs."""
+    i, j, d, r = _pairs(x, box, b_cut)
+    g = box ** 3 / n_particles * pp_reference(r, b_pp, b_cut) / (4 * math.pi * r)
+    f = np.zeros_like(x)
+    for ax in range(3):
+        f[ax] = np.bincount(i, weights=g * d[ax], minlength=x.shape[1])
+    return f
+
+
+def pp_vjp(x, v, box, n_particles, b_pp, b_cut):
+    """d<v, F_PP(x)>/dx (3, N), all pairs."""
+    i, j, d, r = _pairs(x, box, b_cut)
+    vp = box ** 3 / n_particles / (4 * math.pi)
+    rpp = pp_reference(r, b_pp, b_cut)
+    drpp = reference_force_derivative(r, b_pp) - reference_force_derivative(r, b_cut)
+    g = vp * rpp / r
+    gp = vp * (drpp / r - rpp / r ** 2)
+    dv = v[:, j] - v[:, i]
+    term = g * dv + (gp / r) * d * (d * dv).sum(axis=0)
+    w = np.zeros_like(x)
+    for ax in range(3):
+        w[ax] = np.bincount(i, weights=term[ax], minlength=x.shape[1])
+    return w
+
+
+def force(x, wl, greens):
+    """Total force (every PM level plus PP) of workload wl at positions x."""
+    n_part = x.shape[1]
+    f = np.zeros_like(x)
+    for (n, _h, _bs, _bt), g in zip(level_params(wl), greens):
+        f += pm_force_level(x, wl.box, n, n_part, g)
+    n_f, h_f, b_soft, _ = level_params(wl)[-1]
+    return f + pp_force(x, wl.box, n_part, wl.b_pp, b_soft * h_f)
+
+
+def force_vjp(x, v, wl, greens):
+    """d<v, F(x)>/dx for the total force of workload wl."""
+    n_part = x.shape[1]
+    w = np.zeros_like(x)
+    for (n, _h, _bs, _bt), g in zip(level_params(wl), greens):
+        w += pm_vjp_level(x, v, wl.box, n, n_part, g)
+    n_f, h_f, b_soft, _ = level_params(wl)[-1]
+    return w + pp_vjp(x, v, wl.box, n_part, wl.b_pp, b_soft * h_f)

@@ -55,6 +55,19 @@ def reference_force(r, b):
     return np.where(r < 0.5 * b, inner, np.where(r < b, outer_shell, newton))
 
 
+def reference_force_derivative(r, b):
+    """dR/dr of Eq. (refforce), branch by branch (the derivative of each
+    polynomial, and -2/r^3 beyond b)."""
+    r = np.asarray(r, dtype=np.float64)
+    inner = (64 / (5 * b ** 3) - 768 * r ** 2 / (5 * b ** 5) + 128 * r ** 3 / b ** 6
+             + 1536 * r ** 4 / (7 * b ** 7) - 1152 * r ** 5 / (5 * b ** 8))
+    with np.errstate(divide="ignore"):
+        outer_shell = (-6 / (35 * r ** 3) + 256 / (5 * b ** 3) - 192 * r / b ** 4 + 768 * r ** 2 / (5 * b ** 5)
+                       + 128 * r ** 3 / b ** 6 - 1536 * r ** 4 / (7 * b ** 7) + 384 * r ** 5 / (5 * b ** 8))
+        newton = -2.0 / r ** 3
+    return np.where(r < 0.5 * b, inner, np.where(r < b, outer_shell, newton))
+
+
 def pp_reference(r, b_pp, b_cut):
     """Eq. (PP): R_PP(r) = R(r, b_PP) - R(r, b_cut); zero for r >= b_cut."""
     return reference_force(r, b_pp) - reference_force(r, b_cut)

@@ -1,0 +1,93 @@
+"""Pins of the FP64 adjoint oracle (oracle/adjoint.py): the vector-Jacobian
+products against central finite differences of the forward force (FP64,
+continuous positions), the continuous forward against the IOS forward at IOS
+positions, and dR/dr against differences of R."""
+import numpy as np
+import pytest
+
+from inputs import C2_SMALL
+from inputs.workloads import Level
+from inputs.zeldovich import random_ios
+from oracle import adjoint as A
+from oracle import kernels as K
+from oracle import mesh as M
+
+
+def test_reference_force_derivative_matches_differences():
+    for b in (0.3, 1.0, 2.5):
+        r = np.linspace(0.01, 1.6 * b, 997)
+        r = r[(np.abs(r - 0.5 * b) > 1e-3) & (np.abs(r - b) > 1e-3)]
+        h = 1e-6 * b
+        fd = (K.reference_force(r + h, b) - K.reference_force(r - h, b)) / (2 * h)
+        an = K.reference_force_derivative(r, b)
+        assert np.allclose(an, fd, rtol=1e-6, atol=1e-6 * np.abs(an).max())
+
+
+def _directional(fn, x, v, e, h):
+    return ((v * fn(x + h * e)).sum() - (v * fn(x - h * e)).sum()) / (2 * h)
+
+
+@pytest.mark.parametrize("n,bs,bt", [(16, 2.0, None), (16, 2.0, 3.5), (12, 3.5, None)])
+def test_pm_vjp_matches_finite_differences(n, bs, bt):
+    rng = np.random.default_rng(n + int(bs * 10))
+    box, npart = 24.0, 300
+    x = rng.uniform(0, box, (3, npart))
+    v = rng.normal(size=(3, npart))
+    g = K.green(n, bs, bt)
+    w = A.pm_vjp_level(x, v, box, n, npart, g)
+    for k in range(3):
+        e = rng.normal(size=(3, npart))
+        fd = _directional(lambda y: A.pm_force_level(y, box, n, npart, g), x, v, e, 1e-6)
+        assert abs((w * e).sum() - fd) <= 1e-6 * (np.abs(w).sum() + abs(fd))
+    # single components: one particle, one axis
+    for i, d in ((0, 0), (7, 1), (123, 2)):
+        e = np.zeros((3, npart))
+        e[d, i] = 1.0
+        fd = _directional(lambda y: A.pm_force_level(y, box, n, npart, g), x, v, e, 1e-6)
+        assert abs(w[d, i] - fd) <= 1e-6 * np.abs(w).max()
+
+
+def test_pp_vjp_matches_finite_differences():
+    rng = np.random.default_rng(5)
+    box, npart, b_pp, b_cut = 8.0, 400, 0.15, 1.0
+    x = rng.uniform(0, box, (3, npart))
+    x[:, 1] = x[:, 0] + [0.05, 0.02, -0.03]          # a pair closer than b_pp
+    v = rng.normal(size=(3, npart))
+    w = A.pp_vjp(x, v, box, npart, b_pp, b_cut)
+    for k in range(3):
+        e = rng.normal(size=(3, npart))
+        fd = _directional(lambda y: A.pp_force(y, box, npart, b_pp, b_cut), x, v, e, 1e-7)
+        assert abs((w * e).sum() - fd) <= 1e-6 * (np.abs(w).sum() + abs(fd))
+    for i, d in ((0, 0), (1, 2), (77, 1)):
+        e = np.zeros((3, npart))
+        e[d, i] = 1.0
+        fd = _directional(lambda y: A.pp_force(y, box, npart, b_pp, b_cut), x, v, e, 1e-7)
+        assert abs(w[d, i] - fd) <= 1e-6 * np.abs(w).max()
+    # momentum: the PP force is translation invariant, so the VJP sums to zero
+    assert np.abs(w.sum(axis=1)).max() <= 1e-10 * np.abs(w).sum()
+
+
+def test_continuous_forward_equals_ios_forward_at_ios_positions():
+    w = C2_SMALL.with_(n_p=16, box=16.0, n_ios=16, levels=(Level(8, 3.5), Level(32, 2.0)))
+    st = random_ios(16 ** 3, 16, w.box, seed=3, clustered=0.3)
+    x = M.positions(st["off"], st["count"], w.n_ios, w.box)
+    greens = M.green_tables(w)
+    for (n, h, _bs, _bt), g in zip(M.level_params(w), greens):
+        ref, _ = M.pm_force_level(st["off"], st["count"], w.n_ios, n, h, g)
+        got = A.pm_force_level(x, w.box, n, x.shape[1], g)
+        # the coarse level floors one bit of the position (2^-17 cell) in the IOS forward
+        tol = 1e-12 if n >= w.n_ios else 1e-4
+        assert np.abs(got - ref).max() <= tol * np.abs(ref).max()
+
+
+def test_total_force_vjp_two_levels():
+    w = C2_SMALL.with_(n_p=8, box=16.0, n_ios=8, levels=(Level(8, 3.5), Level(16, 2.0)), b_pp=0.3)
+    rng = np.random.default_rng(11)
+    npart = 8 ** 3
+    x = rng.uniform(0, w.box, (3, npart))
+    v = rng.normal(size=(3, npart))
+    greens = M.green_tables(w)
+    wv = A.force_vjp(x, v, w, greens)
+    e = rng.normal(size=(3, npart))
+    fd = _directional(lambda y: A.force(y, w, greens), x, v, e, 1e-6)
+    assert abs((wv * e).sum() - fd) <= 1e-6 * (np.abs(wv).sum() + abs(fd))
