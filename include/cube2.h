@@ -229,6 +229,28 @@ int64_t cube2_launch_count(cube2_ctx *ctx);
 /* Free every buffer the context owns.  Synchronises its stream first. */
 void cube2_destroy(cube2_ctx *ctx);
 
+/* ---- Adjoint: vector-Jacobian product of the force -----------------------
+ * The force of Secs. 2.1-2.2 (every PM level plus PP) as a function of the
+ * particle positions x (Mpc/h), with the IOS quantisation of Sec. 2.3 taken
+ * as the identity (the CIC weights and their gradients are those of the
+ * stored positions).  For a cotangent v the product is
+ * w_i = d<v, F(x)>/dx_i: per PM level, -sum_c grad W(u_i,c) (E(c).v_i) +
+ * sum_c grad W(u_i,c) psi(c) with psi = G * (n^3/N) sum_d D_d * mu_d and mu_d
+ * the CIC deposit of v_d (G even, D_d odd); for PP,
+ * sum_j (g I + g'/r d d^T)(v_j - v_i), g = V_p R_PP(r)/(4 pi r). */
+
+/* Allocate the product's scratch (three FP32 meshes of the largest level).
+ * The one allocating call after cube2_init_mesh; idempotent. */
+int cube2_adjoint_init(cube2_ctx *ctx);
+
+/* w[d] (device FP32 [N], overwritten) = the product for cotangent v[d]
+ * (device FP32 [N]), both in the particle order of p.  Needs
+ * cube2_adjoint_init and every level's Green's table (CUBE2_ERR_STATE).
+ * Overwrites the levels' density/potential grids.  The cotangent deposit
+ * uses float atomics: results agree with the FP64 product to FP32 accuracy
+ * but their last bits may differ between runs. */
+int cube2_force_vjp(cube2_ctx *ctx, const cube2_particles *p, const float *const v[3], float *const w[3]);
+
 /* ---- Ensembles of independent boxes -------------------------------------
  * Many small simulations on one GPU, and their split over GPUs.  Placement
  * follows the load balancing of paper Sec. 2.2.3 (Fig. balance): tasks in

@@ -32,7 +32,8 @@ import math
 import numpy as np
 
 from .kernels import pp_reference, reference_force_derivative
-from .mesh import fd_gradient, level_params, solve_potential
+from .mesh import FIX, fd_gradient, level_params, solve_potential
+from .pp import _neighbour_pairs
 
 
 def cic_corners(u, n):
@@ -128,6 +129,38 @@ def pp_vjp(x, v, box, n_particles, b_pp, b_cut):
     w = np.zeros_like(x)
     for ax in range(3):
         w[ax] = np.bincount(i, weights=term[ax], minlength=x.shape[1])
+    return w
+
+
+def pp_vjp_cells(off, count, start, n_ios, box, b_pp, b_cut, v, n_particles=None):
+    """pp_vjp for IOS data with the cell list of ``oracle.pp`` (the IOS cell is
+    at least b_cut wide, so the 27 cells around a particle hold its partners);
+    separations are formed exactly from the fixed-point offsets."""
+    n_part = int(count.sum()) if n_particles is None else n_particles
+    s_ios = box / n_ios
+    vp = box ** 3 / n_part / (4 * math.pi)
+    off64 = off.astype(np.int64)
+    w = np.zeros((3, n_part))
+    for oz in (-1, 0, 1):
+        for oy in (-1, 0, 1):
+            for ox in (-1, 0, 1):
+                i, j = _neighbour_pairs(count, start, n_ios, (ox, oy, oz))
+                if i.size == 0:
+                    continue
+                d = np.empty((3, i.size))
+                for ax, o in enumerate((ox, oy, oz)):
+                    d[ax] = (o * FIX + off64[ax, j] - off64[ax, i]) * (s_ios / FIX)
+                r = np.sqrt((d * d).sum(axis=0))
+                m = (r > 0) & (r < b_cut) & (i != j)
+                i, j, d, r = i[m], j[m], d[:, m], r[m]
+                rpp = pp_reference(r, b_pp, b_cut)
+                drpp = reference_force_derivative(r, b_pp) - reference_force_derivative(r, b_cut)
+                g = vp * rpp / r
+                gp = vp * (drpp / r - rpp / r ** 2)
+                dv = v[:, j] - v[:, i]
+                term = g * dv + (gp / r) * d * (d * dv).sum(axis=0)
+                for ax in range(3):
+                    w[ax] += np.bincount(i, weights=term[ax], minlength=n_part)
     return w
 
 

@@ -11,6 +11,8 @@
 
 #include "common.cuh"
 
+#include <algorithm>
+
 namespace cube2 {
 bool fft_size_supported(int n);
 
@@ -128,6 +130,7 @@ void free_ctx(cube2_ctx *c) {
     cudaFree(c->big);
     cudaFree(c->big_n);
     cudaFree(c->pos4);
+    cudaFree(c->vjp_mu);
     cudaFree(c->pp_stats);
     cudaFree(c->dev_status);
     cudaFreeHost(c->host_status);
@@ -420,6 +423,51 @@ int cube2_kdk_step(cube2_ctx *ctx, cube2_particles *p, double a0, double a1) {
     if (e == cudaSuccess) e = launch_rebin(ctx, p);
     if (e != cudaSuccess) return cuda_error(ctx, e, "kick/drift/rebin");
     return force_core(ctx, p, (float)(c * f[2]));
+}
+
+int cube2_adjoint_init(cube2_ctx *ctx) {
+    if (!ctx) return CUBE2_ERR_BAD_ARG;
+    if (ctx->vjp_mu) return CUBE2_OK;
+    int64_t m = 0;
+    for (int l = 0; l < ctx->nl; ++l) m = std::max(m, (int64_t)ctx->lev[l].n * ctx->lev[l].n * ctx->lev[l].n);
+    cudaError_t e = cudaMalloc((void **)&ctx->vjp_mu, sizeof(float) * 3 * (size_t)m);
+    if (e != cudaSuccess) {
+        ctx->vjp_mu = nullptr;
+        return cuda_error(ctx, e, "adjoint scratch");
+    }
+    return CUBE2_OK;
+}
+
+int cube2_force_vjp(cube2_ctx *ctx, const cube2_particles *p, const float *const v[3], float *const w[3]) {
+    if (!ctx) return CUBE2_ERR_BAD_ARG;
+    if (!particles_ok(ctx, p, false, false) || !v || !w)
+        return set_error(ctx, CUBE2_ERR_BAD_ARG, "bad particle or cotangent arrays");
+    for (int d = 0; d < 3; ++d)
+        if (ctx->N > 0 && (!v[d] || !w[d])) return set_error(ctx, CUBE2_ERR_BAD_ARG, "null cotangent array");
+    if (!ctx->vjp_mu) return set_error(ctx, CUBE2_ERR_STATE, "call cube2_adjoint_init first");
+    for (int l = 0; l < ctx->nl; ++l)
+        if (!ctx->lev[l].has_green) return set_error(ctx, CUBE2_ERR_STATE, "the product needs every level's Green's table");
+    cudaError_t e = launch_cellid(ctx, p);
+    for (int d = 0; d < 3 && e == cudaSuccess; ++d)
+        if (ctx->N > 0) e = cudaMemsetAsync(w[d], 0, sizeof(float) * (size_t)ctx->N, ctx->stream);
+    for (int l = 0; l < ctx->nl && e == cudaSuccess; ++l) {
+        Level &L = ctx->lev[l];
+        e = launch_deposit(ctx, l, p, nullptr);                        // rho
+        if (e == cudaSuccess) e = launch_fft_forward(ctx, L);           // phi = G * rho
+        if (e == cudaSuccess) e = launch_fft_z_green(ctx, L);
+        if (e == cudaSuccess) e = launch_fft_inverse(ctx, L);
+        if (e == cudaSuccess) e = launch_vjp_gather_e(ctx, L, p, v, w);  // -sum grad W (E . v)
+        if (e == cudaSuccess) e = launch_vjp_source(ctx, L, p, v);      // s = (n^3/N) sum_d D_d * mu_d
+        if (e == cudaSuccess) e = launch_fft_forward(ctx, L);           // psi = G * s
+        if (e == cudaSuccess) e = launch_fft_z_green(ctx, L);
+        if (e == cudaSuccess) e = launch_fft_inverse(ctx, L);
+        if (e == cudaSuccess) e = launch_vjp_gather_psi(ctx, L, p, v, w);  // + sum grad W psi
+        L.has_density = false;
+        L.has_potential = false;
+    }
+    if (e == cudaSuccess) e = launch_pp_vjp(ctx, p, v, w);
+    if (e != cudaSuccess) return cuda_error(ctx, e, "force_vjp");
+    return CUBE2_OK;
 }
 
 int cube2_kdk_step_host(cube2_ctx *ctx, cube2_particles *dev, cube2_particles *host, double a0, double a1) {

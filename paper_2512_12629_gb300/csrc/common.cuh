@@ -89,6 +89,8 @@ struct cube2_ctx {
     cudaEvent_t *ev = nullptr;     // pool of 2 * prof_cap events
     int prof_cap = 0, prof_used = 0;
     int *prof_cls = nullptr;       // [prof_cap] class * CUBE2_MAX_LEVELS + level
+    // force vector-Jacobian product scratch (cube2_adjoint_init)
+    float *vjp_mu = nullptr;       // [3][n_max^3] CIC deposit of the cotangent
 };
 
 namespace cube2 {
@@ -123,6 +125,13 @@ cudaError_t launch_kick_drift(cube2_ctx *ctx, const cube2_particles *p, float ki
 cudaError_t launch_scan(cube2_ctx *ctx, const int32_t *in, int32_t *out, int64_t n);
 cudaError_t launch_rebin(cube2_ctx *ctx, const cube2_particles *p);
 int64_t scan_scratch_len(int64_t n);
+// force vector-Jacobian product
+cudaError_t launch_vjp_gather_e(cube2_ctx *ctx, Level &L, const cube2_particles *p, const float *const v[3],
+                                float *const w[3]);
+cudaError_t launch_vjp_gather_psi(cube2_ctx *ctx, Level &L, const cube2_particles *p, const float *const v[3],
+                                  float *const w[3]);
+cudaError_t launch_vjp_source(cube2_ctx *ctx, Level &L, const cube2_particles *p, const float *const v[3]);
+cudaError_t launch_pp_vjp(cube2_ctx *ctx, const cube2_particles *p, const float *const v[3], float *const w[3]);
 
 }  // namespace cube2
 

@@ -382,6 +382,99 @@ __device__ void lane_path(const PPParams &P, bool has, int c, float4 me, Sum3 &a
         }
 }
 
+// ---------------------------------------------------------------- adjoint
+// d(R(r, b) b^2)/du of Eq. (refforce), u = r/b < 1 (derivative of each branch).
+__device__ __forceinline__ float ref_force_deriv_scaled(float u) {
+    if (u < 0.5f)
+        return 64.0f / 5.0f + u * u * (-768.0f / 5.0f + u * (128.0f + u * (1536.0f / 7.0f - 1152.0f / 5.0f * u)));
+    return -6.0f / (35.0f * u * u * u) +
+           (256.0f / 5.0f + u * (-192.0f + u * (768.0f / 5.0f + u * (128.0f + u * (-1536.0f / 7.0f + 384.0f / 5.0f * u)))));
+}
+
+// For the pair term g(r) d of the PP force (g = R_PP(r)/r, IOS-cell units):
+// gc = g(r) and gp = g'(r)/r, so that the pair's Jacobian block is
+// gc I + gp d d^T.  Far pairs use the shell polynomial m(u) of far_pair and
+// its derivative; pairs closer than b_pp the two-term formula and its
+// derivative.
+__device__ __forceinline__ void pp_jacobian_pair(float r2, float inv_bpp, float inv_bcut, float bpp2, float &gc,
+                                                 float &gp) {
+    const float rinv = rsqrtf(r2);
+    if (r2 >= bpp2) {
+        const float u = r2 * rinv * inv_bcut;
+        float m, dm;
+        if (u >= 0.5f) {
+            const float v = 1.0f - u, v2 = v * v, v4 = v2 * v2;
+            m = v4 * v * (192.0f / 5.0f + v * (-416.0f / 5.0f + v * (2048.0f / 35.0f - 64.0f / 5.0f * v)));
+            dm = -v4 * (192.0f + v * (-2496.0f / 5.0f + v * (2048.0f / 5.0f - 512.0f / 5.0f * v)));
+        } else {
+            const float u2 = u * u;
+            m = 1.0f + u2 * u * (-64.0f / 5.0f + u2 * (256.0f / 5.0f + u * (-32.0f + u * (-1536.0f / 35.0f + 192.0f / 5.0f * u))));
+            dm = u2 * (-192.0f / 5.0f + u2 * (256.0f + u * (-192.0f + u * (-1536.0f / 5.0f + 1536.0f / 5.0f * u))));
+        }
+        const float r3 = rinv * rinv * rinv;
+        gc = m * r3;
+        gp = rinv * r3 * (dm * inv_bcut - 3.0f * m * rinv);
+    } else {
+        const float r = r2 * rinv;
+        gc = (ref_force_scaled(r * inv_bpp) * inv_bpp * inv_bpp - ref_force_scaled(r * inv_bcut) * inv_bcut * inv_bcut) *
+             rinv;
+        const float dr = ref_force_deriv_scaled(r * inv_bpp) * inv_bpp * inv_bpp * inv_bpp -
+                         ref_force_deriv_scaled(r * inv_bcut) * inv_bcut * inv_bcut * inv_bcut;
+        gp = (dr - gc) * rinv * rinv;
+    }
+}
+
+struct VjpIO {
+    const float *v0, *v1, *v2;
+    float *w0, *w1, *w2;
+    float scale;   // coef / s_ios: Jacobian in cell units to d/dx in Mpc/h
+};
+
+// PP part of the vector-Jacobian product: w_i += sum_j A_ij (v_j - v_i) with
+// A_ij = g I + (g'/r) d d^T (the force's Jacobian blocks are symmetric).
+// Each lane walks its target's 27 cells as in the per-lane force path.
+__global__ void __launch_bounds__(PP_CTA) pp_vjp_kernel(PPParams P, VjpIO V) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= P.N) return;
+    const int n = P.n_ios;
+    const float4 me = P.pos[i];
+    const int c = __float_as_int(me.w);
+    const int cx = c % n, cy = (c / n) % n, cz = c / (n * n);
+    const float vix = V.v0[i], viy = V.v1[i], viz = V.v2[i];
+    Sum3 a;
+    for (int dz = -1; dz <= 1; ++dz)
+        for (int dy = -1; dy <= 1; ++dy) {
+            const int64_t r = ((int64_t)wrap(cz + dz, n) * n + wrap(cy + dy, n)) * n;
+            const RowRanges rr(P, r, cx, n);
+            const float fdy = (float)dy, fdz = (float)dz;
+            float px = 0.f, py = 0.f, pz = 0.f;
+            for (int sgi = 0; sgi < rr.nseg; ++sgi) {
+                for (int j = rr.beg[sgi]; j < rr.end[sgi]; ++j) {
+                    const float4 q = __ldg(&P.pos[j]);
+                    const float fdx = (float)(rr.base[sgi] + (j >= rr.b1[sgi]) + (j >= rr.b2[sgi]));
+                    const float rx = (fdx + q.x) - me.x;
+                    const float ry = (fdy + q.y) - me.y;
+                    const float rz = (fdz + q.z) - me.z;
+                    const float r2 = rx * rx + ry * ry + rz * rz;
+                    if (r2 < P.bcut2 && r2 > 0.0f) {
+                        float gc, gp;
+                        pp_jacobian_pair(r2, P.inv_bpp, P.inv_bcut, P.bpp2, gc, gp);
+                        const float dvx = __ldg(&V.v0[j]) - vix, dvy = __ldg(&V.v1[j]) - viy,
+                                    dvz = __ldg(&V.v2[j]) - viz;
+                        const float dd = gp * (rx * dvx + ry * dvy + rz * dvz);
+                        px += gc * dvx + dd * rx;
+                        py += gc * dvy + dd * ry;
+                        pz += gc * dvz + dd * rz;
+                    }
+                }
+            }
+            a.add_block(px, py, pz);
+        }
+    V.w0[i] += V.scale * (a.x - a.cx);
+    V.w1[i] += V.scale * (a.y - a.cy);
+    V.w2[i] += V.scale * (a.z - a.cz);
+}
+
 __global__ void __launch_bounds__(PP_CTA, 3) pp_kernel(PPParams P) {
     __shared__ PPShared sh;
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -411,7 +504,24 @@ __global__ void __launch_bounds__(PP_CTA, 3) pp_kernel(PPParams P) {
 
 }  // namespace
 
-cudaError_t launch_pp(cube2_ctx *ctx, const cube2_particles *p, int accumulate, float kick) {
+static PPParams pp_params(cube2_ctx *ctx, const cube2_particles *p, int accumulate, float kick);
+
+cudaError_t launch_pp_vjp(cube2_ctx *ctx, const cube2_particles *p, const float *const v[3], float *const w[3]) {
+    if (ctx->N == 0) return cudaSuccess;
+    PPParams P = pp_params(ctx, p, 1, 0.0f);
+    VjpIO V{};
+    V.v0 = v[0]; V.v1 = v[1]; V.v2 = v[2];
+    V.w0 = w[0]; V.w1 = w[1]; V.w2 = w[2];
+    V.scale = (float)((double)P.coef / ctx->s_ios);
+    const int nblocks = (int)((ctx->N + PP_CTA - 1) / PP_CTA);
+    prep_positions_kernel<<<(unsigned)nblocks, PP_CTA, 0, ctx->stream>>>(p->off[0], p->off[1], p->off[2], ctx->cellid,
+                                                                       ctx->pos4, ctx->N);
+    pp_vjp_kernel<<<(unsigned)nblocks, PP_CTA, 0, ctx->stream>>>(P, V);
+    ctx->launches += 2;
+    return cudaGetLastError();
+}
+
+static PPParams pp_params(cube2_ctx *ctx, const cube2_particles *p, int accumulate, float kick) {
     PPParams P{};
     P.pos = ctx->pos4;
     P.count = p->count; P.start = p->start;
@@ -430,6 +540,11 @@ cudaError_t launch_pp(cube2_ctx *ctx, const cube2_particles *p, int accumulate, 
     P.coef = (float)(vp / (4.0 * 3.14159265358979323846) / (s * s));
     P.kick = kick;
     P.status = ctx->dev_status;
+    return P;
+}
+
+cudaError_t launch_pp(cube2_ctx *ctx, const cube2_particles *p, int accumulate, float kick) {
+    PPParams P = pp_params(ctx, p, accumulate, kick);
     if (ctx->N == 0) return cudaSuccess;
     const int nblocks = (int)((ctx->N + PP_CTA - 1) / PP_CTA);
     {

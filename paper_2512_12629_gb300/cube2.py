@@ -92,6 +92,8 @@ def _load():
         "cube2_profile_class_name": (ctypes.c_char_p, [I]),
         "cube2_pp_stats": (I, [P, ctypes.POINTER(ctypes.c_int64)]),
         "cube2_solve_pm_noalloc": (I, [P, P, P, ctypes.c_int32, P]),
+        "cube2_adjoint_init": (I, [P]),
+        "cube2_force_vjp": (I, [P, ctypes.POINTER(Particles), P, P]),
         "cube2_lpt_partition": (I, [ctypes.POINTER(D), I, I, ctypes.POINTER(I)]),
         "cube2_config_cost": (I, [ctypes.POINTER(Config), ctypes.POINTER(D)]),
         "cube2_ensemble_create": (I, [ctypes.POINTER(P), P, P, I, ctypes.POINTER(D), I, I]),
@@ -233,6 +235,18 @@ class Context:
 
     def force(self, p: IOSState):
         self._chk(_lib.cube2_force(self.ptr, ctypes.byref(p.struct())))
+
+    def adjoint_init(self):
+        self._chk(_lib.cube2_adjoint_init(self.ptr))
+
+    def force_vjp(self, p: IOSState, v: torch.Tensor, out: torch.Tensor = None):
+        """w = d<v, F>/dx for a cotangent v (3, N) FP32 on the device; returns w (3, N)."""
+        if out is None:
+            out = torch.empty_like(v)
+        vp = (ctypes.c_void_p * 3)(*[v[d].data_ptr() for d in range(3)])
+        wp = (ctypes.c_void_p * 3)(*[out[d].data_ptr() for d in range(3)])
+        self._chk(_lib.cube2_force_vjp(self.ptr, ctypes.byref(p.struct()), vp, wp))
+        return out
 
     def kdk_step(self, p: IOSState, a0, a1):
         self._chk(_lib.cube2_kdk_step(self.ptr, ctypes.byref(p.struct()), float(a0), float(a1)))
@@ -417,3 +431,11 @@ def force(ctx: Context, p: IOSState):
 
 def kdk_step(ctx: Context, p: IOSState, a0, a1):
     ctx.kdk_step(p, a0, a1)
+
+
+def adjoint_init(ctx: Context):
+    ctx.adjoint_init()
+
+
+def force_vjp(ctx: Context, p: IOSState, v, out=None):
+    return ctx.force_vjp(p, v, out)

@@ -1,0 +1,86 @@
+"""cube2_force_vjp (CUDA path through the C ABI) against the FP64 adjoint
+oracle, element by element, at the stored IOS positions.
+
+Tolerance: the force's own bar.  With r_i = |w_gpu - w_or| / max(|w_or|,
+1e-3 rms|w_or|): median <= 1e-5 and 99.9th percentile <= 1e-3 (the product
+is FP32 arithmetic of the same depth as the force: one FFT solve per term,
+CIC sums, pair sums; its cotangent deposit uses FP32 atomics in arbitrary
+order, which moves only the last bits)."""
+import numpy as np
+import pytest
+
+from inputs import C1, C2_SMALL
+from inputs.workloads import Level
+from inputs.zeldovich import random_ios, zeldovich_ios
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+from oracle import adjoint as A  # noqa: E402
+from oracle import kdk as okdk  # noqa: E402
+from oracle import mesh as omesh  # noqa: E402
+from paper_2512_12629_gb300 import cube2  # noqa: E402
+
+CLUSTER = C1.with_(name="clustered", n_ios=16, levels=(Level(32, 2.0),), b_pp=0.4)
+
+
+def _case(name):
+    if name == "C1":
+        return C1, zeldovich_ios(C1)
+    if name == "C2_SMALL":
+        return C2_SMALL, zeldovich_ios(C2_SMALL)
+    if name == "CLUSTER":
+        return CLUSTER, random_ios(5000, 16, CLUSTER.box, seed=32, clustered=0.8)
+    raise KeyError(name)
+
+
+def _oracle_vjp(w, st, v):
+    x = omesh.positions(st["off"], st["count"], w.n_ios, w.box)
+    n_part = x.shape[1]
+    out = np.zeros_like(x)
+    for (n, _h, _bs, _bt), g in zip(omesh.level_params(w), omesh.green_tables(w)):
+        out += A.pm_vjp_level(x, v, w.box, n, n_part, g)
+    b_pp, b_cut = okdk.pp_params(w)
+    return out + A.pp_vjp_cells(st["off"], st["count"], st["start"], w.n_ios, w.box, b_pp, b_cut, v)
+
+
+@pytest.mark.parametrize("name", ["C1", "C2_SMALL", "CLUSTER"])
+def test_force_vjp_matches_oracle(name):
+    w, st = _case(name)
+    n_part = int(st["count"].sum())
+    ctx = cube2.init_mesh(cube2.make_config(w, n_particles=n_part))
+    for l in range(len(w.levels)):
+        ctx.set_green(l)
+    ctx.adjoint_init()
+    p = cube2.IOSState.from_numpy(st)
+    v = np.random.default_rng(3).normal(size=(3, n_part))
+    got = ctx.force_vjp(p, torch.from_numpy(v.astype(np.float32)).cuda()).cpu().numpy().astype(np.float64)
+    ctx.check()
+    ref = _oracle_vjp(w, st, v)
+    err = np.linalg.norm(got - ref, axis=0)
+    mag = np.linalg.norm(ref, axis=0)
+    rel = err / np.maximum(mag, 1e-3 * np.sqrt(np.mean(mag ** 2)))
+    med, p999 = np.median(rel), np.quantile(rel, 0.999)
+    print(f"{name}: median {med:.2e} p99.9 {p999:.2e} max {rel.max():.2e}")
+    assert med <= 1e-5 and p999 <= 1e-3, (med, p999)
+
+
+def test_force_vjp_needs_init_and_is_linear():
+    w, st = _case("C1")
+    n_part = int(st["count"].sum())
+    ctx = cube2.init_mesh(cube2.make_config(w, n_particles=n_part))
+    ctx.set_green(0)
+    p = cube2.IOSState.from_numpy(st)
+    v = torch.randn(3, n_part, device="cuda", generator=torch.Generator("cuda").manual_seed(1))
+    with pytest.raises(cube2.Cube2Error):
+        ctx.force_vjp(p, v)
+    ctx.adjoint_init()
+    w1 = ctx.force_vjp(p, v)
+    w2 = ctx.force_vjp(p, 2.0 * v)
+    w3 = ctx.force_vjp(p, torch.zeros_like(v))
+    ctx.check()
+    assert torch.allclose(w2, 2.0 * w1, rtol=1e-4, atol=1e-4 * w1.abs().max().item())
+    assert w3.abs().max().item() == 0.0

@@ -91,3 +91,12 @@ def test_total_force_vjp_two_levels():
     e = rng.normal(size=(3, npart))
     fd = _directional(lambda y: A.force(y, w, greens), x, v, e, 1e-6)
     assert abs((wv * e).sum() - fd) <= 1e-6 * (np.abs(wv).sum() + abs(fd))
+
+
+def test_cell_list_pp_vjp_equals_all_pairs():
+    st = random_ios(3000, 8, 8.0, seed=21, clustered=0.6)
+    x = M.positions(st["off"], st["count"], 8, 8.0)
+    v = np.random.default_rng(2).normal(size=x.shape)
+    ref = A.pp_vjp(x, v, 8.0, x.shape[1], 0.12, 1.0)
+    got = A.pp_vjp_cells(st["off"], st["count"], st["start"], 8, 8.0, 0.12, 1.0, v)
+    assert np.allclose(got, ref, rtol=1e-10, atol=1e-10 * np.abs(ref).max())
