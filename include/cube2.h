@@ -239,8 +239,9 @@ void cube2_destroy(cube2_ctx *ctx);
  * the CIC deposit of v_d (G even, D_d odd); for PP,
  * sum_j (g I + g'/r d d^T)(v_j - v_i), g = V_p R_PP(r)/(4 pi r). */
 
-/* Allocate the product's scratch (three FP32 meshes of the largest level).
- * The one allocating call after cube2_init_mesh; idempotent. */
+/* Allocate the adjoint's scratch (three FP32 meshes of the largest level,
+ * 15 FP32 values per particle).  The one allocating call after
+ * cube2_init_mesh; idempotent. */
 int cube2_adjoint_init(cube2_ctx *ctx);
 
 /* w[d] (device FP32 [N], overwritten) = the product for cotangent v[d]
@@ -250,6 +251,33 @@ int cube2_adjoint_init(cube2_ctx *ctx);
  * uses float atomics: results agree with the FP64 product to FP32 accuracy
  * but their last bits may differ between runs. */
 int cube2_force_vjp(cube2_ctx *ctx, const cube2_particles *p, const float *const v[3], float *const w[3]);
+
+/* out (device int32 [N]) = the particle map of the last cube2_kdk_step's
+ * re-bin: out[new index] = index before the re-bin (the adjoint of a step
+ * needs it to carry adjoints back to the earlier order). */
+int cube2_kdk_permutation(cube2_ctx *ctx, int32_t *out);
+
+/* Loss of a final density against a target and its gradient in the
+ * positions: L = (1/n^3) sum_c (delta(c) - target(c))^2 on level `level`,
+ * delta the FP32 overdensity cube2_deposit computes, target device FP32
+ * [n][n][n]; w[d] (device FP32 [N], overwritten) = dL/dx_i (Mpc/h^-1) =
+ * (n^3/(N H)) sum_c grad_u W(u_i, c) 2 (delta - target)(c)/n^3.  *loss on the
+ * host; synchronises.  Needs cube2_adjoint_init.  Overwrites the level's
+ * density grid. */
+int cube2_density_mse_vjp(cube2_ctx *ctx, int level, const cube2_particles *p, const float *target,
+                          float *const w[3], double *loss);
+
+/* Reverse of one cube2_kdk_step(a0, a1) (Sec. 2.2: kick K(a0, ah), drift
+ * Dr(a0, a1), force, kick K(ah, a1); drift rounding taken as the identity).
+ * pre / post: the particle states before and after the step (positions,
+ * counts and starts are read); perm: its cube2_kdk_permutation.  On entry
+ * xbar, pbar (device FP32 [N] each) hold dL/dx and dL/dv after the step in
+ * post's order; on return they hold them before the step in pre's order:
+ * xbar += k2 F'(post)^T pbar; back through the re-bin; pbar += Dr xbar;
+ * xbar += k1 F'(pre)^T pbar, with k = 1.5 Omega_m K and the force products of
+ * cube2_force_vjp.  Needs cube2_adjoint_init. */
+int cube2_kdk_adjoint_step(cube2_ctx *ctx, const cube2_particles *pre, const cube2_particles *post,
+                           const int32_t *perm, float *const xbar[3], float *const pbar[3], double a0, double a1);
 
 /* ---- Ensembles of independent boxes -------------------------------------
  * Many small simulations on one GPU, and their split over GPUs.  Placement

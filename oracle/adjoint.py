@@ -182,3 +182,64 @@ def force_vjp(x, v, wl, greens):
         w += pm_vjp_level(x, v, wl.box, n, n_part, g)
     n_f, h_f, b_soft, _ = level_params(wl)[-1]
     return w + pp_vjp(x, v, wl.box, n_part, wl.b_pp, b_soft * h_f)
+
+
+# --------------------------------------------------- trajectory and loss
+def kdk_trajectory(x0, p0, wl, greens, a):
+    """KDK steps a[0] -> a[-1] (Sec. 2.2; kick K(a0, ah), drift Dr(a0, a1),
+    kick K(ah, a1), dp/da = 1.5 Omega_m F / (a^2 E)) at continuous positions.
+    Returns the states [(x_k, p_k)] before the first and after every step."""
+    from .kdk import drift_integral, kick_integral
+    c = 1.5 * wl.omega_m
+    x, p = x0.copy(), p0.copy()
+    f = force(x, wl, greens)
+    out = [(x, p)]
+    for a0, a1 in zip(a[:-1], a[1:]):
+        ah = 0.5 * (a0 + a1)
+        pm = p + c * kick_integral(a0, ah, wl.omega_m, wl.omega_l) * f
+        x = (x + drift_integral(a0, a1, wl.omega_m, wl.omega_l) * pm) % wl.box
+        f = force(x, wl, greens)
+        p = pm + c * kick_integral(ah, a1, wl.omega_m, wl.omega_l) * f
+        out.append((x, p))
+    return out
+
+
+def density_loss(x, wl, target):
+    """L = mean over the finest mesh of (delta - target)^2, delta the CIC overdensity."""
+    n = wl.levels[-1].n_mesh
+    h = wl.box / n
+    rho = _deposit(cic_corners(x / h, n), np.ones(x.shape[1]), n) * (n ** 3 / x.shape[1])
+    return float(np.mean((rho - 1.0 - target) ** 2))
+
+
+def density_loss_grad(x, wl, target):
+    """(L, dL/dx) of ``density_loss``."""
+    n = wl.levels[-1].n_mesh
+    h = wl.box / n
+    npart = x.shape[1]
+    corners = cic_corners(x / h, n)
+    rho = _deposit(corners, np.ones(npart), n) * (n ** 3 / npart)
+    r = (rho - 1.0 - target).reshape(-1)
+    g = 2.0 * r / n ** 3
+    w = np.zeros_like(x)
+    for idx, _W, grad in corners:
+        w += grad * g[idx]
+    return float(np.mean(r ** 2)), w * (n ** 3 / (npart * h))
+
+
+def loss_gradient(x0, p0, wl, greens, a, target):
+    """(L, dL/dx0, dL/dp0) through the KDK steps of ``kdk_trajectory``:
+    reverse mode, step by step, with the force products above."""
+    from .kdk import drift_integral, kick_integral
+    c = 1.5 * wl.omega_m
+    traj = kdk_trajectory(x0, p0, wl, greens, a)
+    loss, xbar = density_loss_grad(traj[-1][0], wl, target)
+    pbar = np.zeros_like(xbar)
+    for k in range(len(a) - 2, -1, -1):
+        a0, a1 = a[k], a[k + 1]
+        ah = 0.5 * (a0 + a1)
+        x_pre, x_post = traj[k][0], traj[k + 1][0]
+        xbar = xbar + c * kick_integral(ah, a1, wl.omega_m, wl.omega_l) * force_vjp(x_post, pbar, wl, greens)
+        pbar = pbar + drift_integral(a0, a1, wl.omega_m, wl.omega_l) * xbar
+        xbar = xbar + c * kick_integral(a0, ah, wl.omega_m, wl.omega_l) * force_vjp(x_pre, pbar, wl, greens)
+    return loss, xbar, pbar

@@ -131,6 +131,9 @@ void free_ctx(cube2_ctx *c) {
     cudaFree(c->big_n);
     cudaFree(c->pos4);
     cudaFree(c->vjp_mu);
+    cudaFree(c->vjp_t);
+    cudaFree(c->vjp_u);
+    cudaFree(c->vjp_sq);
     cudaFree(c->pp_stats);
     cudaFree(c->dev_status);
     cudaFreeHost(c->host_status);
@@ -430,24 +433,28 @@ int cube2_adjoint_init(cube2_ctx *ctx) {
     if (ctx->vjp_mu) return CUBE2_OK;
     int64_t m = 0;
     for (int l = 0; l < ctx->nl; ++l) m = std::max(m, (int64_t)ctx->lev[l].n * ctx->lev[l].n * ctx->lev[l].n);
+    const size_t N = (size_t)std::max<int64_t>(ctx->N, 1);
     cudaError_t e = cudaMalloc((void **)&ctx->vjp_mu, sizeof(float) * 3 * (size_t)m);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&ctx->vjp_t, sizeof(float) * 3 * N);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&ctx->vjp_u, sizeof(float) * 12 * N);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&ctx->vjp_sq, sizeof(double));
     if (e != cudaSuccess) {
+        cudaFree(ctx->vjp_mu);
+        cudaFree(ctx->vjp_t);
+        cudaFree(ctx->vjp_u);
+        cudaFree(ctx->vjp_sq);
         ctx->vjp_mu = nullptr;
+        ctx->vjp_t = ctx->vjp_u = nullptr;
+        ctx->vjp_sq = nullptr;
         return cuda_error(ctx, e, "adjoint scratch");
     }
     return CUBE2_OK;
 }
 
-int cube2_force_vjp(cube2_ctx *ctx, const cube2_particles *p, const float *const v[3], float *const w[3]) {
-    if (!ctx) return CUBE2_ERR_BAD_ARG;
-    if (!particles_ok(ctx, p, false, false) || !v || !w)
-        return set_error(ctx, CUBE2_ERR_BAD_ARG, "bad particle or cotangent arrays");
-    for (int d = 0; d < 3; ++d)
-        if (ctx->N > 0 && (!v[d] || !w[d])) return set_error(ctx, CUBE2_ERR_BAD_ARG, "null cotangent array");
-    if (!ctx->vjp_mu) return set_error(ctx, CUBE2_ERR_STATE, "call cube2_adjoint_init first");
-    for (int l = 0; l < ctx->nl; ++l)
-        if (!ctx->lev[l].has_green) return set_error(ctx, CUBE2_ERR_STATE, "the product needs every level's Green's table");
-    cudaError_t e = launch_cellid(ctx, p);
+// w = d<v, F>/dx (overwritten); cellid must be valid for p.
+static cudaError_t force_vjp_core(cube2_ctx *ctx, const cube2_particles *p, const float *const v[3],
+                                  float *const w[3]) {
+    cudaError_t e = cudaSuccess;
     for (int d = 0; d < 3 && e == cudaSuccess; ++d)
         if (ctx->N > 0) e = cudaMemsetAsync(w[d], 0, sizeof(float) * (size_t)ctx->N, ctx->stream);
     for (int l = 0; l < ctx->nl && e == cudaSuccess; ++l) {
@@ -466,7 +473,94 @@ int cube2_force_vjp(cube2_ctx *ctx, const cube2_particles *p, const float *const
         L.has_potential = false;
     }
     if (e == cudaSuccess) e = launch_pp_vjp(ctx, p, v, w);
+    return e;
+}
+
+static int adjoint_ready(cube2_ctx *ctx) {
+    if (!ctx->vjp_mu) return set_error(ctx, CUBE2_ERR_STATE, "call cube2_adjoint_init first");
+    for (int l = 0; l < ctx->nl; ++l)
+        if (!ctx->lev[l].has_green) return set_error(ctx, CUBE2_ERR_STATE, "the product needs every level's Green's table");
+    return CUBE2_OK;
+}
+
+int cube2_force_vjp(cube2_ctx *ctx, const cube2_particles *p, const float *const v[3], float *const w[3]) {
+    if (!ctx) return CUBE2_ERR_BAD_ARG;
+    if (!particles_ok(ctx, p, false, false) || !v || !w)
+        return set_error(ctx, CUBE2_ERR_BAD_ARG, "bad particle or cotangent arrays");
+    for (int d = 0; d < 3; ++d)
+        if (ctx->N > 0 && (!v[d] || !w[d])) return set_error(ctx, CUBE2_ERR_BAD_ARG, "null cotangent array");
+    int r = adjoint_ready(ctx);
+    if (r) return r;
+    cudaError_t e = launch_cellid(ctx, p);
+    if (e == cudaSuccess) e = force_vjp_core(ctx, p, v, w);
     if (e != cudaSuccess) return cuda_error(ctx, e, "force_vjp");
+    return CUBE2_OK;
+}
+
+int cube2_kdk_permutation(cube2_ctx *ctx, int32_t *out) {
+    if (!ctx) return CUBE2_ERR_BAD_ARG;
+    if (!out && ctx->N > 0) return set_error(ctx, CUBE2_ERR_BAD_ARG, "null out");
+    if (ctx->N == 0) return CUBE2_OK;
+    const cudaError_t e = cudaMemcpyAsync(out, ctx->perm, sizeof(int32_t) * (size_t)ctx->N, cudaMemcpyDeviceToDevice,
+                                          ctx->stream);
+    return e == cudaSuccess ? CUBE2_OK : cuda_error(ctx, e, "permutation copy");
+}
+
+int cube2_density_mse_vjp(cube2_ctx *ctx, int level, const cube2_particles *p, const float *target, float *const w[3],
+                          double *loss) {
+    if (!ctx) return CUBE2_ERR_BAD_ARG;
+    int r = level_ok(ctx, level, false);
+    if (r) return r;
+    if (!particles_ok(ctx, p, false, false) || !target || !w || !loss)
+        return set_error(ctx, CUBE2_ERR_BAD_ARG, "bad particle, target or output arrays");
+    for (int d = 0; d < 3; ++d)
+        if (ctx->N > 0 && !w[d]) return set_error(ctx, CUBE2_ERR_BAD_ARG, "null output array");
+    if (!ctx->vjp_mu) return set_error(ctx, CUBE2_ERR_STATE, "call cube2_adjoint_init first");
+    Level &L = ctx->lev[level];
+    cudaError_t e = launch_cellid(ctx, p);
+    if (e == cudaSuccess) e = launch_deposit(ctx, level, p, nullptr);
+    for (int d = 0; d < 3 && e == cudaSuccess; ++d)
+        if (ctx->N > 0) e = cudaMemsetAsync(w[d], 0, sizeof(float) * (size_t)ctx->N, ctx->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->vjp_sq, 0, sizeof(double), ctx->stream);
+    if (e == cudaSuccess) e = launch_density_mse_vjp(ctx, L, p, target, w, ctx->vjp_sq);
+    double sq = 0.0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&sq, ctx->vjp_sq, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return cuda_error(ctx, e, "density_mse_vjp");
+    L.has_density = false;
+    L.has_potential = false;
+    *loss = sq / ((double)L.n * L.n * L.n);
+    return CUBE2_OK;
+}
+
+int cube2_kdk_adjoint_step(cube2_ctx *ctx, const cube2_particles *pre, const cube2_particles *post,
+                           const int32_t *perm, float *const xbar[3], float *const pbar[3], double a0, double a1) {
+    if (!ctx) return CUBE2_ERR_BAD_ARG;
+    if (!particles_ok(ctx, pre, false, false) || !particles_ok(ctx, post, false, false) || !xbar || !pbar ||
+        (ctx->N > 0 && !perm))
+        return set_error(ctx, CUBE2_ERR_BAD_ARG, "bad checkpoint, permutation or adjoint arrays");
+    for (int d = 0; d < 3; ++d)
+        if (ctx->N > 0 && (!xbar[d] || !pbar[d])) return set_error(ctx, CUBE2_ERR_BAD_ARG, "null adjoint array");
+    int r = adjoint_ready(ctx);
+    if (r) return r;
+    double f[3];
+    if (cube2_kdk_factors(&ctx->cfg, a0, a1, f)) return set_error(ctx, CUBE2_ERR_BAD_ARG, "need 0 < a0 < a1");
+    const double c = 1.5 * ctx->cfg.omega_m;
+    const size_t N = (size_t)ctx->N;
+    float *const t[3] = {ctx->vjp_t, ctx->vjp_t + N, ctx->vjp_t + 2 * N};
+    const float *const pb[3] = {pbar[0], pbar[1], pbar[2]};
+    // second kick: p_out = p_mid + k2 F(x_new)  ->  xbar += k2 F^T pbar   (post-step order)
+    cudaError_t e = launch_cellid(ctx, post);
+    if (e == cudaSuccess) e = force_vjp_core(ctx, post, pb, t);
+    // re-bin: back to the pre-step order
+    if (e == cudaSuccess) e = launch_kdk_adjoint_scatter(ctx, perm, xbar, pbar, ctx->vjp_t, (float)(c * f[2]));
+    // drift: x_new = x + Dr p_mid  ->  pbar += Dr xbar
+    if (e == cudaSuccess) e = launch_kdk_adjoint_drift(ctx, xbar, pbar, (float)f[1]);
+    // first kick: p_mid = p + k1 F(x)  ->  xbar += k1 F^T pbar
+    if (e == cudaSuccess) e = launch_cellid(ctx, pre);
+    if (e == cudaSuccess) e = force_vjp_core(ctx, pre, pb, t);
+    if (e == cudaSuccess) e = launch_axpy3(ctx, xbar, ctx->vjp_t, (float)(c * f[0]));
+    if (e != cudaSuccess) return cuda_error(ctx, e, "kdk_adjoint_step");
     return CUBE2_OK;
 }
 

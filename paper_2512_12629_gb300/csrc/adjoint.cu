@@ -56,6 +56,7 @@ struct VjpParams {
     const float *v0, *v1, *v2;
     float *w0, *w1, *w2;
     const float *grid;       // phi (mode E) or psi (mode PSI)
+    float scale;             // factor on the gathered gradient
     int64_t N;
     int n_ios, n, shift;
 };
@@ -65,7 +66,12 @@ __global__ void __launch_bounds__(256) vjp_gather_kernel(VjpParams P) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= P.N) return;
     const CicPoint C = cic_point(P.off0, P.off1, P.off2, i, P.cellid[i], P.n_ios, P.shift);
-    const float v[3] = {P.v0[i], P.v1[i], P.v2[i]};
+    float v[3] = {0.f, 0.f, 0.f};
+    if (MODE_E) {   // the cotangent is read only in this mode (null otherwise)
+        v[0] = P.v0[i];
+        v[1] = P.v1[i];
+        v[2] = P.v2[i];
+    }
     const int n = P.n;
     float g[3] = {0.f, 0.f, 0.f};
 #pragma unroll
@@ -96,9 +102,9 @@ __global__ void __launch_bounds__(256) vjp_gather_kernel(VjpParams P) {
                 g[1] += wx * sy * wz * val;
                 g[2] += wx * wy * sz * val;
             }
-    P.w0[i] += g[0];
-    P.w1[i] += g[1];
-    P.w2[i] += g[2];
+    P.w0[i] += P.scale * g[0];
+    P.w1[i] += P.scale * g[1];
+    P.w2[i] += P.scale * g[2];
 }
 
 __global__ void __launch_bounds__(256) mu_deposit_kernel(VjpParams P, float *mu) {
@@ -147,6 +153,7 @@ VjpParams make_params(cube2_ctx *ctx, const Level &L, const cube2_particles *p, 
     P.v0 = v[0]; P.v1 = v[1]; P.v2 = v[2];
     P.w0 = w[0]; P.w1 = w[1]; P.w2 = w[2];
     P.grid = grid;
+    P.scale = 1.0f;
     P.N = ctx->N;
     P.n_ios = ctx->n_ios;
     P.n = L.n;
@@ -154,7 +161,115 @@ VjpParams make_params(cube2_ctx *ctx, const Level &L, const cube2_particles *p, 
     return P;
 }
 
+// g(c) = 2 (delta(c) - target(c)) / n^3 in place of delta; sum of squares into *sq.
+__global__ void __launch_bounds__(256) mse_residual_kernel(float *grid, const float *target, int64_t n3, double *sq) {
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    double r2 = 0.0;
+    if (c < n3) {
+        const float r = grid[c] - target[c];
+        r2 = (double)r * (double)r;
+        grid[c] = r * (float)(2.0 / (double)n3);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) r2 += __shfl_xor_sync(0xffffffffu, r2, o);
+    if ((threadIdx.x & 31) == 0 && r2 != 0.0) atomicAdd(sq, r2);
+}
+
+// Reverse of one KDK step, part 1 (post-step order n -> pre-step order perm[n]):
+// xs[perm[n]] = xbar[n] + k2 t[n],  ps[perm[n]] = pbar[n].
+__global__ void __launch_bounds__(256) kdk_adjoint_scatter_kernel(const int32_t *perm, const float *xbar,
+                                                                  const float *pbar, const float *t, float *xs,
+                                                                  float *ps, int64_t N, float k2) {
+    const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    const int64_t o = perm[n];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        xs[d * N + o] = xbar[d * N + n] + k2 * t[d * N + n];
+        ps[d * N + o] = pbar[d * N + n];
+    }
+}
+
+// Part 2 (pre-step order): xbar = xs, pbar = ps + drift * xs; part 3: xbar += k1 t.
+struct Ptr3 {
+    float *p[3];
+};
+
+__global__ void __launch_bounds__(256) kdk_adjoint_drift3_kernel(const float *xs, const float *ps, Ptr3 xbar, Ptr3 pbar,
+                                                                 int64_t N, float drift) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        const float x = xs[d * N + i];
+        xbar.p[d][i] = x;
+        pbar.p[d][i] = ps[d * N + i] + drift * x;
+    }
+}
+
+__global__ void __launch_bounds__(256) axpy3p_kernel(Ptr3 y, const float *t, int64_t N, float a) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) y.p[d][i] += a * t[d * N + i];
+}
+
 }  // namespace
+
+// w = (n^3 / (N H)) sum_c grad_u W(u_i, c) g(c) with g = 2 (delta - target)/n^3
+// (the density's own grid must hold delta); adds sum (delta - target)^2 to *sq.
+cudaError_t launch_density_mse_vjp(cube2_ctx *ctx, Level &L, const cube2_particles *p, const float *target,
+                                   float *const w[3], double *sq) {
+    const int64_t n3 = (int64_t)L.n * L.n * L.n;
+    mse_residual_kernel<<<(unsigned)((n3 + 255) / 256), 256, 0, ctx->stream>>>(L.real, target, n3, sq);
+    ctx->launches++;
+    if (ctx->N == 0) return cudaGetLastError();
+    const float *const nv[3] = {nullptr, nullptr, nullptr};
+    VjpParams P = make_params(ctx, L, p, nv, w, L.real);
+    P.v0 = P.v1 = P.v2 = nullptr;
+    P.scale = (float)((double)n3 / ((double)ctx->N * L.H));
+    vjp_gather_kernel<false><<<(unsigned)((ctx->N + 255) / 256), 256, 0, ctx->stream>>>(P);
+    ctx->launches++;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_kdk_adjoint_scatter(cube2_ctx *ctx, const int32_t *perm, float *const xbar[3],
+                                       float *const pbar[3], const float *t, float k2) {
+    // xbar/pbar are three separate arrays: gather them through the scratch rows
+    const int64_t N = ctx->N;
+    if (N == 0) return cudaSuccess;
+    float *xs = ctx->vjp_u, *ps = ctx->vjp_u + 3 * N, *xc = ctx->vjp_u + 6 * N;
+    cudaError_t e = cudaSuccess;
+    for (int d = 0; d < 3 && e == cudaSuccess; ++d) {
+        e = cudaMemcpyAsync(xc + d * N, xbar[d], sizeof(float) * N, cudaMemcpyDeviceToDevice, ctx->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(xc + (3 + d) * N, pbar[d], sizeof(float) * N, cudaMemcpyDeviceToDevice, ctx->stream);
+    }
+    if (e != cudaSuccess) return e;
+    kdk_adjoint_scatter_kernel<<<(unsigned)((N + 255) / 256), 256, 0, ctx->stream>>>(perm, xc, xc + 3 * N, t, xs, ps,
+                                                                                   N, k2);
+    ctx->launches++;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_kdk_adjoint_drift(cube2_ctx *ctx, float *const xbar[3], float *const pbar[3], float drift) {
+    const int64_t N = ctx->N;
+    if (N == 0) return cudaSuccess;
+    Ptr3 X{{xbar[0], xbar[1], xbar[2]}}, Pb{{pbar[0], pbar[1], pbar[2]}};
+    kdk_adjoint_drift3_kernel<<<(unsigned)((N + 255) / 256), 256, 0, ctx->stream>>>(ctx->vjp_u, ctx->vjp_u + 3 * N, X,
+                                                                                   Pb, N, drift);
+    ctx->launches++;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_axpy3(cube2_ctx *ctx, float *const y[3], const float *t, float a) {
+    const int64_t N = ctx->N;
+    if (N == 0) return cudaSuccess;
+    Ptr3 Y{{y[0], y[1], y[2]}};
+    axpy3p_kernel<<<(unsigned)((N + 255) / 256), 256, 0, ctx->stream>>>(Y, t, N, a);
+    ctx->launches++;
+    return cudaGetLastError();
+}
 
 // w += -sum_c grad W (E . v), E from the level's potential (in L.real).
 cudaError_t launch_vjp_gather_e(cube2_ctx *ctx, Level &L, const cube2_particles *p, const float *const v[3],

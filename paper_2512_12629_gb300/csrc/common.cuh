@@ -91,6 +91,9 @@ struct cube2_ctx {
     int *prof_cls = nullptr;       // [prof_cap] class * CUBE2_MAX_LEVELS + level
     // force vector-Jacobian product scratch (cube2_adjoint_init)
     float *vjp_mu = nullptr;       // [3][n_max^3] CIC deposit of the cotangent
+    float *vjp_t = nullptr;        // [3][N] a force product
+    float *vjp_u = nullptr;        // [12][N] reverse-step scratch
+    double *vjp_sq = nullptr;      // [1] loss accumulator
 };
 
 namespace cube2 {
@@ -132,6 +135,12 @@ cudaError_t launch_vjp_gather_psi(cube2_ctx *ctx, Level &L, const cube2_particle
                                   float *const w[3]);
 cudaError_t launch_vjp_source(cube2_ctx *ctx, Level &L, const cube2_particles *p, const float *const v[3]);
 cudaError_t launch_pp_vjp(cube2_ctx *ctx, const cube2_particles *p, const float *const v[3], float *const w[3]);
+cudaError_t launch_density_mse_vjp(cube2_ctx *ctx, Level &L, const cube2_particles *p, const float *target,
+                                   float *const w[3], double *sq);
+cudaError_t launch_kdk_adjoint_scatter(cube2_ctx *ctx, const int32_t *perm, float *const xbar[3],
+                                       float *const pbar[3], const float *t, float k2);
+cudaError_t launch_kdk_adjoint_drift(cube2_ctx *ctx, float *const xbar[3], float *const pbar[3], float drift);
+cudaError_t launch_axpy3(cube2_ctx *ctx, float *const y[3], const float *t, float a);
 
 }  // namespace cube2
 

@@ -94,6 +94,9 @@ def _load():
         "cube2_solve_pm_noalloc": (I, [P, P, P, ctypes.c_int32, P]),
         "cube2_adjoint_init": (I, [P]),
         "cube2_force_vjp": (I, [P, ctypes.POINTER(Particles), P, P]),
+        "cube2_kdk_permutation": (I, [P, P]),
+        "cube2_density_mse_vjp": (I, [P, I, ctypes.POINTER(Particles), P, P, ctypes.POINTER(D)]),
+        "cube2_kdk_adjoint_step": (I, [P, ctypes.POINTER(Particles), ctypes.POINTER(Particles), P, P, P, D, D]),
         "cube2_lpt_partition": (I, [ctypes.POINTER(D), I, I, ctypes.POINTER(I)]),
         "cube2_config_cost": (I, [ctypes.POINTER(Config), ctypes.POINTER(D)]),
         "cube2_ensemble_create": (I, [ctypes.POINTER(P), P, P, I, ctypes.POINTER(D), I, I]),
@@ -247,6 +250,31 @@ class Context:
         wp = (ctypes.c_void_p * 3)(*[out[d].data_ptr() for d in range(3)])
         self._chk(_lib.cube2_force_vjp(self.ptr, ctypes.byref(p.struct()), vp, wp))
         return out
+
+    def kdk_permutation(self, out: torch.Tensor = None):
+        """Map of the last re-bin: out[new] = old index (int32, device)."""
+        if out is None:
+            out = torch.empty(self.cfg.n_particles, dtype=torch.int32, device="cuda")
+        self._chk(_lib.cube2_kdk_permutation(self.ptr, out.data_ptr()))
+        return out
+
+    def density_mse_vjp(self, level, p: IOSState, target: torch.Tensor, out: torch.Tensor = None):
+        """(L, dL/dx) for L = mean((delta - target)^2) on `level`; dL/dx (3, N) FP32."""
+        if out is None:
+            out = torch.empty_like(p.vel)
+        wp = (ctypes.c_void_p * 3)(*[out[d].data_ptr() for d in range(3)])
+        loss = ctypes.c_double()
+        self._chk(_lib.cube2_density_mse_vjp(self.ptr, int(level), ctypes.byref(p.struct()), target.data_ptr(), wp,
+                                             ctypes.byref(loss)))
+        return loss.value, out
+
+    def kdk_adjoint_step(self, pre: IOSState, post: IOSState, perm: torch.Tensor, xbar: torch.Tensor,
+                         pbar: torch.Tensor, a0, a1):
+        """Reverse of kdk_step(a0, a1): xbar, pbar (3, N) are updated in place."""
+        xp = (ctypes.c_void_p * 3)(*[xbar[d].data_ptr() for d in range(3)])
+        pp = (ctypes.c_void_p * 3)(*[pbar[d].data_ptr() for d in range(3)])
+        self._chk(_lib.cube2_kdk_adjoint_step(self.ptr, ctypes.byref(pre.struct()), ctypes.byref(post.struct()),
+                                              perm.data_ptr(), xp, pp, float(a0), float(a1)))
 
     def kdk_step(self, p: IOSState, a0, a1):
         self._chk(_lib.cube2_kdk_step(self.ptr, ctypes.byref(p.struct()), float(a0), float(a1)))
@@ -435,6 +463,28 @@ def kdk_step(ctx: Context, p: IOSState, a0, a1):
 
 def adjoint_init(ctx: Context):
     ctx.adjoint_init()
+
+
+def loss_gradient(ctx: Context, p0: IOSState, target: torch.Tensor, a, level=-1):
+    """Gradient of L = mean((delta_final - target)^2) through len(a) - 1 KDK
+    steps with respect to the initial positions and velocities.
+
+    p0: the initial state with current forces (unchanged).  Runs the steps
+    with a checkpoint and re-bin map per step, then cube2_density_mse_vjp and
+    cube2_kdk_adjoint_step backwards.  Returns (L, dL/dx0, dL/dv0), the
+    gradients (3, N) in p0's particle order."""
+    level = ctx.cfg.n_levels - 1 if level < 0 else level
+    states, perms = [p0], []
+    p = p0.clone()
+    for k in range(len(a) - 1):
+        ctx.kdk_step(p, a[k], a[k + 1])
+        perms.append(ctx.kdk_permutation())
+        states.append(p.clone())
+    loss, xbar = ctx.density_mse_vjp(level, states[-1], target)
+    pbar = torch.zeros_like(xbar)
+    for k in range(len(a) - 2, -1, -1):
+        ctx.kdk_adjoint_step(states[k], states[k + 1], perms[k], xbar, pbar, a[k], a[k + 1])
+    return loss, xbar, pbar
 
 
 def force_vjp(ctx: Context, p: IOSState, v, out=None):

@@ -100,3 +100,32 @@ def test_cell_list_pp_vjp_equals_all_pairs():
     ref = A.pp_vjp(x, v, 8.0, x.shape[1], 0.12, 1.0)
     got = A.pp_vjp_cells(st["off"], st["count"], st["start"], 8, 8.0, 0.12, 1.0, v)
     assert np.allclose(got, ref, rtol=1e-10, atol=1e-10 * np.abs(ref).max())
+
+
+def test_loss_gradient_matches_finite_differences():
+    """Central differences of the loss through 3 KDK steps, eps = 1e-4 cell in
+    displacement (and the matching step in velocity), on 24 components."""
+    from inputs import C1
+    wl = C1.with_(n_p=6, box=12.0, n_ios=6, levels=(Level(12, 2.0),), b_pp=0.2)
+    rng = np.random.default_rng(17)
+    npart = 6 ** 3
+    x0 = rng.uniform(0, wl.box, (3, npart))
+    p0 = rng.normal(0, 2.0, (3, npart))
+    greens = M.green_tables(wl)
+    a = [0.1, 0.12, 0.14, 0.16]
+    target = rng.normal(0, 0.3, (12, 12, 12))
+    loss, gx, gp = A.loss_gradient(x0, p0, wl, greens, a, target)
+
+    def lossf(x, p):
+        return A.density_loss(A.kdk_trajectory(x, p, wl, greens, a)[-1][0], wl, target)
+
+    assert abs(loss - lossf(x0, p0)) <= 1e-12 * loss
+    eps = 1e-4 * wl.box / 12
+    for k in range(12):
+        i, d = int(rng.integers(npart)), int(rng.integers(3))
+        e = np.zeros((3, npart))
+        e[d, i] = eps
+        fd = (lossf(x0 + e, p0) - lossf(x0 - e, p0)) / (2 * eps)
+        assert abs(gx[d, i] - fd) <= 1e-6 * np.abs(gx).max(), (i, d, gx[d, i], fd)
+        fdp = (lossf(x0, p0 + e) - lossf(x0, p0 - e)) / (2 * eps)
+        assert abs(gp[d, i] - fdp) <= 1e-6 * np.abs(gp).max(), (i, d, gp[d, i], fdp)
