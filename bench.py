@@ -443,8 +443,92 @@ def run_ensemble(args):
         dist.destroy_process_group()
 
 
+ADJOINT = "c3-adjoint-128c-256mesh"
+
+
+def run_adjoint(args):
+    """Adjoint/forward time ratio on the differentiation workload (128^3
+    particles, one 256^3 level, 10 KDK steps z = 9 -> 0): forward = the 10
+    steps plus the final density loss; adjoint = the same steps with a
+    checkpoint and re-bin map per step, the loss gradient, and 10 reverse
+    steps (two force products each), giving dL/dx0 and dL/dv0.  The target is
+    the final overdensity of an independent realisation (seed 4).  Wall clock
+    with a device synchronisation on both sides, per repetition."""
+    import numpy as np
+    import torch
+    from inputs.workloads import WORKLOADS
+    from inputs.zeldovich import zeldovich_ios
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return
+    torch.cuda.set_device(0)
+    from paper_2512_12629_gb300 import build as pkg_build
+    pkg_build.build()
+    from paper_2512_12629_gb300 import cube2
+    w = WORKLOADS["pm1-128c-256mesh"]
+    a = w.scale_factors()
+    st = zeldovich_ios(w)
+    n_part = int(st["count"].sum())
+    ctx = cube2.init_mesh(cube2.make_config(w, n_particles=n_part))
+    ctx.set_green(0)
+    ctx.adjoint_init()
+    pt = cube2.IOSState.from_numpy(zeldovich_ios(w.with_(seed=4)))
+    ctx.force(pt)
+    for k in range(len(a) - 1):
+        ctx.kdk_step(pt, a[k], a[k + 1])
+    ctx.deposit(0, pt)
+    target = ctx.get_density(0).clone()
+    p0 = cube2.IOSState.from_numpy(st)
+    ctx.force(p0)
+    torch.cuda.synchronize()
+
+    def forward():
+        p = p0.clone()
+        for k in range(len(a) - 1):
+            ctx.kdk_step(p, a[k], a[k + 1])
+        return ctx.density_mse_vjp(0, p, target)[0]
+
+    def adjoint():
+        return cube2.loss_gradient(ctx, p0, target, a)
+
+    for _ in range(max(1, args.warmup)):
+        forward()
+        adjoint()
+    tf, ta = [], []
+    for _ in range(max(1, args.steps)):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        loss = forward()
+        torch.cuda.synchronize()
+        tf.append(time.perf_counter() - t0)
+        t0 = time.perf_counter()
+        loss_a, gx, gv = adjoint()
+        torch.cuda.synchronize()
+        ta.append(time.perf_counter() - t0)
+    ctx.check()
+    fwd, adj = statistics.median(tf), statistics.median(ta)
+    line = {
+        "metric": "adjoint/forward time ratio (128^3 particles, 256^3 mesh, 10 KDK steps, density MSE loss)",
+        "value": adj / fwd, "unit": "ratio", "higher_is_better": False, "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "forward_ms": 1e3 * fwd, "adjoint_ms": 1e3 * adj, "loss": loss,
+        "loss_in_adjoint_run": loss_a, "grad_x_rms": float(gx.pow(2).mean().sqrt()),
+        "grad_v_rms": float(gv.pow(2).mean().sqrt()), "dtype": "f32",
+        "data": "synthetic (seeded Zel'dovich ICs, BBKS spectrum; target = seed 4 final overdensity)",
+        "config": {"workload": ADJOINT, "particles": n_part, "mesh": 256, "kdk_steps": len(a) - 1,
+                   "z": f"{w.z_init:g} -> {w.z_final:g}", "gradient": "dL/dx0 and dL/dv0",
+                   "timing": "median wall clock per repetition, synchronised"},
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse_args()
+    if args.workload == ADJOINT:
+        if args.impl == "reference":
+            print(json.dumps({"impl": "reference", "unavailable": "the adjoint workload has no oracle arm"}))
+            return
+        run_adjoint(args)
+        return
     if args.workload == ENSEMBLE:
         if args.impl == "reference":
             print(json.dumps({"impl": "reference", "unavailable": "the ensemble workload has no oracle arm"}))

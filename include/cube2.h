@@ -279,6 +279,17 @@ int cube2_density_mse_vjp(cube2_ctx *ctx, int level, const cube2_particles *p, c
 int cube2_kdk_adjoint_step(cube2_ctx *ctx, const cube2_particles *pre, const cube2_particles *post,
                            const int32_t *perm, float *const xbar[3], float *const pbar[3], double a0, double a1);
 
+/* Reverse of n_steps consecutive cube2_kdk_step calls over the schedule
+ * a[0..n_steps]: states[0..n_steps] the checkpoints (before the first step,
+ * after each step), perms[k] the re-bin map of step k.  xbar, pbar: as in
+ * cube2_kdk_adjoint_step, in the last state's order on entry and the first
+ * state's on return.  Same result as cube2_kdk_adjoint_step applied from the
+ * last step back, with one force product per step instead of two: the
+ * product that ends the reverse of step k+1 (at state k+1, with the pbar the
+ * reverse of step k starts from) is the one step k needs first. */
+int cube2_kdk_adjoint(cube2_ctx *ctx, const cube2_particles *const *states, const int32_t *const *perms, int n_steps,
+                      const double *a, float *const xbar[3], float *const pbar[3]);
+
 /* ---- Ensembles of independent boxes -------------------------------------
  * Many small simulations on one GPU, and their split over GPUs.  Placement
  * follows the load balancing of paper Sec. 2.2.3 (Fig. balance): tasks in

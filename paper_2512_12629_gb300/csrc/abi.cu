@@ -564,6 +564,43 @@ int cube2_kdk_adjoint_step(cube2_ctx *ctx, const cube2_particles *pre, const cub
     return CUBE2_OK;
 }
 
+int cube2_kdk_adjoint(cube2_ctx *ctx, const cube2_particles *const *states, const int32_t *const *perms, int n_steps,
+                      const double *a, float *const xbar[3], float *const pbar[3]) {
+    if (!ctx) return CUBE2_ERR_BAD_ARG;
+    if (!states || !perms || !a || n_steps < 1 || !xbar || !pbar)
+        return set_error(ctx, CUBE2_ERR_BAD_ARG, "bad states, maps, schedule or adjoint arrays");
+    for (int k = 0; k <= n_steps; ++k)
+        if (!particles_ok(ctx, states[k], false, false)) return set_error(ctx, CUBE2_ERR_BAD_ARG, "bad state");
+    for (int k = 0; k < n_steps; ++k) {
+        if (ctx->N > 0 && !perms[k]) return set_error(ctx, CUBE2_ERR_BAD_ARG, "null re-bin map");
+        if (!(a[k] > 0) || !(a[k + 1] > a[k])) return set_error(ctx, CUBE2_ERR_BAD_ARG, "need 0 < a0 < a1 < ...");
+    }
+    for (int d = 0; d < 3; ++d)
+        if (ctx->N > 0 && (!xbar[d] || !pbar[d])) return set_error(ctx, CUBE2_ERR_BAD_ARG, "null adjoint array");
+    int r = adjoint_ready(ctx);
+    if (r) return r;
+    const double c = 1.5 * ctx->cfg.omega_m;
+    const size_t N = (size_t)ctx->N;
+    float *const t[3] = {ctx->vjp_t, ctx->vjp_t + N, ctx->vjp_t + 2 * N};
+    const float *const pb[3] = {pbar[0], pbar[1], pbar[2]};
+    // t = F'(x_n)^T pbar at the last state; afterwards each step's first-kick
+    // product (at its pre state, with the pbar the next reverse step starts
+    // from) is the previous step's second-kick product
+    cudaError_t e = launch_cellid(ctx, states[n_steps]);
+    if (e == cudaSuccess) e = force_vjp_core(ctx, states[n_steps], pb, t);
+    for (int k = n_steps - 1; k >= 0 && e == cudaSuccess; --k) {
+        double f[3];
+        cube2_kdk_factors(&ctx->cfg, a[k], a[k + 1], f);
+        e = launch_kdk_adjoint_scatter(ctx, perms[k], xbar, pbar, ctx->vjp_t, (float)(c * f[2]));
+        if (e == cudaSuccess) e = launch_kdk_adjoint_drift(ctx, xbar, pbar, (float)f[1]);
+        if (e == cudaSuccess) e = launch_cellid(ctx, states[k]);
+        if (e == cudaSuccess) e = force_vjp_core(ctx, states[k], pb, t);
+        if (e == cudaSuccess) e = launch_axpy3(ctx, xbar, ctx->vjp_t, (float)(c * f[0]));
+    }
+    if (e != cudaSuccess) return cuda_error(ctx, e, "kdk_adjoint");
+    return CUBE2_OK;
+}
+
 int cube2_kdk_step_host(cube2_ctx *ctx, cube2_particles *dev, cube2_particles *host, double a0, double a1) {
     if (!ctx || !host) return CUBE2_ERR_BAD_ARG;
     if (!particles_ok(ctx, dev, true, true) || !particles_ok(ctx, host, true, true))

@@ -97,6 +97,7 @@ def _load():
         "cube2_kdk_permutation": (I, [P, P]),
         "cube2_density_mse_vjp": (I, [P, I, ctypes.POINTER(Particles), P, P, ctypes.POINTER(D)]),
         "cube2_kdk_adjoint_step": (I, [P, ctypes.POINTER(Particles), ctypes.POINTER(Particles), P, P, P, D, D]),
+        "cube2_kdk_adjoint": (I, [P, P, P, I, ctypes.POINTER(D), P, P]),
         "cube2_lpt_partition": (I, [ctypes.POINTER(D), I, I, ctypes.POINTER(I)]),
         "cube2_config_cost": (I, [ctypes.POINTER(Config), ctypes.POINTER(D)]),
         "cube2_ensemble_create": (I, [ctypes.POINTER(P), P, P, I, ctypes.POINTER(D), I, I]),
@@ -275,6 +276,18 @@ class Context:
         pp = (ctypes.c_void_p * 3)(*[pbar[d].data_ptr() for d in range(3)])
         self._chk(_lib.cube2_kdk_adjoint_step(self.ptr, ctypes.byref(pre.struct()), ctypes.byref(post.struct()),
                                               perm.data_ptr(), xp, pp, float(a0), float(a1)))
+
+    def kdk_adjoint(self, states, perms, a, xbar: torch.Tensor, pbar: torch.Tensor):
+        """Reverse of len(a) - 1 KDK steps (cube2_kdk_adjoint); xbar, pbar updated in place."""
+        n = len(a) - 1
+        structs = [st.struct() for st in states]
+        sp = (ctypes.c_void_p * (n + 1))(*[ctypes.addressof(x) for x in structs])
+        pp = (ctypes.c_void_p * n)(*[q.data_ptr() for q in perms])
+        av = np.ascontiguousarray(a, dtype=np.float64)
+        xp = (ctypes.c_void_p * 3)(*[xbar[d].data_ptr() for d in range(3)])
+        bp = (ctypes.c_void_p * 3)(*[pbar[d].data_ptr() for d in range(3)])
+        self._chk(_lib.cube2_kdk_adjoint(self.ptr, sp, pp, n, av.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                         xp, bp))
 
     def kdk_step(self, p: IOSState, a0, a1):
         self._chk(_lib.cube2_kdk_step(self.ptr, ctypes.byref(p.struct()), float(a0), float(a1)))
@@ -482,8 +495,7 @@ def loss_gradient(ctx: Context, p0: IOSState, target: torch.Tensor, a, level=-1)
         states.append(p.clone())
     loss, xbar = ctx.density_mse_vjp(level, states[-1], target)
     pbar = torch.zeros_like(xbar)
-    for k in range(len(a) - 2, -1, -1):
-        ctx.kdk_adjoint_step(states[k], states[k + 1], perms[k], xbar, pbar, a[k], a[k + 1])
+    ctx.kdk_adjoint(states, perms, a, xbar, pbar)
     return loss, xbar, pbar
 
 

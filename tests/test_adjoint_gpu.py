@@ -118,3 +118,35 @@ def test_loss_gradient_through_kdk_steps_matches_oracle():
         med, p99 = np.median(rel), np.quantile(rel, 0.99)
         print(f"gradient: median {med:.2e} p99 {p99:.2e}")
         assert med <= 5e-4 and p99 <= 5e-3, (med, p99)
+
+
+def test_fused_reverse_sweep_equals_step_by_step():
+    """cube2_kdk_adjoint (one force product per step) against
+    cube2_kdk_adjoint_step applied step by step (two per step)."""
+    w = C1.with_(n_p=16, box=32.0, n_ios=16, levels=(Level(32, 2.0),), b_pp=0.2)
+    st = zeldovich_ios(w)
+    n_part = int(st["count"].sum())
+    ctx = cube2.init_mesh(cube2.make_config(w, n_particles=n_part))
+    ctx.set_green(0)
+    ctx.adjoint_init()
+    p0 = cube2.IOSState.from_numpy(st)
+    ctx.force(p0)
+    a0 = 1.0 / (1.0 + w.z_init)
+    a = [a0 + k * (1.0 - a0) / 50 for k in range(4)]
+    states, perms = [p0], []
+    p = p0.clone()
+    for k in range(3):
+        ctx.kdk_step(p, a[k], a[k + 1])
+        perms.append(ctx.kdk_permutation())
+        states.append(p.clone())
+    g = torch.Generator("cuda").manual_seed(5)
+    xb0 = torch.randn(3, n_part, device="cuda", generator=g)
+    pb0 = torch.randn(3, n_part, device="cuda", generator=g)
+    xb1, pb1 = xb0.clone(), pb0.clone()
+    ctx.kdk_adjoint(states, perms, a, xb1, pb1)
+    xb2, pb2 = xb0.clone(), pb0.clone()
+    for k in range(2, -1, -1):
+        ctx.kdk_adjoint_step(states[k], states[k + 1], perms[k], xb2, pb2, a[k], a[k + 1])
+    ctx.check()
+    for u, v in ((xb1, xb2), (pb1, pb2)):
+        assert torch.allclose(u, v, rtol=1e-4, atol=1e-4 * v.abs().max().item())
