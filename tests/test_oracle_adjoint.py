@@ -104,7 +104,8 @@ def test_cell_list_pp_vjp_equals_all_pairs():
 
 def test_loss_gradient_matches_finite_differences():
     """Central differences of the loss through 3 KDK steps, eps = 1e-4 cell in
-    displacement (and the matching step in velocity), on 24 components."""
+    displacement (and the matching step in velocity), on 64 random components
+    (32 positions, 32 velocities)."""
     from inputs import C1
     wl = C1.with_(n_p=6, box=12.0, n_ios=6, levels=(Level(12, 2.0),), b_pp=0.2)
     rng = np.random.default_rng(17)
@@ -121,7 +122,7 @@ def test_loss_gradient_matches_finite_differences():
 
     assert abs(loss - lossf(x0, p0)) <= 1e-12 * loss
     eps = 1e-4 * wl.box / 12
-    for k in range(12):
+    for k in range(32):
         i, d = int(rng.integers(npart)), int(rng.integers(3))
         e = np.zeros((3, npart))
         e[d, i] = eps
