@@ -362,6 +362,7 @@ __device__ void lane_path(const PPParams &P, bool has, int c, float4 me, Sum3 &a
             const float fdy = (float)dy, fdz = (float)dz;
             float px = 0.f, py = 0.f, pz = 0.f;
             for (int sgi = 0; sgi < rr.nseg; ++sgi) {
+#pragma unroll 4
                 for (int j = rr.beg[sgi]; j < rr.end[sgi]; ++j) {
                     const float4 q = __ldg(&P.pos[j]);
                     const float fdx = (float)(rr.base[sgi] + (j >= rr.b1[sgi]) + (j >= rr.b2[sgi]));
@@ -370,7 +371,8 @@ __device__ void lane_path(const PPParams &P, bool has, int c, float4 me, Sum3 &a
                     const float rz = (fdz + q.z) - me.z;
                     const float r2 = rx * rx + ry * ry + rz * rz;
                     if (r2 < bcut2 && r2 > 0.0f) {
-                        const float g = r2 >= bpp2 ? far_pair(r2, ibc, bpp2) : close_pair(r2, ibp, ibc);
+                        float g = far_pair(r2, ibc, bpp2);
+                        if (__builtin_expect(r2 < bpp2, 0)) g = close_pair(r2, ibp, ibc);   // rare
                         px = fmaf(g, rx, px);
                         py = fmaf(g, ry, py);
                         pz = fmaf(g, rz, pz);
