@@ -130,6 +130,7 @@ void free_ctx(cube2_ctx *c) {
     cudaFree(c->big);
     cudaFree(c->big_n);
     cudaFree(c->pos4);
+    cudaFree(c->pp_perm);
     cudaFree(c->vjp_mu);
     cudaFree(c->vjp_t);
     cudaFree(c->vjp_u);
@@ -247,6 +248,7 @@ int cube2_init_mesh(cube2_ctx **out, const cube2_config *cfg, void *stream) {
     alloc((void **)&c->big, (size_t)c->n_cells * 4);
     alloc((void **)&c->big_n, sizeof(int));
     alloc((void **)&c->pos4, N * 16);
+    alloc((void **)&c->pp_perm, N * 4);
     alloc((void **)&c->pp_stats, 2 * sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaMemsetAsync(c->pp_stats, 0, 2 * sizeof(unsigned long long), c->stream);
     cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device);

@@ -74,7 +74,8 @@ struct cube2_ctx {
     int32_t *perm2 = nullptr;      // [N] merge scratch of the segmented sort
     int32_t *big = nullptr;        // [n_cells] cells too large for the per-thread sort
     int *big_n = nullptr;          // their number
-    float4 *pos4 = nullptr;        // [N] in-cell offsets as floats (+ cell id bits)
+    float4 *pos4 = nullptr;        // [N] in-cell offsets as floats (+ cell id bits), PP order
+    int32_t *pp_perm = nullptr;    // [N] particle index of each PP slot (sub-cell order in dense cells)
     unsigned long long *pp_stats = nullptr;  // [2] in-range ordered pairs, candidates
     int num_sms = 152;
     int32_t *scan_tmp = nullptr;   // block sums of the multi-level scan
