@@ -216,7 +216,7 @@ def algorithmic_bytes(w, n_part, cls, level):
         "cellid": 8 * C + 4 * N,
         "green": 4 * half,
         "prep": 26 * N,
-        "pp_dense": 0,
+        "pp_order": 4 * C + 26 * N,
         "sort_big": 8 * N,
     }
     return table[cls]
@@ -616,11 +616,7 @@ def main():
     # dominant kernel class -> roofline (PP counts both of its kernels)
     peak, peak_kind = peaks()
     total_prof = sum(v[0] for v in prof.values())
-    merged = dict(prof)
-    if ("pp", 0) in merged and ("pp_dense", 0) in merged:
-        a_, b_ = merged.pop(("pp", 0)), merged.pop(("pp_dense", 0))
-        merged[("pp", 0)] = (a_[0] + b_[0], a_[1])
-    dom = max(merged.items(), key=lambda kv: kv[1][0])
+    dom = max(prof.items(), key=lambda kv: kv[1][0])
     (cls, lvl), (dms, dcount) = dom
     per_launch_ms = dms / dcount
     kname = f"{cls}[level {lvl}]" if cls.startswith("fft") else cls

@@ -752,7 +752,7 @@ int cube2_profile_read(cube2_ctx *ctx, double *ms, int64_t *counts) {
 const char *cube2_profile_class_name(int cls) {
     static const char *names[CUBE2_PROFILE_CLASSES] = {
         "deposit", "fft_x_fwd", "fft_y_fwd", "fft_z_green", "fft_y_inv", "fft_x_inv", "interp", "pp",
-        "kick", "kick_drift", "scan", "scatter", "sort", "gather", "cellid", "green", "pp_dense", "prep",
+        "kick", "kick_drift", "scan", "scatter", "sort", "gather", "cellid", "green", "pp_order", "prep",
         "sort_big"};
     return (cls >= 0 && cls < CUBE2_PROFILE_CLASSES) ? names[cls] : "";
 }

@@ -28,7 +28,7 @@ enum StatusBits : int {
 enum ProfClass : int {
     P_DEPOSIT = 0, P_FFT_X_FWD, P_FFT_Y_FWD, P_FFT_Z_GREEN, P_FFT_Y_INV, P_FFT_X_INV,
     P_INTERP, P_PP, P_KICK, P_KICK_DRIFT, P_SCAN, P_SCATTER, P_SORT, P_GATHER, P_CELLID, P_GREEN,
-    P_PP_DENSE, P_PREP, P_SORT_BIG,
+    P_PP_ORDER, P_PREP, P_SORT_BIG,
     P_NCLASS
 };
 

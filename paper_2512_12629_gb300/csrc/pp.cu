@@ -630,6 +630,9 @@ cudaError_t launch_pp(cube2_ctx *ctx, const cube2_particles *p, int accumulate, 
         ProfScope prof(ctx, P_PREP, 0);
         prep_positions_kernel<<<(unsigned)nblocks, PP_CTA, 0, ctx->stream>>>(p->off[0], p->off[1], p->off[2],
                                                                            ctx->cellid, ctx->pos4, ctx->pp_perm, ctx->N);
+    }
+    {
+        ProfScope prof(ctx, P_PP_ORDER, 0);
         cudaMemsetAsync(ctx->big_n, 0, sizeof(int), ctx->stream);
         pp_dense_list_kernel<<<(unsigned)((ctx->n_cells + 255) / 256), 256, 0, ctx->stream>>>(p->count, ctx->n_cells,
                                                                                           ctx->big, ctx->big_n);
