@@ -158,7 +158,9 @@ int cube2_kdk_step(cube2_ctx *ctx, cube2_particles *p, double a0, double a1);
 
 /* The same step for a particle set held in HOST memory (pinned for speed):
  * copies host -> dev, runs cube2_kdk_step on dev, copies dev -> host (off,
- * count, start, vel, acc), all on the context stream, then synchronises. */
+ * count, start, vel, acc), then synchronises.  Offsets, counts and starts
+ * are final after the re-bin; their download runs on a second stream of the
+ * context while the forces are computed. */
 int cube2_kdk_step_host(cube2_ctx *ctx, cube2_particles *dev, cube2_particles *host,
                         double a0, double a1);
 

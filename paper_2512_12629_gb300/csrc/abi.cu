@@ -138,6 +138,8 @@ void free_ctx(cube2_ctx *c) {
     cudaFree(c->pp_stats);
     cudaFree(c->dev_status);
     cudaFreeHost(c->host_status);
+    if (c->aux_event) cudaEventDestroy(c->aux_event);
+    if (c->aux_stream) cudaStreamDestroy(c->aux_stream);
     delete c;
 }
 
@@ -257,6 +259,8 @@ int cube2_init_mesh(cube2_ctx **out, const cube2_config *cfg, void *stream) {
     alloc((void **)&c->dev_status, sizeof(int));
     if (e == cudaSuccess) e = cudaMemsetAsync(c->dev_status, 0, sizeof(int), c->stream);
     if (e == cudaSuccess) e = cudaHostAlloc((void **)&c->host_status, sizeof(int), cudaHostAllocDefault);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->aux_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->aux_event, cudaEventDisableTiming);
     for (int l = 0; l < c->nl && e == cudaSuccess; ++l) e = launch_init_twiddles(c, c->lev[l]);
     if (e != cudaSuccess) {
         g_init_error = std::string("allocation/setup failed: ") + cudaGetErrorString(e);
@@ -417,7 +421,9 @@ int cube2_kdk_factors(const cube2_config *cfg, double a0, double a1, double out[
     return CUBE2_OK;
 }
 
-int cube2_kdk_step(cube2_ctx *ctx, cube2_particles *p, double a0, double a1) {
+// One KDK step; if after_rebin is given it is recorded on the context stream
+// once the particle positions, counts and starts hold their final values.
+static int kdk_step_core(cube2_ctx *ctx, cube2_particles *p, double a0, double a1, cudaEvent_t after_rebin) {
     if (!ctx) return CUBE2_ERR_BAD_ARG;
     if (!particles_ok(ctx, p, true, true)) return set_error(ctx, CUBE2_ERR_BAD_ARG, "bad particle arrays");
     double f[3];
@@ -426,8 +432,13 @@ int cube2_kdk_step(cube2_ctx *ctx, cube2_particles *p, double a0, double a1) {
     cudaError_t e = launch_cellid(ctx, p);
     if (e == cudaSuccess) e = launch_kick_drift(ctx, p, (float)(c * f[0]), (float)(f[1] * FIX / ctx->s_ios));
     if (e == cudaSuccess) e = launch_rebin(ctx, p);
+    if (e == cudaSuccess && after_rebin) e = cudaEventRecord(after_rebin, ctx->stream);
     if (e != cudaSuccess) return cuda_error(ctx, e, "kick/drift/rebin");
     return force_core(ctx, p, (float)(c * f[2]));
+}
+
+int cube2_kdk_step(cube2_ctx *ctx, cube2_particles *p, double a0, double a1) {
+    return kdk_step_core(ctx, p, a0, a1, nullptr);
 }
 
 int cube2_adjoint_init(cube2_ctx *ctx) {
@@ -609,26 +620,30 @@ int cube2_kdk_step_host(cube2_ctx *ctx, cube2_particles *dev, cube2_particles *h
         return set_error(ctx, CUBE2_ERR_BAD_ARG, "bad particle arrays");
     const size_t N = (size_t)ctx->N, C = (size_t)ctx->n_cells;
     cudaError_t e = cudaSuccess;
-    auto cp = [&](void *dst, const void *src, size_t bytes, cudaMemcpyKind k) {
-        if (e == cudaSuccess && bytes) e = cudaMemcpyAsync(dst, src, bytes, k, ctx->stream);
+    auto cp = [&](void *dst, const void *src, size_t bytes, cudaMemcpyKind k, cudaStream_t s) {
+        if (e == cudaSuccess && bytes) e = cudaMemcpyAsync(dst, src, bytes, k, s);
     };
     for (int d = 0; d < 3; ++d) {
-        cp(dev->off[d], host->off[d], N * 2, cudaMemcpyHostToDevice);
-        cp(dev->vel[d], host->vel[d], N * 4, cudaMemcpyHostToDevice);
-        cp(dev->acc[d], host->acc[d], N * 4, cudaMemcpyHostToDevice);
+        cp(dev->off[d], host->off[d], N * 2, cudaMemcpyHostToDevice, ctx->stream);
+        cp(dev->vel[d], host->vel[d], N * 4, cudaMemcpyHostToDevice, ctx->stream);
+        cp(dev->acc[d], host->acc[d], N * 4, cudaMemcpyHostToDevice, ctx->stream);
     }
-    cp(dev->count, host->count, C * 4, cudaMemcpyHostToDevice);
-    cp(dev->start, host->start, C * 4, cudaMemcpyHostToDevice);
+    cp(dev->count, host->count, C * 4, cudaMemcpyHostToDevice, ctx->stream);
+    cp(dev->start, host->start, C * 4, cudaMemcpyHostToDevice, ctx->stream);
     if (e != cudaSuccess) return cuda_error(ctx, e, "upload");
-    int r = cube2_kdk_step(ctx, dev, a0, a1);
+    int r = kdk_step_core(ctx, dev, a0, a1, ctx->aux_event);
     if (r) return r;
+    // positions, counts and starts are final after the re-bin: download them
+    // on the second stream while the forces are computed
+    e = cudaStreamWaitEvent(ctx->aux_stream, ctx->aux_event, 0);
+    for (int d = 0; d < 3; ++d) cp(host->off[d], dev->off[d], N * 2, cudaMemcpyDeviceToHost, ctx->aux_stream);
+    cp(host->count, dev->count, C * 4, cudaMemcpyDeviceToHost, ctx->aux_stream);
+    cp(host->start, dev->start, C * 4, cudaMemcpyDeviceToHost, ctx->aux_stream);
     for (int d = 0; d < 3; ++d) {
-        cp(host->off[d], dev->off[d], N * 2, cudaMemcpyDeviceToHost);
-        cp(host->vel[d], dev->vel[d], N * 4, cudaMemcpyDeviceToHost);
-        cp(host->acc[d], dev->acc[d], N * 4, cudaMemcpyDeviceToHost);
+        cp(host->vel[d], dev->vel[d], N * 4, cudaMemcpyDeviceToHost, ctx->stream);
+        cp(host->acc[d], dev->acc[d], N * 4, cudaMemcpyDeviceToHost, ctx->stream);
     }
-    cp(host->count, dev->count, C * 4, cudaMemcpyDeviceToHost);
-    cp(host->start, dev->start, C * 4, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->aux_stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
     if (e != cudaSuccess) return cuda_error(ctx, e, "download");
     return CUBE2_OK;

@@ -54,6 +54,8 @@ struct Level {
 struct cube2_ctx {
     cube2_config cfg{};
     cudaStream_t stream = nullptr;
+    cudaStream_t aux_stream = nullptr;   // host-buffer step: early downloads
+    cudaEvent_t aux_event = nullptr;     // ... after the re-bin
     int device = 0;
     int nl = 0;
     cube2::Level lev[CUBE2_MAX_LEVELS];

@@ -344,3 +344,19 @@ def test_single_particle_and_empty_box():
     ctx0.kdk_step(p0, 0.5, 0.6)
     ctx0.check()
     assert int(p0.count.sum()) == 0
+
+
+def test_host_buffer_step_equals_device_step():
+    """cube2_kdk_step_host (pinned host state, uploads, step, overlapped
+    downloads) leaves the host arrays bitwise equal to a device-side step."""
+    w, st, _, ctx = case("C2_SMALL")
+    p = cube2.IOSState.from_numpy(st)
+    ctx.force(p)
+    a = w.scale_factors()
+    host = cube2.IOSState(*(x.cpu().pin_memory() for x in (p.off, p.count, p.start, p.vel, p.acc)))
+    dev = p.clone()
+    ctx.kdk_step(p, a[0], a[1])
+    ctx.kdk_step_host(dev, host, a[0], a[1])
+    ctx.check()
+    for x, y in zip((host.off, host.count, host.start, host.vel, host.acc), (p.off, p.count, p.start, p.vel, p.acc)):
+        assert torch.equal(x, y.cpu())
