@@ -39,7 +39,7 @@ def _boxes(n_boxes, n_steps, sizes, seed):
     return ws, ctxs, states
 
 
-@pytest.mark.parametrize("n_streams", [1, 3])
+@pytest.mark.parametrize("n_streams", [1, 3, 16])
 def test_ensemble_graph_equals_box_by_box(n_streams):
     ws, ctxs, states = _boxes(5, 3, (16, 24, 32), seed=7)
     ref = [p.clone() for p in states]

@@ -344,6 +344,14 @@ def test_single_particle_and_empty_box():
     ctx0.kdk_step(p0, 0.5, 0.6)
     ctx0.check()
     assert int(p0.count.sum()) == 0
+    # ... and so is the adjoint chain
+    ctx0.adjoint_init()
+    assert ctx0.force_vjp(p0, torch.zeros(3, 0, device="cuda")).shape == (3, 0)
+    loss, g = ctx0.density_mse_vjp(0, p0, torch.zeros(16, 16, 16, device="cuda"))
+    assert loss == 0.0 and g.shape == (3, 0)
+    loss, gx, gv = cube2.loss_gradient(ctx0, p0, torch.zeros(16, 16, 16, device="cuda"), [0.5, 0.6, 0.7])
+    ctx0.check()
+    assert loss == 0.0 and gx.shape == (3, 0) and gv.shape == (3, 0)
 
 
 def test_host_buffer_step_equals_device_step():
