@@ -521,8 +521,101 @@ def run_adjoint(args):
     print(json.dumps(line), flush=True)
 
 
+LARGE = "c5-force-1024c-512x2048mesh"
+
+
+def run_large(args):
+    """One force evaluation of the large workload (1024^3 particles, 512^3 +
+    2048^3 meshes, 1024^3 IOS cells, Zel'dovich displacement to z = 0, initial
+    conditions from the device generator): W warm-up and K timed evaluations,
+    CUDA events on the library's stream, with the per-class profile."""
+    import torch
+    from inputs.workloads import WORKLOADS
+    from inputs.zeldovich_gpu import zeldovich_ios_torch
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return
+    torch.cuda.set_device(0)
+    from paper_2512_12629_gb300 import build as pkg_build
+    pkg_build.build()
+    from paper_2512_12629_gb300 import cube2
+    w = WORKLOADS["pm2-1024c-512x2048mesh"]
+    st = zeldovich_ios_torch(w)
+    torch.cuda.empty_cache()
+    n_part = w.n_particles
+    p = cube2.IOSState(st["off"], st["count"], st["start"], torch.zeros((3, 1), device="cuda"),
+                       torch.zeros((3, n_part), device="cuda"))
+    ctx = cube2.init_mesh(cube2.make_config(w, n_particles=n_part))
+    t0 = time.perf_counter()
+    for l in range(len(w.levels)):
+        ctx.set_green(l)
+    torch.cuda.synchronize()
+    green_s = time.perf_counter() - t0
+    for _ in range(max(1, args.warmup)):
+        ctx.force(p)
+    ctx.check()
+    torch.cuda.synchronize()
+    stream = ctx.stream
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ctx.profile(capacity=64 * (args.steps + 2))
+    ctx.pp_stats()
+    launches0 = ctx.launch_count()
+    clocks = ClockSampler(bus_id_of(torch.cuda.current_device()))
+    clocks.start()
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    for _ in range(args.steps):
+        ctx.force(p)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = ev0.elapsed_time(ev1)
+    prof = ctx.profile_read()
+    ctx.profile(0)
+    ctx.check()
+    pairs, cands = ctx.pp_stats()
+    launches = ctx.launch_count() - launches0
+    total_prof = sum(v[0] for v in prof.values())
+    kernels = {f"{c}/{l}": {"share": v[0] / total_prof, "ms_per_launch": v[0] / v[1], "launches": v[1]}
+               for (c, l), v in sorted(prof.items(), key=lambda kv: -kv[1][0])}
+    (cls, lvl), (dms, dcount) = max(prof.items(), key=lambda kv: kv[1][0])
+    per_launch_ms = dms / dcount
+    if cls == "pp":
+        mhz = (clk or {}).get("sm_mhz") or 2070.0
+        fpk = fp32_peak_tflops(mhz)
+        achieved = pairs * PP_FLOPS_PAIR / dcount / (per_launch_ms / 1e3) / 1e12
+        roofline = {"bound": "alu", "kernel": "pp_kernel", "achieved": achieved, "peak": fpk, "unit": "TFLOP/s",
+                    "frac": achieved / fpk, "pairs_per_launch": pairs / dcount, "mean_launch_ms": per_launch_ms,
+                    "traffic": None}
+    else:
+        peak, kind = peaks()
+        alg = algorithmic_bytes(w, n_part, cls, lvl)
+        achieved = alg / (per_launch_ms / 1e3) / 1e9
+        roofline = {"bound": "hbm", "kernel": f"{cls}[level {lvl}]", "achieved": achieved, "peak": peak,
+                    "unit": "GB/s", "frac": achieved / peak, "peak_source": kind,
+                    "algorithmic_bytes_per_launch": alg, "mean_launch_ms": per_launch_ms, "traffic": None}
+    line = {
+        "metric": "particle-force evaluations/sec (1024^3 particles, 512^3 + 2048^3 meshes, PM + PP)",
+        "value": n_part * args.steps / (ms / 1e3), "unit": "particle-forces/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (device-generated Zel'dovich displacement to z = 0, BBKS spectrum)",
+        "config": {"workload": LARGE, "particles": n_part, "meshes": [lv.n_mesh for lv in w.levels],
+                   "ios_cells": w.n_ios, "step": "one force evaluation (deposit, two solves, interp, PP)",
+                   "l2": "inputs larger than L2", "green_tables_s": green_s},
+        "roofline": roofline, "gpu_launches": launches, "clocks": clk, "kernels": kernels,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse_args()
+    if args.workload == LARGE:
+        if args.impl == "reference":
+            print(json.dumps({"impl": "reference", "unavailable": "the large workload has no oracle arm (host memory)"}))
+            return
+        run_large(args)
+        return
     if args.workload == ADJOINT:
         if args.impl == "reference":
             print(json.dumps({"impl": "reference", "unavailable": "the adjoint workload has no oracle arm"}))

@@ -167,6 +167,10 @@ struct Tile {
     static constexpr int T = T0 < 64 ? 64 : (T0 > 1024 ? 1024 : T0);
     static constexpr size_t SMEM = (size_t)N * LP * sizeof(float2);
     static constexpr size_t SMEMY = (size_t)N * LPY * sizeof(float2);
+    // resident CTAs the z pass asks registers for: two for 512-thread tiles
+    // that fit twice in shared memory (64 registers, no spills); one otherwise
+    // (larger tiles do not fit twice, and smaller bounds only cost registers)
+    static constexpr int ZMINB = (T == 512 && 2 * SMEMY <= 200 * 1024) ? 2 : 1;
 };
 
 __device__ __forceinline__ void cp_async16(void *smem_dst, const void *gsrc) {
@@ -252,7 +256,7 @@ __global__ void __launch_bounds__(Tile<N>::T) fft_y(float2 *__restrict__ data, i
 
 // ------------------------------------------------------------ Z (+ Green)
 template <int N, bool GREEN>
-__global__ void __launch_bounds__(Tile<N>::T, (Tile<N>::T >= 512 ? 2 : 1)) fft_z(float2 *__restrict__ data, const float *__restrict__ green,
+__global__ void __launch_bounds__(Tile<N>::T, Tile<N>::ZMINB) fft_z(float2 *__restrict__ data, const float *__restrict__ green,
                                                    int kxp, const float2 *__restrict__ tw) {
     constexpr int L = Tile<N>::L, LP = Tile<N>::LPY, T = Tile<N>::T;
     extern __shared__ __align__(16) float2 S[];

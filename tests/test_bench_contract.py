@@ -33,6 +33,6 @@ def test_reference_arm_line():
 
 
 def test_arms_without_oracle_say_so():
-    for wl in ("c4-ensemble-64x20", "c3-adjoint-128c-256mesh"):
+    for wl in ("c4-ensemble-64x20", "c3-adjoint-128c-256mesh", "c5-force-1024c-512x2048mesh"):
         d = _run("--impl", "reference", "--workload", wl)
         assert d["impl"] == "reference" and "unavailable" in d
