@@ -42,6 +42,7 @@ class Workload:
     # growth factor used for the displacement: None -> D(a_init);
     # a float -> D at that scale factor (e.g. 1.0 for a z=0-like state)
     displace_to_a: float | None = None
+    assign_order: int = 2        # mass assignment: 2 = CIC (the workload's), 3 = TSC (the paper's)
 
     @property
     def n_particles(self) -> int:
@@ -85,6 +86,12 @@ C2 = Workload(
 C2_SMALL = C2.with_(name="pm2-64c-32x128mesh", n_p=64, box=64.0, n_ios=64,
                     levels=(Level(32, 3.5), Level(128, 2.0)), seed=12)
 
+# The two-level recipe at 64^3 particles with the paper's TSC assignment
+# (Eq. filter) instead of CIC.
+C2_SMALL_TSC = C2_SMALL.with_(name="pm2-64c-32x128mesh-tsc", assign_order=3)
+# The 256^3 workload with TSC assignment.
+C2_TSC = C2.with_(name="pm2-256c-128x512mesh-tsc", assign_order=3)
+
 # Same recipe as C2 at 27/64 of the volume (192^3 particles, 96^3 + 384^3
 # meshes, the same IOS/mesh ratios): every array larger than L2, a working
 # set of about 1.5 GB; the size used for multi-pass profiler captures.
@@ -123,4 +130,4 @@ def c4_ensemble(n_boxes=64, seed=100, n_steps=20, sizes=(32, 48, 64, 96)):
             for b, (n, sg) in enumerate(zip(n_ps, s8))]
 
 
-WORKLOADS = {w.name: w for w in (C1, C2, C2_SMALL, C2_MID, C3, C5)}
+WORKLOADS = {w.name: w for w in (C1, C2, C2_SMALL, C2_MID, C3, C5, C2_SMALL_TSC, C2_TSC)}

@@ -186,7 +186,9 @@ def level_params(w):
 
 
 def green_tables(w, alias=2):
-    return [green(n, bs, bt, alias=alias) for (n, _h, bs, bt) in level_params(w)]
+    """Eq. Gk per level, with the workload's assignment order (2 CIC, 3 TSC)."""
+    order = getattr(w, "assign_order", 2)
+    return [green(n, bs, bt, alias=alias, order=order) for (n, _h, bs, bt) in level_params(w)]
 
 
 def pm_force_level(off, count, n_ios, n_mesh, h, g):
@@ -202,9 +204,10 @@ def pm_force_level(off, count, n_ios, n_mesh, h, g):
 def pm_force(off, count, w, greens=None):
     """Sum of all PM levels of workload ``w`` (F = -grad u, (3, N))."""
     greens = green_tables(w) if greens is None else greens
+    level_force = pm_force_level_tsc if getattr(w, "assign_order", 2) == 3 else pm_force_level
     total = 0.0
     for (n, h, _bs, _bt), g in zip(level_params(w), greens):
-        f, _ = pm_force_level(off, count, w.n_ios, n, h, g)
+        f, _ = level_force(off, count, w.n_ios, n, h, g)
         total = total + f
     return total
 
@@ -244,3 +247,64 @@ def deposit_u64_at(off, count, start, n_ios, n_mesh, cells):
                         total += int(wgt[idx == cell].sum())
         out[k] = np.uint64(total % (1 << 64))
     return out
+
+
+# ------------------------------------------------------ TSC (order 3)
+# The paper's own assignment (Eq. filter): triangular-shaped cloud, W(k) =
+# prod_d sinc^3(k_d/2).  With u the position in mesh cells, i = floor(u) the
+# cell holding it and d = u - (i + 1/2) in [-1/2, 1/2), the 1-D weights are
+# (1/2 - d)^2/2, 3/4 - d^2 and (1/2 + d)^2/2 on cells i - 1, i, i + 1.  The
+# position is the IOS fixed point in mesh units, floored to 2^-16 mesh cell
+# as for CIC; weights and sums are FP64 (no exact-integer form: a 3-D weight
+# would need 99 bits).
+def tsc_weights_1d(X, s):
+    """Cell i and the three weights (cells i-1, i, i+1) per particle, FP64."""
+    xm = (X >> s) if s >= 0 else (X << (-s))
+    i = xm >> 16
+    d = (xm - (i << 16)).astype(np.float64) / FIX - 0.5
+    return i, (0.5 * (0.5 - d) ** 2, 0.75 - d * d, 0.5 * (0.5 + d) ** 2)
+
+
+def _tsc_corners(X, n_mesh, s):
+    """Yield (flat cell index, weight) for the 27 TSC cells."""
+    parts = [tsc_weights_1d(X[d], s) for d in range(3)]
+    for jz in (-1, 0, 1):
+        iz = (parts[2][0] + jz) % n_mesh
+        wz = parts[2][1][jz + 1]
+        for jy in (-1, 0, 1):
+            iy = (parts[1][0] + jy) % n_mesh
+            wy = parts[1][1][jy + 1]
+            for jx in (-1, 0, 1):
+                ix = (parts[0][0] + jx) % n_mesh
+                yield (iz * n_mesh + iy) * n_mesh + ix, parts[0][1][jx + 1] * wy * wz
+
+
+def density_tsc(off, count, n_ios, n_mesh):
+    """FP64 overdensity (n^3/N) sum_i W(u_i, c) - 1 with TSC weights."""
+    X = fixed_coords(off, count, n_ios)
+    s = level_shift(n_ios, n_mesh)
+    rho = np.zeros(n_mesh ** 3)
+    for idx, w in _tsc_corners(X, n_mesh, s):
+        np.add.at(rho, idx, w)
+    n_part = int(count.sum())
+    return (rho * (n_mesh ** 3 / n_part) - 1.0).reshape(n_mesh, n_mesh, n_mesh)
+
+
+def interpolate_tsc(field, off, count, n_ios):
+    """TSC gather of a (3, n, n, n) field with the deposit's weights -> (3, N)."""
+    n = field.shape[1]
+    X = fixed_coords(off, count, n_ios)
+    s = level_shift(n_ios, n)
+    flat = field.reshape(3, -1)
+    out = np.zeros((3, X.shape[1]))
+    for idx, w in _tsc_corners(X, n, s):
+        out += flat[:, idx] * w
+    return out
+
+
+def pm_force_level_tsc(off, count, n_ios, n_mesh, h, g):
+    """F = -H interp_TSC(D * phi) with phi = G * rho_TSC; also returns (rho, phi)."""
+    rho = density_tsc(off, count, n_ios, n_mesh)
+    phi = solve_potential(rho, g)
+    e = fd_gradient(phi)
+    return -h * interpolate_tsc(e, off, count, n_ios), dict(rho=rho, phi=phi)
