@@ -80,6 +80,9 @@ typedef struct {
     double  omega_m, omega_l;          /* flat LCDM density parameters             */
     int64_t n_particles;               /* particle count N (fixes V_p = L^3/N)     */
     int32_t alias_max;                 /* images per axis in Eq. (Gk); 2 in paper  */
+    int32_t assign_order;              /* mass assignment: 2 (or 0) = CIC, exact
+                                        * integer deposit; 3 = TSC (Eq. filter,
+                                        * the paper's), FP32 accumulation      */
 } cube2_config;
 
 /* Particle set in IOS form; every pointer is a device pointer (see above). */
@@ -100,12 +103,12 @@ typedef struct {
  * CUBE2_ERR_CUDA if an allocation fails (nothing is leaked). */
 int cube2_init_mesh(cube2_ctx **ctx, const cube2_config *cfg, void *stream);
 
-/* Eq. (Gk) with Eqs. (Rk), (Sk), (diff) and the CIC W(k) = prod sinc^2(k_d/2),
- * alias sum over |n_d| <= alias_max, evaluated in FP64 on the GPU for level
+/* Eq. (Gk) with Eqs. (Rk), (Sk), (diff) and the assignment's W(k) =
+ * prod sinc^p(k_d/2) (p = 2 CIC, 3 TSC), alias sum over |n_d| <= alias_max, evaluated in FP64 on the GPU for level
  * `level` and stored as FP32 on the r2c half spectrum [kz][ky][kx <= n/2]
  * with the inverse-FFT factor 1/n^3 folded in.  G = 0 where |D(k)| = 0.
  * cache_path (optional, may be NULL) names a file: if it holds a table for
- * the same (n, b_soft, b_trunc, alias) it is read instead of computed,
+ * the same (n, b_soft, b_trunc, alias, order) it is read instead of computed,
  * otherwise the computed table is written there (Sec. 2.1.2: tables may be
  * stored as files).  Synchronises the stream when a file is used. */
 int cube2_set_green(cube2_ctx *ctx, int level, const char *cache_path);

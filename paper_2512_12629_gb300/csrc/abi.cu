@@ -175,7 +175,8 @@ int cube2_init_mesh(cube2_ctx **out, const cube2_config *cfg, void *stream) {
     *out = nullptr;
     if (!(cfg->box > 0) || cfg->n_ios < 4 || cfg->n_levels < 1 || cfg->n_levels > CUBE2_MAX_LEVELS ||
         cfg->n_particles < 0 || cfg->n_particles > 2147483647LL || !(cfg->b_pp > 0) ||
-        !(cfg->omega_m > 0) || cfg->omega_l < 0 || cfg->alias_max < 0 || cfg->alias_max > 4)
+        !(cfg->omega_m > 0) || cfg->omega_l < 0 || cfg->alias_max < 0 || cfg->alias_max > 4 ||
+        (cfg->assign_order != 0 && cfg->assign_order != 2 && cfg->assign_order != 3))
         return fail(CUBE2_ERR_BAD_ARG, "invalid config field");
     if ((int64_t)cfg->n_ios * cfg->n_ios * cfg->n_ios > 2147483647LL)
         return fail(CUBE2_ERR_UNSUPPORTED_SIZE, "n_ios^3 exceeds int32 cell ids");
@@ -189,6 +190,7 @@ int cube2_init_mesh(cube2_ctx **out, const cube2_config *cfg, void *stream) {
     }
     cube2_ctx *c = new cube2_ctx();
     c->cfg = *cfg;
+    if (c->cfg.assign_order == 0) c->cfg.assign_order = 2;
     c->stream = (cudaStream_t)stream;
     cudaGetDevice(&c->device);
     c->nl = cfg->n_levels;
@@ -278,12 +280,13 @@ int cube2_set_green(cube2_ctx *ctx, int level, const char *cache_path) {
     if (r) return r;
     Level &L = ctx->lev[level];
     const size_t nh = (size_t)L.n * L.n * L.kxp;
-    // cache header: magic, n, kxp, alias, b_soft, b_trunc
-    struct Header { char magic[8]; int32_t n, kxp, alias, pad; double b_soft, b_trunc; } hdr{};
-    memcpy(hdr.magic, "CUBE2G01", 8);
+    // cache header: magic, n, kxp, alias, assignment order, b_soft, b_trunc
+    struct Header { char magic[8]; int32_t n, kxp, alias, order; double b_soft, b_trunc; } hdr{};
+    memcpy(hdr.magic, "CUBE2G02", 8);
     hdr.n = L.n;
     hdr.kxp = L.kxp;
     hdr.alias = ctx->cfg.alias_max;
+    hdr.order = ctx->cfg.assign_order;
     hdr.b_soft = L.b_soft;
     hdr.b_trunc = L.b_trunc;
     if (cache_path && cache_path[0]) {
@@ -307,7 +310,7 @@ int cube2_set_green(cube2_ctx *ctx, int level, const char *cache_path) {
             }
         }
     }
-    cudaError_t e = launch_green(ctx, L, ctx->cfg.alias_max);
+    cudaError_t e = launch_green(ctx, L, ctx->cfg.alias_max, ctx->cfg.assign_order);
     if (e != cudaSuccess) return cuda_error(ctx, e, "green kernel");
     L.has_green = true;
     if (cache_path && cache_path[0]) {
@@ -324,13 +327,36 @@ int cube2_set_green(cube2_ctx *ctx, int level, const char *cache_path) {
     return CUBE2_OK;
 }
 
+// Deposit / interpolation of one level (level >= 0) or of all levels (-1),
+// with the context's assignment (CIC: one exact-integer pass over all
+// levels; TSC: per level).
+static cudaError_t deposit_levels(cube2_ctx *ctx, int level, const cube2_particles *p) {
+    if (ctx->cfg.assign_order != 3) return launch_deposit(ctx, level, p, nullptr);
+    cudaError_t e = cudaSuccess;
+    for (int l = 0; l < ctx->nl && e == cudaSuccess; ++l)
+        if (level < 0 || l == level) e = launch_tsc_deposit(ctx, ctx->lev[l], p);
+    return e;
+}
+
+static cudaError_t interp_levels(cube2_ctx *ctx, int level, const cube2_particles *p, int accumulate) {
+    if (ctx->cfg.assign_order != 3) return launch_interp(ctx, level, p, accumulate);
+    cudaError_t e = cudaSuccess;
+    bool first = true;
+    for (int l = 0; l < ctx->nl && e == cudaSuccess; ++l)
+        if (level < 0 || l == level) {
+            e = launch_tsc_interp(ctx, ctx->lev[l], p, (accumulate || !first) ? 1 : 0);
+            first = false;
+        }
+    return e;
+}
+
 int cube2_deposit(cube2_ctx *ctx, int level, const cube2_particles *p) {
     if (!ctx) return CUBE2_ERR_BAD_ARG;
     int r = level_ok(ctx, level, true);
     if (r) return r;
     if (!particles_ok(ctx, p, false, false)) return set_error(ctx, CUBE2_ERR_BAD_ARG, "bad particle arrays");
     cudaError_t e = launch_cellid(ctx, p);
-    if (e == cudaSuccess) e = launch_deposit(ctx, level, p, nullptr);
+    if (e == cudaSuccess) e = deposit_levels(ctx, level, p);
     if (e != cudaSuccess) return cuda_error(ctx, e, "deposit");
     for (int l = 0; l < ctx->nl; ++l)
         if (level < 0 || l == level) { ctx->lev[l].has_density = true; ctx->lev[l].has_potential = false; }
@@ -342,6 +368,8 @@ int cube2_deposit_u64(cube2_ctx *ctx, int level, const cube2_particles *p, uint6
     int r = level_ok(ctx, level, false);
     if (r) return r;
     if (!out || !particles_ok(ctx, p, false, false)) return set_error(ctx, CUBE2_ERR_BAD_ARG, "bad arguments");
+    if (ctx->cfg.assign_order == 3)
+        return set_error(ctx, CUBE2_ERR_UNSUPPORTED_SIZE, "the exact integer accumulator exists for CIC only");
     cudaError_t e = launch_cellid(ctx, p);
     if (e == cudaSuccess) e = launch_deposit(ctx, level, p, out);
     if (e != cudaSuccess) return cuda_error(ctx, e, "deposit_u64");
@@ -372,7 +400,7 @@ int cube2_interp_force(cube2_ctx *ctx, int level, const cube2_particles *p, int 
         if ((level < 0 || l == level) && !ctx->lev[l].has_potential)
             return set_error(ctx, CUBE2_ERR_STATE, "interp_force needs solve_pm");
     cudaError_t e = launch_cellid(ctx, p);
-    if (e == cudaSuccess) e = launch_interp(ctx, level, p, accumulate);
+    if (e == cudaSuccess) e = interp_levels(ctx, level, p, accumulate);
     if (e != cudaSuccess) return cuda_error(ctx, e, "interp_force");
     return CUBE2_OK;
 }
@@ -390,7 +418,7 @@ int cube2_pp_force(cube2_ctx *ctx, const cube2_particles *p, int accumulate) {
 static int force_core(cube2_ctx *ctx, const cube2_particles *p, float kick) {
     for (int l = 0; l < ctx->nl; ++l)
         if (!ctx->lev[l].has_green) return set_error(ctx, CUBE2_ERR_STATE, "force needs every level's Green's table");
-    cudaError_t e = launch_deposit(ctx, -1, p, nullptr);
+    cudaError_t e = deposit_levels(ctx, -1, p);
     for (int l = 0; l < ctx->nl && e == cudaSuccess; ++l) {
         e = launch_fft_forward(ctx, ctx->lev[l]);
         if (e == cudaSuccess) e = launch_fft_z_green(ctx, ctx->lev[l]);
@@ -398,7 +426,7 @@ static int force_core(cube2_ctx *ctx, const cube2_particles *p, float kick) {
         ctx->lev[l].has_density = false;
         ctx->lev[l].has_potential = true;
     }
-    if (e == cudaSuccess) e = launch_interp(ctx, -1, p, 0);
+    if (e == cudaSuccess) e = interp_levels(ctx, -1, p, 0);
     if (e == cudaSuccess) e = launch_pp(ctx, p, 1, kick);
     if (e != cudaSuccess) return cuda_error(ctx, e, "force");
     return CUBE2_OK;
@@ -490,6 +518,8 @@ static cudaError_t force_vjp_core(cube2_ctx *ctx, const cube2_particles *p, cons
 }
 
 static int adjoint_ready(cube2_ctx *ctx) {
+    if (ctx->cfg.assign_order == 3)
+        return set_error(ctx, CUBE2_ERR_UNSUPPORTED_SIZE, "the adjoint is built for the CIC assignment");
     if (!ctx->vjp_mu) return set_error(ctx, CUBE2_ERR_STATE, "call cube2_adjoint_init first");
     for (int l = 0; l < ctx->nl; ++l)
         if (!ctx->lev[l].has_green) return set_error(ctx, CUBE2_ERR_STATE, "the product needs every level's Green's table");
@@ -528,6 +558,8 @@ int cube2_density_mse_vjp(cube2_ctx *ctx, int level, const cube2_particles *p, c
         return set_error(ctx, CUBE2_ERR_BAD_ARG, "bad particle, target or output arrays");
     for (int d = 0; d < 3; ++d)
         if (ctx->N > 0 && !w[d]) return set_error(ctx, CUBE2_ERR_BAD_ARG, "null output array");
+    if (ctx->cfg.assign_order == 3)
+        return set_error(ctx, CUBE2_ERR_UNSUPPORTED_SIZE, "the adjoint is built for the CIC assignment");
     if (!ctx->vjp_mu) return set_error(ctx, CUBE2_ERR_STATE, "call cube2_adjoint_init first");
     Level &L = ctx->lev[level];
     cudaError_t e = launch_cellid(ctx, p);

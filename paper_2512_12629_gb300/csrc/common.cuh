@@ -117,7 +117,9 @@ int cuda_error(cube2_ctx *ctx, cudaError_t e, const char *what);
 // Launch wrappers implemented in the kernel translation units.  Each returns
 // the cudaError_t of its last launch and bumps ctx->launches.
 cudaError_t launch_init_twiddles(cube2_ctx *ctx, Level &L);
-cudaError_t launch_green(cube2_ctx *ctx, Level &L, int alias);
+cudaError_t launch_green(cube2_ctx *ctx, Level &L, int alias, int order);
+cudaError_t launch_tsc_deposit(cube2_ctx *ctx, Level &L, const cube2_particles *p);
+cudaError_t launch_tsc_interp(cube2_ctx *ctx, Level &L, const cube2_particles *p, int accumulate);
 cudaError_t launch_deposit(cube2_ctx *ctx, int level, const cube2_particles *p, uint64_t *out_u64);
 cudaError_t launch_fft_forward(cube2_ctx *ctx, Level &L);          // real -> spec (x, y passes)
 cudaError_t launch_fft_z_green(cube2_ctx *ctx, Level &L);          // z fwd * G * z inv

@@ -3,7 +3,7 @@
 //
 // For a mode k = 2 pi m / n (m_d in (-n/2, n/2]) the kernel forms
 //   d_d   = 4/3 sin k_d - 1/6 sin 2k_d                     (Eq. diff, D = i d)
-//   W^2   = prod_d sinc^4((k_d + 2 pi n_d)/2)               (CIC)
+//   W^2   = prod_d sinc^(2p)((k_d + 2 pi n_d)/2)            (p = 2 CIC, 3 TSC)
 //   dS2   = S^2(|k_n|, b_soft) - S^2(|k_n|, b_trunc)        (Eqs. Rk, Sk)
 //   G     = -sum_n W^2 (d.k_n) dS2/|k_n|^2 / (|d|^2 [sum_n W^2]^2)
 // over the images |n_d| <= alias, and stores G / n^3 (the inverse FFT is
@@ -49,7 +49,7 @@ __device__ double fd_weight(int m, int n) {
 }
 
 __global__ void green_kernel(float *__restrict__ G, int n, int kxp, double b_soft, double b_trunc,
-                             int alias, double norm) {
+                             int alias, int order, double norm) {
     const int64_t total = (int64_t)n * n * kxp;
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= total) return;
@@ -63,7 +63,7 @@ __global__ void green_kernel(float *__restrict__ G, int n, int kxp, double b_sof
     if (d2 == 0.0) { G[idx] = 0.0f; return; }
     const double two_pi = 6.283185307179586476925286766559;
     const double pi = 3.141592653589793238462643383279;
-    // per-axis image wavenumbers and CIC factors sinc^4(k_n/2)
+    // per-axis image wavenumbers and squared assignment factors sinc^(2p)(k_n/2)
     double kn[3][2 * MAX_ALIAS + 1], w2[3][2 * MAX_ALIAS + 1];
     double den = 1.0;
     for (int a = 0; a < 3; ++a) {
@@ -75,7 +75,10 @@ __global__ void green_kernel(float *__restrict__ G, int n, int kxp, double b_sof
             kn[a][i + alias] = two_pi * u;
             double w;
             if (u == 0.0) w = 1.0;
-            else { const double sc = s / (pi * u); const double sc2 = sc * sc; w = sc2 * sc2; }
+            else {
+                const double sc = s / (pi * u), sc2 = sc * sc;
+                w = order == 3 ? sc2 * sc2 * sc2 : sc2 * sc2;   // W^2 = sinc^(2 order)
+            }
             w2[a][i + alias] = w;
             sum += w;
         }
@@ -116,7 +119,7 @@ cudaError_t launch_init_twiddles(cube2_ctx *ctx, Level &L) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_green(cube2_ctx *ctx, Level &L, int alias) {
+cudaError_t launch_green(cube2_ctx *ctx, Level &L, int alias, int order) {
     if (alias > MAX_ALIAS) alias = MAX_ALIAS;
     const int64_t total = (int64_t)L.n * L.n * L.kxp;
     const double norm = 1.0 / ((double)L.n * (double)L.n * (double)L.n);
@@ -124,7 +127,7 @@ cudaError_t launch_green(cube2_ctx *ctx, Level &L, int alias) {
     const int64_t blocks = (total + threads - 1) / threads;
     ProfScope prof(ctx, P_GREEN, L.index);
     green_kernel<<<(unsigned)blocks, threads, 0, ctx->stream>>>(L.green, L.n, L.kxp, L.b_soft,
-                                                                 L.b_trunc, alias, norm);
+                                                                 L.b_trunc, alias, order, norm);
     ctx->launches++;
     return cudaGetLastError();
 }

@@ -1,0 +1,186 @@
+// TSC mass assignment and force interpolation: the paper's own assignment
+// window (Eq. filter, W(k) = prod_d sinc^3(k_d/2)), selected by
+// cube2_config.assign_order = 3 in place of the workload's exact-integer CIC.
+//
+// Per axis, with the position in mesh cells u (the IOS fixed point in mesh
+// units, floored to 2^-16 mesh cell as for CIC), i = floor(u) and
+// d = u - (i + 1/2): weights (1/2 - d)^2/2, 3/4 - d^2, (1/2 + d)^2/2 on cells
+// i - 1, i, i + 1.  A 3-D TSC weight would need 99 bits as an exact integer,
+// so the deposit accumulates FP32 with global atomics onto a grid filled
+// with -1 (the overdensity of an empty cell): sums are correct to FP32
+// rounding, their last bits depend on the atomic order.
+//
+// Interpolation evaluates the 4-point difference of Eq. diff on the fly like
+// the CIC gather: along axis d the three weights and the stencil combine into
+// 7 coefficients on cells i-3 .. i+3,
+//   c_m = sum_j w_j f_(m-j),  f = (1/12, -2/3, 0, 2/3, -1/12) on offsets -2..2,
+// applied on the 3x3 lines of the two other axes (63 potential reads per
+// component).
+#include "common.cuh"
+
+namespace cube2 {
+namespace {
+
+struct TscAxis {
+    int i;        // cell holding the position
+    float w[3];   // weights of cells i-1, i, i+1
+};
+
+__device__ __forceinline__ TscAxis tsc_axis(int X, int shift) {
+    const int xm = shift >= 0 ? (X >> shift) : (X << (-shift));
+    TscAxis a;
+    a.i = xm >> FIX_BITS;
+    const float d = (float)(xm & (FIX - 1)) * (1.0f / FIX) - 0.5f;
+    a.w[0] = 0.5f * (0.5f - d) * (0.5f - d);
+    a.w[1] = 0.75f - d * d;
+    a.w[2] = 0.5f * (0.5f + d) * (0.5f + d);
+    return a;
+}
+
+__device__ __forceinline__ int wrapc(int j, int n) { return j < 0 ? j + n : (j >= n ? j - n : j); }
+
+struct TscParams {
+    const uint16_t *off0, *off1, *off2;
+    const int32_t *cellid;
+    int64_t N;
+    int n_ios, n, shift;
+    float scale;         // n^3 / N (deposit)
+    float hscale;        // -H (interpolation)
+    float *grid;         // density (deposit)
+    const float *phi;    // potential (interpolation)
+    float *acc0, *acc1, *acc2;
+    int accumulate;
+};
+
+__device__ __forceinline__ void particle_axes(const TscParams &P, int64_t i, TscAxis a[3]) {
+    const int cell = P.cellid[i], n = P.n_ios;
+    const int c[3] = {cell % n, (cell / n) % n, cell / (n * n)};
+    const int o[3] = {(int)P.off0[i], (int)P.off1[i], (int)P.off2[i]};
+#pragma unroll
+    for (int d = 0; d < 3; ++d) a[d] = tsc_axis(c[d] * FIX + o[d], P.shift);
+}
+
+__global__ void __launch_bounds__(256) fill_kernel(float *g, int64_t n, float v) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) g[i] = v;
+}
+
+__global__ void __launch_bounds__(256) tsc_deposit_kernel(TscParams P) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= P.N) return;
+    TscAxis a[3];
+    particle_axes(P, i, a);
+    const int n = P.n;
+#pragma unroll
+    for (int jz = 0; jz < 3; ++jz) {
+        const int64_t z = wrapc(a[2].i + jz - 1, n);
+        const float wz = P.scale * a[2].w[jz];
+#pragma unroll
+        for (int jy = 0; jy < 3; ++jy) {
+            const int64_t row = (z * n + wrapc(a[1].i + jy - 1, n)) * n;
+            const float wyz = wz * a[1].w[jy];
+#pragma unroll
+            for (int jx = 0; jx < 3; ++jx) atomicAdd(&P.grid[row + wrapc(a[0].i + jx - 1, n)], wyz * a[0].w[jx]);
+        }
+    }
+}
+
+// 7-point coefficients of the TSC-weighted 4-point difference along one axis.
+__device__ __forceinline__ void fd7(const float w[3], float c[7]) {
+    const float a = 2.0f / 3.0f, b = 1.0f / 12.0f;
+    c[0] = b * w[0];
+    c[1] = -a * w[0] + b * w[1];
+    c[2] = -a * w[1] + b * w[2];
+    c[3] = a * (w[0] - w[2]);
+    c[4] = -b * w[0] + a * w[1];
+    c[5] = -b * w[1] + a * w[2];
+    c[6] = -b * w[2];
+}
+
+__device__ __forceinline__ float phi_at(const float *phi, int n, int x, int y, int z) {
+    return __ldg(&phi[((int64_t)wrapc(z, n) * n + wrapc(y, n)) * n + wrapc(x, n)]);
+}
+
+__global__ void __launch_bounds__(256) tsc_interp_kernel(TscParams P) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= P.N) return;
+    TscAxis a[3];
+    particle_axes(P, i, a);
+    const int n = P.n;
+    const float *f = P.phi;
+    float cx[7], cy[7], cz[7];
+    fd7(a[0].w, cx);
+    fd7(a[1].w, cy);
+    fd7(a[2].w, cz);
+    const int ix = a[0].i, iy = a[1].i, iz = a[2].i;
+    float ex = 0.f, ey = 0.f, ez = 0.f;
+#pragma unroll 1
+    for (int j1 = 0; j1 < 3; ++j1)
+#pragma unroll 1
+        for (int j2 = 0; j2 < 3; ++j2) {
+            float sx = 0.f, sy = 0.f, sz = 0.f;
+#pragma unroll
+            for (int m = 0; m < 7; ++m) {
+                sx += cx[m] * phi_at(f, n, ix + m - 3, iy + j1 - 1, iz + j2 - 1);
+                sy += cy[m] * phi_at(f, n, ix + j1 - 1, iy + m - 3, iz + j2 - 1);
+                sz += cz[m] * phi_at(f, n, ix + j1 - 1, iy + j2 - 1, iz + m - 3);
+            }
+            ex += a[1].w[j1] * a[2].w[j2] * sx;
+            ey += a[0].w[j1] * a[2].w[j2] * sy;
+            ez += a[0].w[j1] * a[1].w[j2] * sz;
+        }
+    const float fx = P.hscale * ex, fy = P.hscale * ey, fz = P.hscale * ez;
+    if (P.accumulate) {
+        P.acc0[i] += fx;
+        P.acc1[i] += fy;
+        P.acc2[i] += fz;
+    } else {
+        P.acc0[i] = fx;
+        P.acc1[i] = fy;
+        P.acc2[i] = fz;
+    }
+}
+
+TscParams tsc_params(cube2_ctx *ctx, const Level &L, const cube2_particles *p) {
+    TscParams P{};
+    P.off0 = p->off[0]; P.off1 = p->off[1]; P.off2 = p->off[2];
+    P.cellid = ctx->cellid;
+    P.N = ctx->N;
+    P.n_ios = ctx->n_ios;
+    P.n = L.n;
+    P.shift = L.shift;
+    P.scale = (float)((double)L.n * L.n * L.n / (double)(ctx->N > 0 ? ctx->N : 1));
+    P.hscale = (float)(-L.H);
+    P.grid = L.real;
+    P.phi = L.real;
+    P.acc0 = p->acc[0]; P.acc1 = p->acc[1]; P.acc2 = p->acc[2];
+    return P;
+}
+
+}  // namespace
+
+// L.real = TSC overdensity of the particles (cell ids must be current).
+cudaError_t launch_tsc_deposit(cube2_ctx *ctx, Level &L, const cube2_particles *p) {
+    ProfScope prof(ctx, P_DEPOSIT, L.index);
+    const int64_t n3 = (int64_t)L.n * L.n * L.n;
+    fill_kernel<<<(unsigned)((n3 + 255) / 256), 256, 0, ctx->stream>>>(L.real, n3, -1.0f);
+    ctx->launches++;
+    if (ctx->N > 0) {
+        tsc_deposit_kernel<<<(unsigned)((ctx->N + 255) / 256), 256, 0, ctx->stream>>>(tsc_params(ctx, L, p));
+        ctx->launches++;
+    }
+    return cudaGetLastError();
+}
+
+// acc (=, or += with accumulate) -H TSC-gather of D * phi, phi in L.real.
+cudaError_t launch_tsc_interp(cube2_ctx *ctx, Level &L, const cube2_particles *p, int accumulate) {
+    if (ctx->N == 0) return cudaSuccess;
+    ProfScope prof(ctx, P_INTERP, L.index);
+    TscParams P = tsc_params(ctx, L, p);
+    P.accumulate = accumulate;
+    tsc_interp_kernel<<<(unsigned)((ctx->N + 255) / 256), 256, 0, ctx->stream>>>(P);
+    ctx->launches++;
+    return cudaGetLastError();
+}
+
+}  // namespace cube2

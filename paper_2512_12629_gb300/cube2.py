@@ -49,6 +49,7 @@ class Config(ctypes.Structure):
         ("omega_l", ctypes.c_double),
         ("n_particles", ctypes.c_int64),
         ("alias_max", ctypes.c_int32),
+        ("assign_order", ctypes.c_int32),
     ]
 
 
@@ -134,6 +135,7 @@ def make_config(w, n_particles=None, alias_max=2) -> Config:
     c.omega_l = w.omega_l
     c.n_particles = w.n_particles if n_particles is None else n_particles
     c.alias_max = alias_max
+    c.assign_order = getattr(w, "assign_order", 2)
     return c
 
 
