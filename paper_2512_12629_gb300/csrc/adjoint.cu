@@ -62,7 +62,10 @@ struct VjpParams {
 };
 
 template <bool MODE_E>
-__global__ void __launch_bounds__(256) vjp_gather_kernel(VjpParams P) {
+#ifndef VJP_MINB
+#define VJP_MINB 1
+#endif
+__global__ void __launch_bounds__(256, VJP_MINB) vjp_gather_kernel(VjpParams P) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= P.N) return;
     const CicPoint C = cic_point(P.off0, P.off1, P.off2, i, P.cellid[i], P.n_ios, P.shift);

@@ -524,7 +524,10 @@ struct VjpIO {
 // PP part of the vector-Jacobian product: w_i += sum_j A_ij (v_j - v_i) with
 // A_ij = g I + (g'/r) d d^T (the force's Jacobian blocks are symmetric).
 // Each lane walks its target's 27 cells as in the per-lane force path.
-__global__ void __launch_bounds__(PP_CTA) pp_vjp_kernel(PPParams P, VjpIO V) {
+#ifndef PPV_MINB
+#define PPV_MINB 1
+#endif
+__global__ void __launch_bounds__(PP_CTA, PPV_MINB) pp_vjp_kernel(PPParams P, VjpIO V) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= P.N) return;
     const int n = P.n_ios;
