@@ -43,6 +43,7 @@ class Workload:
     # a float -> D at that scale factor (e.g. 1.0 for a z=0-like state)
     displace_to_a: float | None = None
     assign_order: int = 2        # mass assignment: 2 = CIC (the workload's), 3 = TSC (the paper's)
+    iso_length: float = 0.0      # > 0: isolated boundary conditions, force truncated at this r [Mpc/h]
 
     @property
     def n_particles(self) -> int:
@@ -92,6 +93,18 @@ C2_SMALL_TSC = C2_SMALL.with_(name="pm2-64c-32x128mesh-tsc", assign_order=3)
 # The 256^3 workload with TSC assignment.
 C2_TSC = C2.with_(name="pm2-256c-128x512mesh-tsc", assign_order=3)
 
+# Pairwise force accuracy under isolated boundary conditions (Sec. 3.1,
+# Appendix A): two particles at a time in a 64 Mpc/h box with the force
+# truncated at L = 32 Mpc/h (the doubled box of the paper's test), the paper's
+# softening of 3.5 cells on both levels (coarse mesh n_ios/2, fine mesh
+# 4 n_ios so that the PP range 1.75 Mpc/h fits the 2 Mpc/h IOS cell),
+# b_pp = 0.1 IOS cell.  Separations below L - b_coarse = 18 Mpc/h are exactly
+# isolated.  n_p is unused: the pairs are placed explicitly.
+ISO_PAIRS = Workload(
+    name="pm2-iso-pairs-32c-16x128mesh", n_p=2, box=64.0, n_ios=32,
+    levels=(Level(16, 3.5), Level(128, 3.5)), b_pp=0.2, iso_length=32.0, seed=31,
+)
+
 # Same recipe as C2 at 27/64 of the volume (192^3 particles, 96^3 + 384^3
 # meshes, the same IOS/mesh ratios): every array larger than L2, a working
 # set of about 1.5 GB; the size used for multi-pass profiler captures.
@@ -130,4 +143,4 @@ def c4_ensemble(n_boxes=64, seed=100, n_steps=20, sizes=(32, 48, 64, 96)):
             for b, (n, sg) in enumerate(zip(n_ps, s8))]
 
 
-WORKLOADS = {w.name: w for w in (C1, C2, C2_SMALL, C2_MID, C3, C5, C2_SMALL_TSC, C2_TSC)}
+WORKLOADS = {w.name: w for w in (C1, C2, C2_SMALL, C2_MID, C3, C5, C2_SMALL_TSC, C2_TSC, ISO_PAIRS)}

@@ -140,10 +140,25 @@ def half_spectrum_wavenumbers(n):
     return kx, ky, kz
 
 
-def green(n, b_soft, b_trunc=None, alias=2, order=2):
+def isolation_factor(k, length):
+    """1 - sinc(k L) of Eq. (isok) (Appendix A): multiplies R(k, b) when the
+    reference force is truncated at r = L (isolated boundary conditions in a
+    box of side >= 2L); sinc(x) = sin(x)/x.  length None or 0 = periodic (1).
+    Below kL = 0.01 the Taylor series x^2/6 - x^4/120 replaces the difference."""
+    if not length:
+        return 1.0
+    x = np.asarray(k, dtype=np.float64) * length
+    small = x < 1e-2
+    xs = np.where(small, 1.0, x)
+    return np.where(small, x * x / 6.0 - x ** 4 / 120.0, 1.0 - np.sin(xs) / xs)
+
+
+def green(n, b_soft, b_trunc=None, alias=2, order=2, iso=None):
     """Eq. (Gk) on the rfftn half spectrum [kz][ky][kx] of an n^3 mesh.
 
-    b_soft, b_trunc are in this mesh's cells (b_trunc None = infinity).
+    b_soft, b_trunc are in this mesh's cells (b_trunc None = infinity); iso
+    (cells, None = periodic) truncates the level's reference force at r = iso
+    by Eq. (isok), each image's R(k_n) times 1 - sinc(|k_n| iso).
     Returned unnormalised: phi = irfftn(rfftn(rho) * G) (numpy's 1/n^3)."""
     kx, ky, kz = half_spectrum_wavenumbers(n)
     mx, my, mz = half_spectrum_modes(n)
@@ -167,6 +182,7 @@ def green(n, b_soft, b_trunc=None, alias=2, order=2):
                 safe = np.where(kn2 > 0, kn2, 1.0)
                 kn = np.sqrt(safe)
                 ds2 = profile_transform(kn, b_soft) ** 2 - profile_transform(kn, b_trunc) ** 2
+                ds2 = ds2 * isolation_factor(kn, iso)
                 # D.R*_alpha(k_n) = (i d).(i k_n dS2/|k_n|^2) = -(d.k_n) dS2/|k_n|^2
                 dr = -(dx * knx + dy * kny + dz * knz) * ds2 / safe
                 num += np.where(kn2 > 0, w2 * dr, 0.0)
@@ -177,7 +193,7 @@ def green(n, b_soft, b_trunc=None, alias=2, order=2):
     return out
 
 
-def green_at(n, modes, b_soft, b_trunc=None, alias=2, order=2):
+def green_at(n, modes, b_soft, b_trunc=None, alias=2, order=2, iso=None):
     """Eq. (Gk) at selected modes of an n^3 mesh, without the full table.
 
     modes: int array (K, 3) of (m_x, m_y, m_z) in rfftn index ranges
@@ -209,6 +225,7 @@ def green_at(n, modes, b_soft, b_trunc=None, alias=2, order=2):
                 safe = np.where(kn2 > 0, kn2, 1.0)
                 kn = np.sqrt(safe)
                 ds2 = profile_transform(kn, b_soft) ** 2 - profile_transform(kn, b_trunc) ** 2
+                ds2 = ds2 * isolation_factor(kn, iso)
                 dr = -(dx * knx + dy * kny + dz * knz) * ds2 / safe
                 num += np.where(kn2 > 0, w2 * dr, 0.0)
                 den += w2

@@ -186,9 +186,14 @@ def level_params(w):
 
 
 def green_tables(w, alias=2):
-    """Eq. Gk per level, with the workload's assignment order (2 CIC, 3 TSC)."""
+    """Eq. Gk per level, with the workload's assignment order (2 CIC, 3 TSC).
+    With w.iso_length > 0 the coarsest level (the only one whose force reaches
+    past its softening) is isolated by Eq. isok at r = iso_length (Appendix A);
+    the finer levels' kernels vanish beyond the coarser softening already."""
     order = getattr(w, "assign_order", 2)
-    return [green(n, bs, bt, alias=alias, order=order) for (n, _h, bs, bt) in level_params(w)]
+    iso = getattr(w, "iso_length", 0.0)
+    return [green(n, bs, bt, alias=alias, order=order, iso=(iso / h if iso and bt is None else None))
+            for (n, h, bs, bt) in level_params(w)]
 
 
 def pm_force_level(off, count, n_ios, n_mesh, h, g):
