@@ -83,6 +83,14 @@ typedef struct {
     int32_t assign_order;              /* mass assignment: 2 (or 0) = CIC, exact
                                         * integer deposit; 3 = TSC (Eq. filter,
                                         * the paper's), FP32 accumulation      */
+    double  iso_length;                /* 0 = periodic.  > 0: isolated boundary
+                                        * conditions (Appendix A): the coarsest
+                                        * level's reference force is truncated
+                                        * at r = iso_length [Mpc/h] by Eq. isok,
+                                        * R(k) times 1 - sinc(|k| iso_length) in
+                                        * every alias image; at most box/2, so a
+                                        * pair closer than iso_length - b_coarse
+                                        * feels no periodic image             */
 } cube2_config;
 
 /* Particle set in IOS form; every pointer is a device pointer (see above). */
@@ -107,8 +115,10 @@ int cube2_init_mesh(cube2_ctx **ctx, const cube2_config *cfg, void *stream);
  * prod sinc^p(k_d/2) (p = 2 CIC, 3 TSC), alias sum over |n_d| <= alias_max, evaluated in FP64 on the GPU for level
  * `level` and stored as FP32 on the r2c half spectrum [kz][ky][kx <= n/2]
  * with the inverse-FFT factor 1/n^3 folded in.  G = 0 where |D(k)| = 0.
+ * With cfg.iso_length > 0 the coarsest level's images are weighted by
+ * 1 - sinc(|k_n| iso_length) (Eq. isok, isolated boundary conditions).
  * cache_path (optional, may be NULL) names a file: if it holds a table for
- * the same (n, b_soft, b_trunc, alias, order) it is read instead of computed,
+ * the same (n, b_soft, b_trunc, alias, order, iso) it is read instead of computed,
  * otherwise the computed table is written there (Sec. 2.1.2: tables may be
  * stored as files).  Synchronises the stream when a file is used. */
 int cube2_set_green(cube2_ctx *ctx, int level, const char *cache_path);

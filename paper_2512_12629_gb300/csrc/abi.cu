@@ -176,7 +176,8 @@ int cube2_init_mesh(cube2_ctx **out, const cube2_config *cfg, void *stream) {
     if (!(cfg->box > 0) || cfg->n_ios < 4 || cfg->n_levels < 1 || cfg->n_levels > CUBE2_MAX_LEVELS ||
         cfg->n_particles < 0 || cfg->n_particles > 2147483647LL || !(cfg->b_pp > 0) ||
         !(cfg->omega_m > 0) || cfg->omega_l < 0 || cfg->alias_max < 0 || cfg->alias_max > 4 ||
-        (cfg->assign_order != 0 && cfg->assign_order != 2 && cfg->assign_order != 3))
+        (cfg->assign_order != 0 && cfg->assign_order != 2 && cfg->assign_order != 3) ||
+        !(cfg->iso_length >= 0) || cfg->iso_length > 0.5 * cfg->box)
         return fail(CUBE2_ERR_BAD_ARG, "invalid config field");
     if ((int64_t)cfg->n_ios * cfg->n_ios * cfg->n_ios > 2147483647LL)
         return fail(CUBE2_ERR_UNSUPPORTED_SIZE, "n_ios^3 exceeds int32 cell ids");
@@ -208,6 +209,8 @@ int cube2_init_mesh(cube2_ctx **out, const cube2_config *cfg, void *stream) {
         L.H = cfg->box / L.n;
         L.b_soft = cfg->beta[l];
         L.b_trunc = prev_b < 0 ? -1.0 : prev_b / L.H;
+        // only the coarsest level's force reaches past its own softening
+        L.iso = (l == 0 && cfg->iso_length > 0) ? cfg->iso_length / L.H : 0.0;
         prev_b = cfg->beta[l] * L.H;
         const int64_t n3 = (int64_t)L.n * L.n * L.n;
         // M = floor(N 2^48 / n^3) in 128-bit integer arithmetic
@@ -280,15 +283,16 @@ int cube2_set_green(cube2_ctx *ctx, int level, const char *cache_path) {
     if (r) return r;
     Level &L = ctx->lev[level];
     const size_t nh = (size_t)L.n * L.n * L.kxp;
-    // cache header: magic, n, kxp, alias, assignment order, b_soft, b_trunc
-    struct Header { char magic[8]; int32_t n, kxp, alias, order; double b_soft, b_trunc; } hdr{};
-    memcpy(hdr.magic, "CUBE2G02", 8);
+    // cache header: magic, n, kxp, alias, assignment order, b_soft, b_trunc, isolation length
+    struct Header { char magic[8]; int32_t n, kxp, alias, order; double b_soft, b_trunc, iso; } hdr{};
+    memcpy(hdr.magic, "CUBE2G03", 8);
     hdr.n = L.n;
     hdr.kxp = L.kxp;
     hdr.alias = ctx->cfg.alias_max;
     hdr.order = ctx->cfg.assign_order;
     hdr.b_soft = L.b_soft;
     hdr.b_trunc = L.b_trunc;
+    hdr.iso = L.iso;
     if (cache_path && cache_path[0]) {
         FILE *f = fopen(cache_path, "rb");
         if (f) {

@@ -40,6 +40,7 @@ struct Level {
     double H = 0;            // cell size [Mpc/h]
     double b_soft = 0;       // softening, this level's cells
     double b_trunc = -1;     // truncation, this level's cells (< 0: infinity)
+    double iso = 0;          // isolation length, this level's cells (0: periodic)
     float *real = nullptr;   // [n^3]  density, then potential
     float2 *spec = nullptr;  // [n][n][kxp] half spectrum scratch
     float *green = nullptr;  // [n][n][kxp] Green's table (1/n^3 folded in)

@@ -5,6 +5,7 @@
 //   d_d   = 4/3 sin k_d - 1/6 sin 2k_d                     (Eq. diff, D = i d)
 //   W^2   = prod_d sinc^(2p)((k_d + 2 pi n_d)/2)            (p = 2 CIC, 3 TSC)
 //   dS2   = S^2(|k_n|, b_soft) - S^2(|k_n|, b_trunc)        (Eqs. Rk, Sk)
+//           times 1 - sinc(|k_n| L_iso) when the level is isolated (Eq. isok)
 //   G     = -sum_n W^2 (d.k_n) dS2/|k_n|^2 / (|d|^2 [sum_n W^2]^2)
 // over the images |n_d| <= alias, and stores G / n^3 (the inverse FFT is
 // unnormalised).  G = 0 where |d| = 0.  The alias sum of W^2 factorises per
@@ -42,13 +43,23 @@ __device__ double profile_transform(double k, double b) {
     return 12.0 / (x2 * x2) * (2.0 - 2.0 * c - x * s);
 }
 
+// 1 - sin(x)/x of Eq. (isok); below x = 0.01 its Taylor series (the
+// difference cancels there).
+__device__ double one_minus_sinc(double x) {
+    if (x < 1e-2) {
+        const double x2 = x * x;
+        return x2 / 6.0 - x2 * x2 / 120.0;
+    }
+    return 1.0 - sin(x) / x;
+}
+
 __device__ double fd_weight(int m, int n) {
     // 4/3 sin(2 pi m/n) - 1/6 sin(4 pi m/n); sinpi gives exact zeros at k in {0, pi}
     const double t = 2.0 * (double)m / (double)n;
     return 4.0 / 3.0 * sinpi(t) - 1.0 / 6.0 * sinpi(2.0 * t);
 }
 
-__global__ void green_kernel(float *__restrict__ G, int n, int kxp, double b_soft, double b_trunc,
+__global__ void green_kernel(float *__restrict__ G, int n, int kxp, double b_soft, double b_trunc, double iso,
                              int alias, int order, double norm) {
     const int64_t total = (int64_t)n * n * kxp;
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -95,7 +106,8 @@ __global__ void green_kernel(float *__restrict__ G, int n, int kxp, double b_sof
                 const double kabs = sqrt(kk);
                 const double s1 = profile_transform(kabs, b_soft);
                 const double s2 = profile_transform(kabs, b_trunc);
-                const double ds2 = s1 * s1 - s2 * s2;
+                double ds2 = s1 * s1 - s2 * s2;
+                if (iso > 0.0) ds2 *= one_minus_sinc(kabs * iso);
                 num -= w2[0][ix] * wyz * (d[0] * k0 + d[1] * k1 + d[2] * k2) * ds2 / kk;
             }
         }
@@ -127,7 +139,7 @@ cudaError_t launch_green(cube2_ctx *ctx, Level &L, int alias, int order) {
     const int64_t blocks = (total + threads - 1) / threads;
     ProfScope prof(ctx, P_GREEN, L.index);
     green_kernel<<<(unsigned)blocks, threads, 0, ctx->stream>>>(L.green, L.n, L.kxp, L.b_soft,
-                                                                 L.b_trunc, alias, order, norm);
+                                                                 L.b_trunc, L.iso, alias, order, norm);
     ctx->launches++;
     return cudaGetLastError();
 }

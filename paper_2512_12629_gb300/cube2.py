@@ -50,6 +50,7 @@ class Config(ctypes.Structure):
         ("n_particles", ctypes.c_int64),
         ("alias_max", ctypes.c_int32),
         ("assign_order", ctypes.c_int32),
+        ("iso_length", ctypes.c_double),
     ]
 
 
@@ -136,6 +137,7 @@ def make_config(w, n_particles=None, alias_max=2) -> Config:
     c.n_particles = w.n_particles if n_particles is None else n_particles
     c.alias_max = alias_max
     c.assign_order = getattr(w, "assign_order", 2)
+    c.iso_length = getattr(w, "iso_length", 0.0)
     return c
 
 

@@ -1,0 +1,111 @@
+"""Isolated boundary conditions (cube2_config.iso_length, Eq. isok of Appendix
+A) through the C ABI: the coarse level's Green's table against the FP64
+oracle's (FP32 rounding), the table cache keyed by the isolation length, and
+the pairwise force accuracy test of Sec. 3.1 on the GPU path: two particles
+at a time, each pair's total force against the oracle's (force bar relative to
+the pair's reference force) and, binned in separation, F.r_hat/R - 1 and the
+direction against the reference V_p R(r, b_PP)/(4 pi) of Eq. (force_decomp).
+The binned table is printed (pytest -s) for the record."""
+import math
+
+import numpy as np
+import pytest
+
+from inputs.workloads import ISO_PAIRS
+from inputs.zeldovich import ios_from_positions
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+from oracle import kdk as okdk  # noqa: E402
+from oracle import kernels as okern  # noqa: E402
+from oracle import mesh as omesh  # noqa: E402
+from paper_2512_12629_gb300 import cube2  # noqa: E402
+
+W = ISO_PAIRS
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    c = cube2.init_mesh(cube2.make_config(W, n_particles=2))
+    for l in range(len(W.levels)):
+        c.set_green(l)
+    yield c
+    c.close()
+
+
+def test_isolated_green_table_matches_oracle(ctx):
+    params = omesh.level_params(W)
+    for l, (n, h, bs, bt) in enumerate(params):
+        g = ctx.get_green(l).cpu().numpy().astype(np.float64) * float(n) ** 3
+        iso = W.iso_length / h if l == 0 else None
+        ref = okern.green(n, bs, bt, iso=iso)
+        scale = np.abs(ref).max()
+        assert np.abs(g - ref).max() <= 2e-6 * scale, l
+    # the coarse table differs from the periodic one (off-axis images)
+    n0, _h0, bs0, _ = params[0]
+    per = okern.green(n0, bs0, None)
+    g0 = ctx.get_green(0).cpu().numpy().astype(np.float64) * float(n0) ** 3
+    assert np.abs(g0 - per).max() > 1e-3 * np.abs(per).max()
+
+
+def test_green_cache_is_keyed_by_isolation_length(ctx, tmp_path):
+    path = str(tmp_path / "g0.bin")
+    ctx.set_green(0, path)                       # writes the isolated table
+    per = cube2.init_mesh(cube2.make_config(W.with_(iso_length=0.0), n_particles=2))
+    try:
+        per.set_green(0, path)                   # header differs: recomputed, not read
+        n0 = W.levels[0].n_mesh
+        _n, _h, bs0, _ = omesh.level_params(W)[0]
+        g = per.get_green(0).cpu().numpy().astype(np.float64) * float(n0) ** 3
+        ref = okern.green(n0, bs0, None)
+        assert np.abs(g - ref).max() <= 2e-6 * np.abs(ref).max()
+    finally:
+        per.close()
+    ctx.set_green(0, path)                       # read back: the isolated table again
+    g = ctx.get_green(0).cpu().numpy().astype(np.float64) * float(n0) ** 3
+    _n, h0, _, _ = omesh.level_params(W)[0]
+    ref = okern.green(n0, bs0, None, iso=W.iso_length / h0)
+    assert np.abs(g - ref).max() <= 2e-6 * np.abs(ref).max()
+
+
+def test_pairwise_force_accuracy(ctx):
+    greens = omesh.green_tables(W)
+    b_pp = W.b_pp
+    rng = np.random.Generator(np.random.Philox(W.seed + 1))
+    rows = []
+    for r in np.geomspace(0.05, 24.0, 36):
+        xa = rng.uniform(0.0, W.box, 3)
+        u = rng.normal(size=3)
+        u /= np.linalg.norm(u)
+        pos = np.stack([xa, (xa + r * u) % W.box], axis=1)
+        st = ios_from_positions(pos, np.zeros((3, 2)), W.n_ios, W.box)
+        p = cube2.IOSState.from_numpy(st)
+        ctx.force(p)
+        ctx.check()
+        f = p.acc.cpu().numpy().astype(np.float64)
+        f_or = okdk.total_force(st["off"], st["count"], st["start"], W, greens)
+        x = omesh.positions(st["off"], st["count"], W.n_ios, W.box)
+        d = x[:, 1] - x[:, 0]
+        d -= W.box * np.rint(d / W.box)
+        rr = float(np.linalg.norm(d))
+        ref = W.box ** 3 / 2 / (4 * math.pi) * float(okern.reference_force(rr, b_pp))
+        # parity with the oracle at the force bar, relative to the pair's reference force
+        assert np.abs(f - f_or).max() <= 1e-4 * ref, (rr, np.abs(f - f_or).max() / ref)
+        # momentum: the two forces cancel
+        assert np.abs(f[:, 0] + f[:, 1]).max() <= 1e-4 * ref
+        f0 = f[:, 0]
+        rows.append((rr, float(np.dot(f0, d)) / rr / ref - 1.0,
+                     math.acos(max(-1.0, min(1.0, float(np.dot(f0, d)) / (np.linalg.norm(f0) * rr))))))
+    rows = np.array(rows)
+    print("\npairwise force accuracy, isolated boundary conditions (GPU path):")
+    print("  r range [Mpc/h]   pairs   mean(F/R-1)   std(F/R-1)   max|F/R-1|   max theta [rad]")
+    for lo, hi in ((0.05, 0.3), (0.3, 2.0), (2.0, 6.0), (6.0, 12.0), (12.0, 24.1)):
+        m = (rows[:, 0] >= lo) & (rows[:, 0] < hi)
+        e, th = rows[m, 1], rows[m, 2]
+        print(f"  [{lo:5.2f}, {hi:5.2f})   {m.sum():5d}   {e.mean():+.2e}     {e.std():.2e}     "
+              f"{np.abs(e).max():.2e}     {th.max():.2e}")
+        assert abs(e.mean()) < 0.02 and e.std() < 0.04 and np.abs(e).max() < 0.1 and th.max() < 0.1, (lo, hi)
