@@ -113,12 +113,16 @@ int cube2_init_mesh(cube2_ctx **ctx, const cube2_config *cfg, void *stream);
 
 /* Eq. (Gk) with Eqs. (Rk), (Sk), (diff) and the assignment's W(k) =
  * prod sinc^p(k_d/2) (p = 2 CIC, 3 TSC), alias sum over |n_d| <= alias_max, evaluated in FP64 on the GPU for level
- * `level` and stored as FP32 on the r2c half spectrum [kz][ky][kx <= n/2]
- * with the inverse-FFT factor 1/n^3 folded in.  G = 0 where |D(k)| = 0.
+ * `level` with the inverse-FFT factor 1/n^3 folded in, G = 0 where |D(k)| = 0.
+ * G is even in each k_d and symmetric under axis permutations, so it is
+ * computed and stored once per sorted triple 0 <= a <= b <= c <= n/2 of
+ * |m_x|, |m_y|, |m_z| (entry c(c+1)(c+2)/6 + b(b+1)/2 + a, FP32,
+ * (n/2+1)(n/2+2)(n/2+3)/6 entries: 11 MB at n = 512, 0.7 GB at n = 2048) and
+ * looked up by the z pass; cube2_get_green expands it.
  * With cfg.iso_length > 0 the coarsest level's images are weighted by
  * 1 - sinc(|k_n| iso_length) (Eq. isok, isolated boundary conditions).
  * cache_path (optional, may be NULL) names a file: if it holds a table for
- * the same (n, b_soft, b_trunc, alias, order, iso) it is read instead of computed,
+ * the same (n, b_soft, b_trunc, alias, order, iso) in the reduced layout it is read instead of computed,
  * otherwise the computed table is written there (Sec. 2.1.2: tables may be
  * stored as files).  Synchronises the stream when a file is used. */
 int cube2_set_green(cube2_ctx *ctx, int level, const char *cache_path);
@@ -179,7 +183,8 @@ int cube2_kdk_step_host(cube2_ctx *ctx, cube2_particles *dev, cube2_particles *h
 
 /* Test/diagnostic copies of internal grids into caller device buffers:
  * density after cube2_deposit, potential after cube2_solve_pm ([n][n][n]
- * FP32), Green's table ([n][n][n/2+1] FP32 including the 1/n^3 factor). */
+ * FP32), Green's table (expanded from the reduced layout to [n][n][n/2+1]
+ * FP32, including the 1/n^3 factor). */
 int cube2_get_density(cube2_ctx *ctx, int level, float *out);
 int cube2_get_potential(cube2_ctx *ctx, int level, float *out);
 int cube2_get_green(cube2_ctx *ctx, int level, float *out);

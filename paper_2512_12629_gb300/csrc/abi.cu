@@ -238,7 +238,8 @@ int cube2_init_mesh(cube2_ctx **out, const cube2_config *cfg, void *stream) {
         const size_t nh = (size_t)L.n * L.n * L.kxp;
         alloc((void **)&L.real, n3 * sizeof(float));
         alloc((void **)&L.spec, nh * sizeof(float2));
-        alloc((void **)&L.green, nh * sizeof(float));
+        L.green_len = green_table_len(L.n);
+        alloc((void **)&L.green, (size_t)L.green_len * sizeof(float));
         alloc((void **)&L.tw, (size_t)L.n * sizeof(float2));
         if (e == cudaSuccess) e = cudaMemsetAsync(L.spec, 0, nh * sizeof(float2), c->stream);
     }
@@ -282,12 +283,12 @@ int cube2_set_green(cube2_ctx *ctx, int level, const char *cache_path) {
     int r = level_ok(ctx, level, false);
     if (r) return r;
     Level &L = ctx->lev[level];
-    const size_t nh = (size_t)L.n * L.n * L.kxp;
-    // cache header: magic, n, kxp, alias, assignment order, b_soft, b_trunc, isolation length
-    struct Header { char magic[8]; int32_t n, kxp, alias, order; double b_soft, b_trunc, iso; } hdr{};
-    memcpy(hdr.magic, "CUBE2G03", 8);
+    const size_t nh = (size_t)L.green_len;
+    // cache header: magic, n, entries (reduced layout), alias, assignment order, b_soft, b_trunc, isolation length
+    struct Header { char magic[8]; int32_t n, len, alias, order; double b_soft, b_trunc, iso; } hdr{};
+    memcpy(hdr.magic, "CUBE2G04", 8);
     hdr.n = L.n;
-    hdr.kxp = L.kxp;
+    hdr.len = (int32_t)L.green_len;
     hdr.alias = ctx->cfg.alias_max;
     hdr.order = ctx->cfg.assign_order;
     hdr.b_soft = L.b_soft;
@@ -717,10 +718,8 @@ int cube2_get_green(cube2_ctx *ctx, int level, float *out) {
     if (!out) return set_error(ctx, CUBE2_ERR_BAD_ARG, "null out");
     const Level &L = ctx->lev[level];
     if (!L.has_green) return set_error(ctx, CUBE2_ERR_STATE, "no Green's table");
-    const int nh = L.n / 2 + 1;
-    cudaError_t e = cudaMemcpy2DAsync(out, nh * 4, L.green, L.kxp * 4, nh * 4, (size_t)L.n * L.n,
-                                      cudaMemcpyDeviceToDevice, ctx->stream);
-    return e == cudaSuccess ? CUBE2_OK : cuda_error(ctx, e, "green copy");
+    const cudaError_t e = launch_green_expand(ctx, L, out);
+    return e == cudaSuccess ? CUBE2_OK : cuda_error(ctx, e, "green expand");
 }
 
 int cube2_debug_forward_fft(cube2_ctx *ctx, int level, float *out) {

@@ -43,7 +43,8 @@ struct Level {
     double iso = 0;          // isolation length, this level's cells (0: periodic)
     float *real = nullptr;   // [n^3]  density, then potential
     float2 *spec = nullptr;  // [n][n][kxp] half spectrum scratch
-    float *green = nullptr;  // [n][n][kxp] Green's table (1/n^3 folded in)
+    float *green = nullptr;  // symmetry-reduced Green's table (1/n^3 folded in), see green_index
+    int64_t green_len = 0;   // entries of the reduced table
     float2 *tw = nullptr;    // [n] twiddles exp(-2 pi i k / n)
     uint64_t mean_int = 0;   // M = floor(N 2^48 / n^3)
     float dens_scale = 0;    // RN32(n^3/N 2^-48)
@@ -119,6 +120,24 @@ int cuda_error(cube2_ctx *ctx, cudaError_t e, const char *what);
 // the cudaError_t of its last launch and bumps ctx->launches.
 cudaError_t launch_init_twiddles(cube2_ctx *ctx, Level &L);
 cudaError_t launch_green(cube2_ctx *ctx, Level &L, int alias, int order);
+cudaError_t launch_green_expand(cube2_ctx *ctx, const Level &L, float *out);   // full [n][n][n/2+1] copy
+
+// Eq. (Gk) is even in every k_d and symmetric under permutations of the axes
+// (cubic mesh, symmetric image sums), so the table is stored once per sorted
+// triple 0 <= a <= b <= c <= n/2 of |m_x|, |m_y|, |m_z| (m_d the signed mode):
+// entry c(c+1)(c+2)/6 + b(b+1)/2 + a, (n/2+1)(n/2+2)(n/2+3)/6 entries.
+__host__ __device__ inline int64_t green_table_len(int n) {
+    const int64_t m = n / 2 + 1;
+    return m * (m + 1) * (m + 2) / 6;
+}
+__device__ __forceinline__ int green_index(int kx, int ky, int kz, int n) {
+    int a = kx, b = ky <= n / 2 ? ky : n - ky, c = kz <= n / 2 ? kz : n - kz;
+    int t;
+    if (a > b) { t = a; a = b; b = t; }
+    if (b > c) { t = b; b = c; c = t; }
+    if (a > b) { t = a; a = b; b = t; }
+    return c * (c + 1) * (c + 2) / 6 + b * (b + 1) / 2 + a;
+}
 cudaError_t launch_tsc_deposit(cube2_ctx *ctx, Level &L, const cube2_particles *p);
 cudaError_t launch_tsc_interp(cube2_ctx *ctx, Level &L, const cube2_particles *p, int accumulate);
 cudaError_t launch_deposit(cube2_ctx *ctx, int level, const cube2_particles *p, uint64_t *out_u64);

@@ -255,7 +255,9 @@ __global__ void __launch_bounds__(Tile<N>::T) fft_y(float2 *__restrict__ data, i
 }
 
 // ------------------------------------------------------------ Z (+ Green)
-template <int N, bool GREEN>
+// GMODE 0: forward z FFT only; 1: G from a full [kz][ky][kxp] table; 2: G
+// from the symmetry-reduced table (green_index).
+template <int N, int GMODE>
 __global__ void __launch_bounds__(Tile<N>::T, Tile<N>::ZMINB) fft_z(float2 *__restrict__ data, const float *__restrict__ green,
                                                    int kxp, const float2 *__restrict__ tw) {
     constexpr int L = Tile<N>::L, LP = Tile<N>::LPY, T = Tile<N>::T;
@@ -272,11 +274,18 @@ __global__ void __launch_bounds__(Tile<N>::T, Tile<N>::ZMINB) fft_z(float2 *__re
     cp_async_wait_all();
     __syncthreads();
     fft_lines<N, L, LP, T, 1, false>(S, tw);
-    if (GREEN) {
+    if (GMODE != 0) {
         const float *g = green + ky * kxp + tx * L;
         for (int i = threadIdx.x; i < N * L / 2; i += T) {
             const int z = i / (L / 2), l2 = 2 * (i % (L / 2));
-            const float2 gv = __ldg(reinterpret_cast<const float2 *>(&g[z * zstride + l2]));
+            float2 gv;
+            if (GMODE == 1) {
+                gv = __ldg(reinterpret_cast<const float2 *>(&g[z * zstride + l2]));
+            } else {
+                const int kx = tx * L + l2;   // padding columns (kx > N/2) hold zeros
+                gv.x = kx <= N / 2 ? __ldg(&green[green_index(kx, (int)ky, z, N)]) : 0.0f;
+                gv.y = kx + 1 <= N / 2 ? __ldg(&green[green_index(kx + 1, (int)ky, z, N)]) : 0.0f;
+            }
             float4 v = *reinterpret_cast<const float4 *>(&S[z * LP + l2]);
             v.x *= gv.x;
             v.y *= gv.x;
@@ -316,9 +325,9 @@ struct Launcher {
         const unsigned bz = (unsigned)((int64_t)N * (Lv.kxp / Tile<N>::L));
         ProfScope prof(ctx, P_FFT_Z_GREEN, Lv.index);
         if (green)
-            fft_z<N, true><<<bz, Tile<N>::T, Tile<N>::SMEMY, ctx->stream>>>(Lv.spec, Lv.green, Lv.kxp, Lv.tw);
+            fft_z<N, 2><<<bz, Tile<N>::T, Tile<N>::SMEMY, ctx->stream>>>(Lv.spec, Lv.green, Lv.kxp, Lv.tw);
         else
-            fft_z<N, false><<<bz, Tile<N>::T, Tile<N>::SMEMY, ctx->stream>>>(Lv.spec, nullptr, Lv.kxp, Lv.tw);
+            fft_z<N, 0><<<bz, Tile<N>::T, Tile<N>::SMEMY, ctx->stream>>>(Lv.spec, nullptr, Lv.kxp, Lv.tw);
         ctx->launches += 1;
         return cudaGetLastError();
     }
@@ -346,8 +355,9 @@ struct Launcher {
         cudaFuncSetAttribute(fft_x_c2r<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         cudaFuncSetAttribute(fft_y<N, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         cudaFuncSetAttribute(fft_y<N, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        cudaFuncSetAttribute(fft_z<N, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        cudaFuncSetAttribute(fft_z<N, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        cudaFuncSetAttribute(fft_z<N, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        cudaFuncSetAttribute(fft_z<N, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        cudaFuncSetAttribute(fft_z<N, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         done = true;
     }
 };
@@ -454,7 +464,7 @@ cudaError_t noalloc_passes(const float *rho, float2 *spec, const float *gpad, fl
     const unsigned by = (unsigned)((int64_t)N * (kxp / L));
     fft_x_r2c<N><<<bx, Tile<N>::T, Tile<N>::SMEM, st>>>(rho, spec, nrows, kxp, tw);
     fft_y<N, false><<<by, Tile<N>::T, Tile<N>::SMEMY, st>>>(spec, kxp, tw);
-    fft_z<N, true><<<by, Tile<N>::T, Tile<N>::SMEMY, st>>>(spec, gpad, kxp, tw);
+    fft_z<N, 1><<<by, Tile<N>::T, Tile<N>::SMEMY, st>>>(spec, gpad, kxp, tw);
     fft_y<N, true><<<by, Tile<N>::T, Tile<N>::SMEMY, st>>>(spec, kxp, tw);
     fft_x_c2r<N><<<bx, Tile<N>::T, Tile<N>::SMEM, st>>>(spec, phi, nrows, kxp, tw);
     return cudaGetLastError();

@@ -8,7 +8,8 @@
 //           times 1 - sinc(|k_n| L_iso) when the level is isolated (Eq. isok)
 //   G     = -sum_n W^2 (d.k_n) dS2/|k_n|^2 / (|d|^2 [sum_n W^2]^2)
 // over the images |n_d| <= alias, and stores G / n^3 (the inverse FFT is
-// unnormalised).  G = 0 where |d| = 0.  The alias sum of W^2 factorises per
+// unnormalised) in the symmetry-reduced layout of green_index.  G = 0 where
+// |d| = 0.  The alias sum of W^2 factorises per
 // axis; the numerator does not and is summed image by image.
 #include "common.cuh"
 
@@ -59,38 +60,45 @@ __device__ double fd_weight(int m, int n) {
     return 4.0 / 3.0 * sinpi(t) - 1.0 / 6.0 * sinpi(2.0 * t);
 }
 
-__global__ void green_kernel(float *__restrict__ G, int n, int kxp, double b_soft, double b_trunc, double iso,
+// One entry of the reduced table per thread: entry idx holds the sorted
+// triple (a, b, c) of non-negative modes, evaluated as m = (a, b, c).
+__global__ void green_kernel(float *__restrict__ G, int n, double b_soft, double b_trunc, double iso,
                              int alias, int order, double norm) {
-    const int64_t total = (int64_t)n * n * kxp;
+    const int64_t total = green_table_len(n);
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= total) return;
-    const int kx = (int)(idx % kxp);
-    const int ky = (int)((idx / kxp) % n);
-    const int kz = (int)(idx / ((int64_t)kxp * n));
-    if (kx > n / 2) { G[idx] = 0.0f; return; }
-    const int m[3] = {kx, ky <= n / 2 ? ky : ky - n, kz <= n / 2 ? kz : kz - n};
+    // c: largest with c(c+1)(c+2)/6 <= idx; b: largest with b(b+1)/2 <= rest
+    int c = (int)cbrt(6.0 * (double)idx);
+    while ((int64_t)c * (c + 1) * (c + 2) / 6 > idx) --c;
+    while ((int64_t)(c + 1) * (c + 2) * (c + 3) / 6 <= idx) ++c;
+    const int64_t rest = idx - (int64_t)c * (c + 1) * (c + 2) / 6;
+    int b = (int)((sqrt(8.0 * (double)rest + 1.0) - 1.0) * 0.5);
+    while ((int64_t)b * (b + 1) / 2 > rest) --b;
+    while ((int64_t)(b + 1) * (b + 2) / 2 <= rest) ++b;
+    const int a = (int)(rest - (int64_t)b * (b + 1) / 2);
+    const int m[3] = {a, b, c};
     double d[3], d2 = 0.0;
-    for (int a = 0; a < 3; ++a) { d[a] = fd_weight(m[a], n); d2 += d[a] * d[a]; }
+    for (int ax = 0; ax < 3; ++ax) { d[ax] = fd_weight(m[ax], n); d2 += d[ax] * d[ax]; }
     if (d2 == 0.0) { G[idx] = 0.0f; return; }
     const double two_pi = 6.283185307179586476925286766559;
     const double pi = 3.141592653589793238462643383279;
     // per-axis image wavenumbers and squared assignment factors sinc^(2p)(k_n/2)
     double kn[3][2 * MAX_ALIAS + 1], w2[3][2 * MAX_ALIAS + 1];
     double den = 1.0;
-    for (int a = 0; a < 3; ++a) {
-        const double frac = (double)m[a] / (double)n;
+    for (int ax = 0; ax < 3; ++ax) {
+        const double frac = (double)m[ax] / (double)n;
         const double s = sinpi(frac);
         double sum = 0.0;
         for (int i = -alias; i <= alias; ++i) {
             const double u = frac + i;           // k_n / (2 pi)
-            kn[a][i + alias] = two_pi * u;
+            kn[ax][i + alias] = two_pi * u;
             double w;
             if (u == 0.0) w = 1.0;
             else {
                 const double sc = s / (pi * u), sc2 = sc * sc;
                 w = order == 3 ? sc2 * sc2 * sc2 : sc2 * sc2;   // W^2 = sinc^(2 order)
             }
-            w2[a][i + alias] = w;
+            w2[ax][i + alias] = w;
             sum += w;
         }
         den *= sum;
@@ -115,6 +123,16 @@ __global__ void green_kernel(float *__restrict__ G, int n, int kxp, double b_sof
     G[idx] = (float)(num / (d2 * den * den) * norm);
 }
 
+// Full half spectrum [kz][ky][kx <= n/2] from the reduced table.
+__global__ void green_expand_kernel(const float *__restrict__ G, float *__restrict__ out, int n) {
+    const int nh = n / 2 + 1;
+    const int64_t total = (int64_t)n * n * nh;
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= total) return;
+    const int kx = (int)(idx % nh), ky = (int)((idx / nh) % n), kz = (int)(idx / ((int64_t)nh * n));
+    out[idx] = G[green_index(kx, ky, kz, n)];
+}
+
 __global__ void twiddle_kernel(float2 *tw, int n) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n) return;
@@ -131,15 +149,22 @@ cudaError_t launch_init_twiddles(cube2_ctx *ctx, Level &L) {
     return cudaGetLastError();
 }
 
+cudaError_t launch_green_expand(cube2_ctx *ctx, const Level &L, float *out) {
+    const int64_t total = (int64_t)L.n * L.n * (L.n / 2 + 1);
+    green_expand_kernel<<<(unsigned)((total + 255) / 256), 256, 0, ctx->stream>>>(L.green, out, L.n);
+    ctx->launches++;
+    return cudaGetLastError();
+}
+
 cudaError_t launch_green(cube2_ctx *ctx, Level &L, int alias, int order) {
     if (alias > MAX_ALIAS) alias = MAX_ALIAS;
-    const int64_t total = (int64_t)L.n * L.n * L.kxp;
+    const int64_t total = green_table_len(L.n);
     const double norm = 1.0 / ((double)L.n * (double)L.n * (double)L.n);
     const int threads = 128;
     const int64_t blocks = (total + threads - 1) / threads;
     ProfScope prof(ctx, P_GREEN, L.index);
-    green_kernel<<<(unsigned)blocks, threads, 0, ctx->stream>>>(L.green, L.n, L.kxp, L.b_soft,
-                                                                 L.b_trunc, L.iso, alias, order, norm);
+    green_kernel<<<(unsigned)blocks, threads, 0, ctx->stream>>>(L.green, L.n, L.b_soft, L.b_trunc, L.iso, alias,
+                                                                 order, norm);
     ctx->launches++;
     return cudaGetLastError();
 }

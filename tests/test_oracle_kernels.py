@@ -86,9 +86,13 @@ def test_cic_alias_sum_matches_closed_form():
     assert np.allclose(s_full, exact, rtol=2e-8)
 
 
-@pytest.fixture(scope="module")
-def g24():
-    return K.green(24, 2.0, 9.0)
+@pytest.fixture(scope="module", params=["cic", "tsc-iso"])
+def g24(request):
+    # the symmetries the GPU's reduced table storage relies on, for CIC and
+    # for TSC with an isolated coarsest level
+    if request.param == "cic":
+        return K.green(24, 2.0, 9.0)
+    return K.green(24, 3.5, None, order=3, iso=5.0)
 
 
 def test_green_symmetries(g24):
