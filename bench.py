@@ -507,12 +507,21 @@ def run_adjoint(args):
         ta.append(time.perf_counter() - t0)
     ctx.check()
     fwd, adj = statistics.median(tf), statistics.median(ta)
+    # per-class kernel time of one more repetition of each, CUDA events, outside the timing
+    breakdown = {}
+    for name, fn in (("forward", forward), ("adjoint", adjoint)):
+        ctx.profile(capacity=5000)
+        fn()
+        prof = ctx.profile_read()
+        ctx.profile(0)
+        breakdown[name] = {f"{c}/{l}": round(ms, 3) for (c, l), (ms, _n) in
+                           sorted(prof.items(), key=lambda kv: -kv[1][0])}
     line = {
         "metric": "adjoint/forward time ratio (128^3 particles, 256^3 mesh, 10 KDK steps, density MSE loss)",
         "value": adj / fwd, "unit": "ratio", "higher_is_better": False, "n_gpus": 1, "steps": args.steps,
         "warmup": args.warmup, "forward_ms": 1e3 * fwd, "adjoint_ms": 1e3 * adj, "loss": loss,
         "loss_in_adjoint_run": loss_a, "grad_x_rms": float(gx.pow(2).mean().sqrt()),
-        "grad_v_rms": float(gv.pow(2).mean().sqrt()), "dtype": "f32",
+        "grad_v_rms": float(gv.pow(2).mean().sqrt()), "kernels_ms_per_repetition": breakdown, "dtype": "f32",
         "data": "synthetic (seeded Zel'dovich ICs, BBKS spectrum; target = seed 4 final overdensity)",
         "config": {"workload": ADJOINT, "particles": n_part, "mesh": 256, "kdk_steps": len(a) - 1,
                    "z": f"{w.z_init:g} -> {w.z_final:g}", "gradient": "dL/dx0 and dL/dv0",

@@ -231,7 +231,7 @@ const char *cube2_last_error(cube2_ctx *ctx);
  * counts[...] (arrays of CUBE2_PROFILE_CLASSES * CUBE2_MAX_LEVELS), clears the
  * records, and returns CUBE2_ERR_CAPACITY if the pool overflowed.  Class
  * names: cube2_profile_class_name. */
-#define CUBE2_PROFILE_CLASSES 19
+#define CUBE2_PROFILE_CLASSES 23
 int cube2_profile(cube2_ctx *ctx, int cap);
 int cube2_profile_read(cube2_ctx *ctx, double *ms, int64_t *counts);
 const char *cube2_profile_class_name(int cls);

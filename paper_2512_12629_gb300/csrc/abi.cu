@@ -803,7 +803,7 @@ const char *cube2_profile_class_name(int cls) {
     static const char *names[CUBE2_PROFILE_CLASSES] = {
         "deposit", "fft_x_fwd", "fft_y_fwd", "fft_z_green", "fft_y_inv", "fft_x_inv", "interp", "pp",
         "kick", "kick_drift", "scan", "scatter", "sort", "gather", "cellid", "green", "pp_order", "prep",
-        "sort_big"};
+        "sort_big", "vjp_gather", "vjp_source", "pp_vjp", "adj_kdk"};
     return (cls >= 0 && cls < CUBE2_PROFILE_CLASSES) ? names[cls] : "";
 }
 

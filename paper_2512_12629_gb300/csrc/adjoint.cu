@@ -241,6 +241,7 @@ cudaError_t launch_kdk_adjoint_scatter(cube2_ctx *ctx, const int32_t *perm, floa
     // xbar/pbar are three separate arrays: gather them through the scratch rows
     const int64_t N = ctx->N;
     if (N == 0) return cudaSuccess;
+    ProfScope prof(ctx, P_ADJ_KDK, 0);
     float *xs = ctx->vjp_u, *ps = ctx->vjp_u + 3 * N, *xc = ctx->vjp_u + 6 * N;
     cudaError_t e = cudaSuccess;
     for (int d = 0; d < 3 && e == cudaSuccess; ++d) {
@@ -258,6 +259,7 @@ cudaError_t launch_kdk_adjoint_scatter(cube2_ctx *ctx, const int32_t *perm, floa
 cudaError_t launch_kdk_adjoint_drift(cube2_ctx *ctx, float *const xbar[3], float *const pbar[3], float drift) {
     const int64_t N = ctx->N;
     if (N == 0) return cudaSuccess;
+    ProfScope prof(ctx, P_ADJ_KDK, 0);
     Ptr3 X{{xbar[0], xbar[1], xbar[2]}}, Pb{{pbar[0], pbar[1], pbar[2]}};
     kdk_adjoint_drift3_kernel<<<(unsigned)((N + 255) / 256), 256, 0, ctx->stream>>>(ctx->vjp_u, ctx->vjp_u + 3 * N, X,
                                                                                    Pb, N, drift);
@@ -278,6 +280,7 @@ cudaError_t launch_axpy3(cube2_ctx *ctx, float *const y[3], const float *t, floa
 cudaError_t launch_vjp_gather_e(cube2_ctx *ctx, Level &L, const cube2_particles *p, const float *const v[3],
                                 float *const w[3]) {
     if (ctx->N == 0) return cudaSuccess;
+    ProfScope prof(ctx, P_VJP_GATHER, L.index);
     VjpParams P = make_params(ctx, L, p, v, w, L.real);
     vjp_gather_kernel<true><<<(unsigned)((ctx->N + 255) / 256), 256, 0, ctx->stream>>>(P);
     ctx->launches++;
@@ -288,6 +291,7 @@ cudaError_t launch_vjp_gather_e(cube2_ctx *ctx, Level &L, const cube2_particles 
 cudaError_t launch_vjp_gather_psi(cube2_ctx *ctx, Level &L, const cube2_particles *p, const float *const v[3],
                                   float *const w[3]) {
     if (ctx->N == 0) return cudaSuccess;
+    ProfScope prof(ctx, P_VJP_GATHER, L.index);
     VjpParams P = make_params(ctx, L, p, v, w, L.real);
     vjp_gather_kernel<false><<<(unsigned)((ctx->N + 255) / 256), 256, 0, ctx->stream>>>(P);
     ctx->launches++;
@@ -297,6 +301,7 @@ cudaError_t launch_vjp_gather_psi(cube2_ctx *ctx, Level &L, const cube2_particle
 // L.real = (n^3/N) sum_d D_d * mu_d with mu_d the CIC deposit of v_d.
 cudaError_t launch_vjp_source(cube2_ctx *ctx, Level &L, const cube2_particles *p, const float *const v[3]) {
     const int64_t n3 = (int64_t)L.n * L.n * L.n;
+    ProfScope prof(ctx, P_VJP_SOURCE, L.index);
     cudaError_t e = cudaMemsetAsync(ctx->vjp_mu, 0, sizeof(float) * 3 * n3, ctx->stream);
     if (e != cudaSuccess) return e;
     if (ctx->N > 0) {

@@ -29,6 +29,7 @@ enum ProfClass : int {
     P_DEPOSIT = 0, P_FFT_X_FWD, P_FFT_Y_FWD, P_FFT_Z_GREEN, P_FFT_Y_INV, P_FFT_X_INV,
     P_INTERP, P_PP, P_KICK, P_KICK_DRIFT, P_SCAN, P_SCATTER, P_SORT, P_GATHER, P_CELLID, P_GREEN,
     P_PP_ORDER, P_PREP, P_SORT_BIG,
+    P_VJP_GATHER, P_VJP_SOURCE, P_PP_VJP, P_ADJ_KDK,   // adjoint: PM gathers, cotangent source, PP product, reverse KDK
     P_NCLASS
 };
 

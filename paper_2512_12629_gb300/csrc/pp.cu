@@ -523,19 +523,26 @@ struct VjpIO {
 
 // PP part of the vector-Jacobian product: w_i += sum_j A_ij (v_j - v_i) with
 // A_ij = g I + (g'/r) d d^T (the force's Jacobian blocks are symmetric).
-// Each lane walks its target's 27 cells as in the per-lane force path.
-#ifndef PPV_MINB
-#define PPV_MINB 1
-#endif
-__global__ void __launch_bounds__(PP_CTA, PPV_MINB) pp_vjp_kernel(PPParams P, VjpIO V) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= P.N) return;
+// Warps are dispatched as in the force: a warp inside one narrow row shares a
+// source stream (positions and v_j staged together, the candidate test and
+// set-bit evaluation of the force), other warps walk each lane's 27 cells.
+
+__device__ __forceinline__ void jacobian_term(float rx, float ry, float rz, float r2, float4 vj, float vix, float viy,
+                                              float viz, const PPParams &P, float &px, float &py, float &pz) {
+    float gc, gp;
+    pp_jacobian_pair(r2, P.inv_bpp, P.inv_bcut, P.bpp2, gc, gp);
+    const float dvx = vj.x - vix, dvy = vj.y - viy, dvz = vj.z - viz;
+    const float dd = gp * (rx * dvx + ry * dvy + rz * dvz);
+    px += gc * dvx + dd * rx;
+    py += gc * dvy + dd * ry;
+    pz += gc * dvz + dd * rz;
+}
+
+__device__ void lane_vjp(const PPParams &P, const VjpIO &V, bool has, int c, float4 me, float vix, float viy,
+                         float viz, Sum3 &a) {
+    if (!has) return;
     const int n = P.n_ios;
-    const float4 me = P.pos[i];
-    const int c = __float_as_int(me.w);
     const int cx = c % n, cy = (c / n) % n, cz = c / (n * n);
-    const float vix = V.v0[i], viy = V.v1[i], viz = V.v2[i];
-    Sum3 a;
     for (int dz = -1; dz <= 1; ++dz)
         for (int dy = -1; dy <= 1; ++dy) {
             const int64_t r = ((int64_t)wrap(cz + dz, n) * n + wrap(cy + dy, n)) * n;
@@ -551,22 +558,100 @@ __global__ void __launch_bounds__(PP_CTA, PPV_MINB) pp_vjp_kernel(PPParams P, Vj
                     const float rz = (fdz + q.z) - me.z;
                     const float r2 = rx * rx + ry * ry + rz * rz;
                     if (r2 < P.bcut2 && r2 > 0.0f) {
-                        float gc, gp;
-                        pp_jacobian_pair(r2, P.inv_bpp, P.inv_bcut, P.bpp2, gc, gp);
-                        const float dvx = __ldg(&V.v0[j]) - vix, dvy = __ldg(&V.v1[j]) - viy,
-                                    dvz = __ldg(&V.v2[j]) - viz;
-                        const float dd = gp * (rx * dvx + ry * dvy + rz * dvz);
-                        px += gc * dvx + dd * rx;
-                        py += gc * dvy + dd * ry;
-                        pz += gc * dvz + dd * rz;
+                        const float4 vj = make_float4(__ldg(&V.v0[j]), __ldg(&V.v1[j]), __ldg(&V.v2[j]), 0.f);
+                        jacobian_term(rx, ry, rz, r2, vj, vix, viy, viz, P, px, py, pz);
                     }
                 }
             }
             a.add_block(px, py, pz);
         }
-    V.w0[i] += V.scale * (a.x - a.cx);
-    V.w1[i] += V.scale * (a.y - a.cy);
-    V.w2[i] += V.scale * (a.z - a.cz);
+}
+
+// The particle index of stream position p (-1 past the end); s as in stage_source.
+__device__ __forceinline__ int stream_index(const WarpSegs &W, int p, int &s) {
+    if (p >= W.cum[PP_SEGS]) return -1;
+    while (p >= W.cum[s + 1]) ++s;
+    return W.beg[s] + (p - W.cum[s]);
+}
+
+__device__ void union_vjp(const PPParams &P, const VjpIO &V, const WarpSegs &W, float4 *S, float4 *SV, int64_t i,
+                          bool has, int c0, int xa, float4 me, float vix, float viy, float viz, Sum3 &a) {
+    const int lane = threadIdx.x & 31;
+    const int n = P.n_ios;
+    const int total = W.cum[PP_SEGS];
+    const int pself = has ? W.cum[8] + (int)(i - W.beg[8]) : -1000;
+    const int cx = (has ? __float_as_int(me.w) : c0) % n;
+    const float mx = (float)(cx - xa) + me.x, my = me.y + 1.0f, mz = me.z + 1.0f;
+    const float bcut2 = P.bcut2;
+    int sa = 0, sb = 0, ta = 0, tb = 0;
+    for (int b0 = 0; b0 < total; b0 += 64) {
+        S[lane] = stage_source(P, W, b0 + lane, sa);
+        S[32 + lane] = stage_source(P, W, b0 + 32 + lane, sb);
+        const int ja = stream_index(W, b0 + lane, ta), jb = stream_index(W, b0 + 32 + lane, tb);
+        SV[lane] = ja >= 0 ? make_float4(__ldg(&V.v0[ja]), __ldg(&V.v1[ja]), __ldg(&V.v2[ja]), 0.f)
+                           : make_float4(0.f, 0.f, 0.f, 0.f);
+        SV[32 + lane] = jb >= 0 ? make_float4(__ldg(&V.v0[jb]), __ldg(&V.v1[jb]), __ldg(&V.v2[jb]), 0.f)
+                                : make_float4(0.f, 0.f, 0.f, 0.f);
+        __syncwarp();
+        unsigned mh = test32(S, mx, my, mz, bcut2), ml = test32(S + 32, mx, my, mz, bcut2);
+        const int ts = pself - b0;
+        if (ts >= 0 && ts < 32) mh &= ~(0x80000000u >> ts);
+        if (ts >= 32 && ts < 64) ml &= ~(0x80000000u >> (ts - 32));
+        if (!has) mh = ml = 0u;
+        float px = 0.f, py = 0.f, pz = 0.f;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            unsigned m = h ? ml : mh;
+            const float4 *SB = S + 32 * h, *SVB = SV + 32 * h;
+            while (m) {
+                const int k = __clz(m);
+                m ^= 0x80000000u >> k;
+                const float4 q = SB[k];
+                const float rx = q.x - mx, ry = q.y - my, rz = q.z - mz;
+                const float r2 = rx * rx + ry * ry + rz * rz;
+                if (r2 > 0.0f) jacobian_term(rx, ry, rz, r2, SVB[k], vix, viy, viz, P, px, py, pz);
+            }
+        }
+        a.add_block(px, py, pz);
+        __syncwarp();
+    }
+}
+
+struct PPVjpWarpShared {
+    float4 buf[64];   // staged source positions
+    float4 vbuf[64];  // and their v_j
+    WarpSegs seg;
+};
+
+#ifndef PPV_MINB
+#define PPV_MINB 1
+#endif
+__global__ void __launch_bounds__(PP_CTA, PPV_MINB) pp_vjp_kernel(PPParams P, VjpIO V) {
+    __shared__ PPVjpWarpShared sh[PP_WARPS_CTA];
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int wib = threadIdx.x >> 5;
+    const bool has = i < P.N;
+    const int n = P.n_ios;
+    const float4 me = has ? P.pos[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+    int c = has ? __float_as_int(me.w) : -1;
+    const int c0 = __shfl_sync(0xffffffffu, c, 0);
+    if (!has) c = c0;
+    const int c31 = __reduce_max_sync(0xffffffffu, c);
+    const int xa = c0 % n, xb = c31 % n;
+    const bool one_row = (c0 / n) == (c31 / n) && xb - xa <= PP_WMAX && xb - xa + 3 <= n;
+    const float vix = has ? V.v0[i] : 0.f, viy = has ? V.v1[i] : 0.f, viz = has ? V.v2[i] : 0.f;
+    Sum3 a;
+    if (one_row) {
+        build_segments(P, sh[wib].seg, c0, xa, xb);
+        union_vjp(P, V, sh[wib].seg, sh[wib].buf, sh[wib].vbuf, i, has, c0, xa, me, vix, viy, viz, a);
+    } else {
+        lane_vjp(P, V, has, c, me, vix, viy, viz, a);
+    }
+    if (has) {
+        V.w0[i] += V.scale * (a.x - a.cx);
+        V.w1[i] += V.scale * (a.y - a.cy);
+        V.w2[i] += V.scale * (a.z - a.cz);
+    }
 }
 
 // Full occupancy (16 CTAs of 4 warps, 32 registers): the per-lane walk is
@@ -614,6 +699,7 @@ cudaError_t launch_pp_vjp(cube2_ctx *ctx, const cube2_particles *p, const float 
     V.v0 = v[0]; V.v1 = v[1]; V.v2 = v[2];
     V.w0 = w[0]; V.w1 = w[1]; V.w2 = w[2];
     V.scale = (float)((double)P.coef / ctx->s_ios);
+    ProfScope prof(ctx, P_PP_VJP, 0);
     const int nblocks = (int)((ctx->N + PP_CTA - 1) / PP_CTA);
     prep_positions_kernel<<<(unsigned)nblocks, PP_CTA, 0, ctx->stream>>>(p->off[0], p->off[1], p->off[2], ctx->cellid,
                                                                        ctx->pos4, nullptr, ctx->N);

@@ -28,7 +28,7 @@ ERR_UNSUPPORTED_SIZE = -6
 ERR_STATE = -7
 ERR_DISPLACEMENT = -8
 MAX_LEVELS = 2
-PROFILE_CLASSES = 19
+PROFILE_CLASSES = 23
 
 
 class Cube2Error(RuntimeError):
