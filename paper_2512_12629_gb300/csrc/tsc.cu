@@ -65,12 +65,30 @@ __global__ void __launch_bounds__(256) fill_kernel(float *g, int64_t n, float v)
     if (i < n) g[i] = v;
 }
 
+// Particles are in IOS order, so on a coarse level the lanes of a warp come in
+// runs that share the cell holding them, and with it all 27 target cells.  A
+// warp with runs (at most 16 distinct cells) sums each target's weights over
+// every run with a segmented shuffle scan and lets the run's last lane add the
+// total; other warps add per lane.
 __global__ void __launch_bounds__(256) tsc_deposit_kernel(TscParams P) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= P.N) return;
+    const bool has = i < P.N;
+    const int lane = threadIdx.x & 31;
     TscAxis a[3];
-    particle_axes(P, i, a);
+    if (has) {
+        particle_axes(P, i, a);
+    } else {
+#pragma unroll
+        for (int d = 0; d < 3; ++d) a[d] = TscAxis{0, {0.f, 0.f, 0.f}};
+    }
     const int n = P.n;
+    const long long key = has ? ((long long)a[2].i * n + a[1].i) * n + a[0].i : -1ll;
+    const long long prev = __shfl_up_sync(0xffffffffu, key, 1), next = __shfl_down_sync(0xffffffffu, key, 1);
+    const bool head = lane == 0 || prev != key;
+    const bool tail = lane == 31 || next != key;
+    const unsigned heads = __ballot_sync(0xffffffffu, head);
+    const bool agg = __popc(heads) <= 16;
+    const int s0 = 31 - __clz(heads & (0xffffffffu >> (31 - lane)));   // first lane of this lane's run
 #pragma unroll
     for (int jz = 0; jz < 3; ++jz) {
         const int64_t z = wrapc(a[2].i + jz - 1, n);
@@ -80,7 +98,19 @@ __global__ void __launch_bounds__(256) tsc_deposit_kernel(TscParams P) {
             const int64_t row = (z * n + wrapc(a[1].i + jy - 1, n)) * n;
             const float wyz = wz * a[1].w[jy];
 #pragma unroll
-            for (int jx = 0; jx < 3; ++jx) atomicAdd(&P.grid[row + wrapc(a[0].i + jx - 1, n)], wyz * a[0].w[jx]);
+            for (int jx = 0; jx < 3; ++jx) {
+                float v = wyz * a[0].w[jx];
+                if (agg) {
+#pragma unroll
+                    for (int d = 1; d < 32; d <<= 1) {
+                        const float u = __shfl_up_sync(0xffffffffu, v, d);
+                        if (lane - d >= s0) v += u;
+                    }
+                    if (has && tail) atomicAdd(&P.grid[row + wrapc(a[0].i + jx - 1, n)], v);
+                } else if (has) {
+                    atomicAdd(&P.grid[row + wrapc(a[0].i + jx - 1, n)], v);
+                }
+            }
         }
     }
 }
