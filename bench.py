@@ -772,6 +772,26 @@ def main():
                "h2d_bytes_per_step": bytes_step, "d2h_bytes_per_step": bytes_step,
                "api": "cube2_kdk_step_host (pinned host state, H2D + step + D2H each step)"}
 
+    # cuFFT (through torch.fft), timed only as a comparison with the library's own
+    # FFT passes of the finest level: r2c + c2r of the same n^3 FP32 grid
+    cufft = None
+    if rank == 0:
+        nf = w.levels[-1].n_mesh
+        own = sum(kms / kc for (c, l), (kms, kc) in prof.items() if c.startswith("fft_") and l == len(w.levels) - 1)
+        grid = torch.randn((nf, nf, nf), device="cuda", generator=torch.Generator(device="cuda").manual_seed(3))
+        for _ in range(2):
+            torch.fft.irfftn(torch.fft.rfftn(grid), s=grid.shape)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = 5
+        e0.record()
+        for _ in range(reps):
+            torch.fft.irfftn(torch.fft.rfftn(grid), s=grid.shape)
+        e1.record()
+        torch.cuda.synchronize()
+        cufft = {"n": nf, "torch_cufft_r2c_c2r_ms": e0.elapsed_time(e1) / reps, "own_fft_passes_ms": own,
+                 "note": "own passes include the Green's multiply (fused into the z pass); cuFFT is not on the path"}
+        del grid
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, k, el, desc = oracle_sample(w, args.cpu_seconds)
@@ -785,7 +805,7 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic (seeded Zel'dovich ICs, BBKS spectrum)", "config": workload_config(w),
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-            "clocks": clk, "kernels": kernels,
+            "clocks": clk, "kernels": kernels, "cufft_comparison": cufft,
         }
         print(json.dumps(line), flush=True)
     if dist:

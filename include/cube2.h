@@ -181,6 +181,21 @@ int cube2_kdk_step(cube2_ctx *ctx, cube2_particles *p, double a0, double a1);
 int cube2_kdk_step_host(cube2_ctx *ctx, cube2_particles *dev, cube2_particles *host,
                         double a0, double a1);
 
+/* Information Optimized Storage from arbitrary positions (Sec. 2.3: a particle
+ * is its cell, given by its place in the cell-sorted order and the per-cell
+ * counts, plus uint16 offsets inside the cell).  pos: three device FP64 [N]
+ * arrays of comoving positions [Mpc/h], any real values (wrapped into the
+ * periodic box); mom: three device FP32 [N] momentum arrays, or NULL for
+ * zero momenta.  X_d = rint(x_d / s_ios * 2^16) mod n_ios 2^16 (FP64, round
+ * half to even), cell = floor(X/2^16), offset = X mod 2^16; particles are
+ * stably sorted by cell (ties keep the input order).  Writes p->off, p->vel,
+ * p->count, p->start (p->acc untouched) and, when perm is not NULL, perm[j] =
+ * the input index of IOS slot j (device int32 [N]).  Non-finite or enormous
+ * positions set CUBE2_ERR_NONFINITE in the sticky status (cube2_check).  The
+ * entry of a differentiable run: gradients in IOS order map back through perm. */
+int cube2_ios_from_positions(cube2_ctx *ctx, const double *const pos[3], const float *const mom[3],
+                             cube2_particles *p, int32_t *perm);
+
 /* Test/diagnostic copies of internal grids into caller device buffers:
  * density after cube2_deposit, potential after cube2_solve_pm ([n][n][n]
  * FP32), Green's table (expanded from the reduced layout to [n][n][n/2+1]

@@ -474,6 +474,22 @@ int cube2_kdk_step(cube2_ctx *ctx, cube2_particles *p, double a0, double a1) {
     return kdk_step_core(ctx, p, a0, a1, nullptr);
 }
 
+int cube2_ios_from_positions(cube2_ctx *ctx, const double *const pos[3], const float *const mom[3],
+                             cube2_particles *p, int32_t *perm) {
+    if (!ctx) return CUBE2_ERR_BAD_ARG;
+    if (!particles_ok(ctx, p, true, false)) return set_error(ctx, CUBE2_ERR_BAD_ARG, "bad particle arrays");
+    if (ctx->N > 0 && (!pos || !pos[0] || !pos[1] || !pos[2]))
+        return set_error(ctx, CUBE2_ERR_BAD_ARG, "null position arrays");
+    if (ctx->N > 0 && mom && (!mom[0] || !mom[1] || !mom[2]))
+        return set_error(ctx, CUBE2_ERR_BAD_ARG, "momenta must be three arrays or null");
+    cudaError_t e = launch_place(ctx, pos, mom);
+    if (e == cudaSuccess) e = launch_rebin(ctx, p);
+    if (e == cudaSuccess && perm && ctx->N > 0)
+        e = cudaMemcpyAsync(perm, ctx->perm, sizeof(int32_t) * (size_t)ctx->N, cudaMemcpyDeviceToDevice, ctx->stream);
+    if (e != cudaSuccess) return cuda_error(ctx, e, "ios_from_positions");
+    return CUBE2_OK;
+}
+
 int cube2_adjoint_init(cube2_ctx *ctx) {
     if (!ctx) return CUBE2_ERR_BAD_ARG;
     if (ctx->vjp_mu) return CUBE2_OK;

@@ -153,6 +153,7 @@ cudaError_t launch_kick(cube2_ctx *ctx, const cube2_particles *p, float kick);
 cudaError_t launch_kick_drift(cube2_ctx *ctx, const cube2_particles *p, float kick, float drift_fix);
 cudaError_t launch_scan(cube2_ctx *ctx, const int32_t *in, int32_t *out, int64_t n);
 cudaError_t launch_rebin(cube2_ctx *ctx, const cube2_particles *p);
+cudaError_t launch_place(cube2_ctx *ctx, const double *const pos[3], const float *const mom[3]);
 int64_t scan_scratch_len(int64_t n);
 // force vector-Jacobian product
 cudaError_t launch_vjp_gather_e(cube2_ctx *ctx, Level &L, const cube2_particles *p, const float *const v[3],

@@ -87,6 +87,53 @@ __global__ void __launch_bounds__(256) kick_drift_kernel(DriftParams P) {
     P.tslot[i] = slot;
 }
 
+// Placement of arbitrary positions into IOS (the entry of a differentiable
+// run): X_d = rint(x_d / s_ios * 2^16) mod n_ios 2^16 in FP64 (round half to
+// even), then the same stable counting sort as the re-bin, ties in input order.
+struct PlaceParams {
+    const double *pos0, *pos1, *pos2;
+    const float *mom0, *mom1, *mom2;   // may be null: zero momenta
+    int32_t *count;
+    uint16_t *toff;
+    float *tvel;
+    int32_t *tcell, *tslot;
+    int64_t N;
+    int n_ios;
+    double s_ios;
+    int *status;
+};
+
+__global__ void __launch_bounds__(256) place_kernel(PlaceParams P) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= P.N) return;
+    const int n = P.n_ios;
+    const int64_t period = (int64_t)n * FIX;
+    const double x[3] = {P.pos0[i], P.pos1[i], P.pos2[i]};
+    int nc[3];
+    uint16_t no[3];
+    bool bad = false;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const double u = rint(x[a] / P.s_ios * (double)FIX);
+        if (!(fabs(u) < 4.0e18)) bad = true;   // also catches NaN
+        int64_t X = bad ? 0 : (int64_t)u % period;
+        if (X < 0) X += period;
+        nc[a] = (int)(X >> FIX_BITS);
+        no[a] = (uint16_t)(X & (FIX - 1));
+    }
+    if (bad) set_status(P.status, ST_NONFINITE);
+    const int cell = (nc[2] * n + nc[1]) * n + nc[0];
+    const int slot = atomicAdd(&P.count[cell], 1);
+    P.toff[i] = no[0];
+    P.toff[P.N + i] = no[1];
+    P.toff[2 * P.N + i] = no[2];
+    P.tvel[i] = P.mom0 ? P.mom0[i] : 0.0f;
+    P.tvel[P.N + i] = P.mom1 ? P.mom1[i] : 0.0f;
+    P.tvel[2 * P.N + i] = P.mom2 ? P.mom2[i] : 0.0f;
+    P.tcell[i] = cell;
+    P.tslot[i] = slot;
+}
+
 // -------------------------------------------------------------- scan
 __device__ __forceinline__ int block_exclusive_scan(int v, int *warp_sums, int &total) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -346,6 +393,28 @@ cudaError_t launch_kick_drift(cube2_ctx *ctx, const cube2_particles *p, float ki
     const int64_t blocks = (ctx->N + 255) / 256;
     if (blocks == 0) return cudaSuccess;
     kick_drift_kernel<<<(unsigned)blocks, 256, 0, ctx->stream>>>(P);
+    ctx->launches++;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_place(cube2_ctx *ctx, const double *const pos[3], const float *const mom[3]) {
+    PlaceParams P{};
+    P.pos0 = pos[0]; P.pos1 = pos[1]; P.pos2 = pos[2];
+    if (mom) { P.mom0 = mom[0]; P.mom1 = mom[1]; P.mom2 = mom[2]; }
+    P.count = ctx->ncount;
+    P.toff = ctx->toff;
+    P.tvel = ctx->tvel;
+    P.tcell = ctx->tcell;
+    P.tslot = ctx->tslot;
+    P.N = ctx->N;
+    P.n_ios = ctx->n_ios;
+    P.s_ios = ctx->s_ios;
+    P.status = ctx->dev_status;
+    cudaError_t e = cudaMemsetAsync(ctx->ncount, 0, sizeof(int32_t) * ctx->n_cells, ctx->stream);
+    if (e != cudaSuccess) return e;
+    const int64_t blocks = (ctx->N + 255) / 256;
+    if (blocks == 0) return cudaSuccess;
+    place_kernel<<<(unsigned)blocks, 256, 0, ctx->stream>>>(P);
     ctx->launches++;
     return cudaGetLastError();
 }

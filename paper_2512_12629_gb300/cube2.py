@@ -80,6 +80,7 @@ def _load():
         "cube2_pp_force": (I, [P, ctypes.POINTER(Particles), I]),
         "cube2_force": (I, [P, ctypes.POINTER(Particles)]),
         "cube2_kdk_step": (I, [P, ctypes.POINTER(Particles), D, D]),
+        "cube2_ios_from_positions": (I, [P, P, P, ctypes.POINTER(Particles), P]),
         "cube2_kdk_step_host": (I, [P, ctypes.POINTER(Particles), ctypes.POINTER(Particles), D, D]),
         "cube2_get_density": (I, [P, I, P]),
         "cube2_get_potential": (I, [P, I, P]),
@@ -296,6 +297,31 @@ class Context:
     def kdk_step(self, p: IOSState, a0, a1):
         self._chk(_lib.cube2_kdk_step(self.ptr, ctypes.byref(p.struct()), float(a0), float(a1)))
 
+    def ios_from_positions(self, pos: torch.Tensor, mom: torch.Tensor = None, out: IOSState = None,
+                           perm: torch.Tensor = None):
+        """IOS state of positions pos (3, N) FP64 [Mpc/h] and momenta mom (3, N)
+        FP32 (None: zero), on the device: (state, perm) with perm[j] (int32) the
+        input index of IOS slot j; the state's acc is zero."""
+        n, nc = int(self.cfg.n_particles), int(self.cfg.n_ios) ** 3
+        if pos.dtype != torch.float64 or pos.shape != (3, n) or not pos.is_cuda:
+            raise ValueError("pos must be a (3, N) float64 CUDA tensor")
+        pos = pos.contiguous()
+        if mom is not None:
+            if mom.dtype != torch.float32 or mom.shape != (3, n) or not mom.is_cuda:
+                raise ValueError("mom must be a (3, N) float32 CUDA tensor")
+            mom = mom.contiguous()
+        if out is None:
+            dev = pos.device
+            out = IOSState(torch.empty((3, n), dtype=torch.int16, device=dev), torch.empty(nc, dtype=torch.int32, device=dev),
+                           torch.empty(nc, dtype=torch.int32, device=dev), torch.empty((3, n), dtype=torch.float32, device=dev),
+                           torch.zeros((3, n), dtype=torch.float32, device=dev))
+        if perm is None:
+            perm = torch.empty(n, dtype=torch.int32, device=pos.device)
+        pp = (ctypes.c_void_p * 3)(*[pos[d].data_ptr() for d in range(3)])
+        mp = None if mom is None else (ctypes.c_void_p * 3)(*[mom[d].data_ptr() for d in range(3)])
+        self._chk(_lib.cube2_ios_from_positions(self.ptr, pp, mp, ctypes.byref(out.struct()), perm.data_ptr()))
+        return out, perm
+
     def kdk_step_host(self, dev: IOSState, host: IOSState, a0, a1):
         self._chk(_lib.cube2_kdk_step_host(self.ptr, ctypes.byref(dev.struct()), ctypes.byref(host.struct()),
                                            float(a0), float(a1)))
@@ -505,3 +531,60 @@ def loss_gradient(ctx: Context, p0: IOSState, target: torch.Tensor, a, level=-1)
 
 def force_vjp(ctx: Context, p: IOSState, v, out=None):
     return ctx.force_vjp(p, v, out)
+
+
+def ios_from_positions(ctx: Context, pos, mom=None, out=None, perm=None):
+    return ctx.ios_from_positions(pos, mom, out, perm)
+
+
+class FinalDensity(torch.autograd.Function):
+    """The final overdensity of one level after len(a) - 1 KDK steps as a
+    differentiable function of the initial positions x0 ((3, N) FP64, Mpc/h)
+    and momenta v0 ((3, N) FP32), in the caller's particle order.
+
+    Forward: cube2_ios_from_positions, the force, the steps (a checkpoint and
+    re-bin map kept per step), cube2_deposit of the final state.  Backward, for
+    a cotangent g on the density: cube2_density_mse_vjp with the target
+    delta - g n^3 / 2 (its cotangent 2 (delta - target) / n^3 is then g), the
+    reverse sweep cube2_kdk_adjoint, and the gradients put back into the input
+    order through the placement's permutation.  The IOS quantisation of x0 and
+    the drift's rounding are taken as the identity (the gradient of the
+    continuous map at the stored positions)."""
+
+    @staticmethod
+    def forward(fctx, x0, v0, ctx, a, level):
+        ctx.adjoint_init()
+        p, perm = ctx.ios_from_positions(x0.detach(), v0.detach())
+        ctx.force(p)
+        states, perms = [p], []
+        q = p.clone()
+        for k in range(len(a) - 1):
+            ctx.kdk_step(q, a[k], a[k + 1])
+            perms.append(ctx.kdk_permutation())
+            states.append(q.clone())
+        ctx.deposit(level, states[-1])
+        delta = ctx.get_density(level).clone()
+        fctx.sim = (ctx, list(a), level, states, perms, perm, delta)
+        fctx.dtypes = (x0.dtype, v0.dtype)
+        return delta
+
+    @staticmethod
+    def backward(fctx, g):
+        ctx, a, level, states, perms, perm, delta = fctx.sim
+        n3 = delta.numel()
+        target = (delta - g.to(delta.dtype) * (n3 / 2.0)).contiguous()
+        _, xbar = ctx.density_mse_vjp(level, states[-1], target)
+        pbar = torch.zeros_like(xbar)
+        ctx.kdk_adjoint(states, perms, a, xbar, pbar)
+        idx = perm.long()
+        gx = torch.zeros(xbar.shape, dtype=fctx.dtypes[0], device=xbar.device)
+        gv = torch.zeros(pbar.shape, dtype=fctx.dtypes[1], device=pbar.device)
+        gx[:, idx] = xbar.to(gx.dtype)
+        gv[:, idx] = pbar.to(gv.dtype)
+        return gx, gv, None, None, None
+
+
+def final_density(ctx: Context, x0, v0, a, level=-1):
+    """Differentiable final overdensity (FinalDensity.apply)."""
+    level = ctx.cfg.n_levels - 1 if level < 0 else level
+    return FinalDensity.apply(x0, v0, ctx, a, level)
