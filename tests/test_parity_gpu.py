@@ -45,6 +45,7 @@ def rel_err(f_gpu, f_or):
 def assert_force_close(f_gpu, f_or, what=""):
     rel = rel_err(np.asarray(f_gpu, np.float64), f_or)
     med, p999 = np.median(rel), np.quantile(rel, 0.999)
+    print(f"\n  force error {what}: median {med:.2e}, 99.9th percentile {p999:.2e} (N = {rel.size})")
     assert med <= MEDIAN_TOL and p999 <= P999_TOL, f"{what}: median {med:.3e}, p99.9 {p999:.3e}"
 
 
@@ -165,7 +166,7 @@ def test_pm_and_pp_forces_match_oracle(name):
         ctx.interp_force(l, p, accumulate=False)
         n, h, _, _ = params[l]
         ref, _ = omesh.pm_force_level(st["off"], st["count"], w.n_ios, n, h, greens[l])
-        assert_force_close(p.acc.cpu().numpy(), ref, f"PM level {l}")
+        assert_force_close(p.acc.cpu().numpy(), ref, f"{name} PM level {l}")
     b_pp, b_cut = okdk.pp_params(w)
     ctx.pp_force(p, accumulate=False)
     ref = opp.pp_force(st["off"], st["count"], st["start"], w.n_ios, w.box, b_pp, b_cut)
@@ -177,7 +178,7 @@ def test_pm_and_pp_forces_match_oracle(name):
     err = np.linalg.norm(got - ref, axis=0)
     bound = 1e-5 * (pair_scale + np.linalg.norm(ref, axis=0))
     assert np.all(err <= bound), (err / bound).max()
-    assert_force_close(got, ref, "PP")
+    assert_force_close(got, ref, f"{name} PP")
     ctx.check()
 
 
@@ -188,7 +189,7 @@ def test_total_force_matches_oracle(name):
     ctx.force(p)
     ctx.check()
     ref = okdk.total_force(st["off"], st["count"], st["start"], w, greens)
-    assert_force_close(p.acc.cpu().numpy(), ref, "total force")
+    assert_force_close(p.acc.cpu().numpy(), ref, f"{name} total force")
 
 
 def test_force_conserves_momentum_and_is_deterministic():
