@@ -198,14 +198,18 @@ def algorithmic_bytes(w, n_part, cls, level):
     meshes = [lv.n_mesh for lv in w.levels]
     n = meshes[level] if level < len(meshes) else meshes[-1]
     half = n * n * (n // 2 + 1)
+    m = n // 2 + 1
+    green_len = m * (m + 1) * (m + 2) // 6           # the symmetry-reduced Green's table
+    tsc = getattr(w, "assign_order", 2) == 3
     table = {
-        "deposit": 6 * N + 8 * C + sum(4 * m ** 3 for m in meshes),
+        # CIC: both levels in one pass; TSC: one launch group per level (fill, atomic deposit)
+        "deposit": 10 * N + 4 * n ** 3 if tsc else 6 * N + 8 * C + sum(4 * m ** 3 for m in meshes),
         "fft_x_fwd": 4 * n ** 3 + 8 * half,
         "fft_y_fwd": 16 * half,
-        "fft_z_green": 20 * half,
+        "fft_z_green": 16 * half + 4 * green_len,
         "fft_y_inv": 16 * half,
         "fft_x_inv": 8 * half + 4 * n ** 3,
-        "interp": sum(4 * m ** 3 for m in meshes) + 22 * N,
+        "interp": 4 * n ** 3 + 22 * N if tsc else sum(4 * m ** 3 for m in meshes) + 22 * N,
         "pp": 58 * N + 8 * C,
         "kick": 36 * N,
         "kick_drift": 68 * N + 4 * C,
@@ -214,7 +218,7 @@ def algorithmic_bytes(w, n_part, cls, level):
         "sort": 8 * C + 8 * N,
         "gather": 48 * N,
         "cellid": 8 * C + 4 * N,
-        "green": 4 * half,
+        "green": 4 * green_len,
         "prep": 26 * N,
         "pp_order": 4 * C + 26 * N,
         "sort_big": 8 * N,
