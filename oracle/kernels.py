@@ -12,7 +12,7 @@ Everything here restates Sec. 2.1 of the paper (CUBE2, Yu et al. 2026):
 * Eq. (diff)        D(k)           4-point finite difference in k-space
 * Eq. (Gk)          G_alpha(k)     optimised Green's function, alias sum |n_d| <= 2
 
-Readings of the paper taken here (each listed in the design doc):
+Readings of the paper taken here (where it is silent or departs from the workload):
 
 * Mass assignment is CIC, W(k) = prod_d sinc^2(k_d/2) (the paper's TSC has the
   cube); ``order`` selects the power (2 = CIC, 3 = TSC).

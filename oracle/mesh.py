@@ -8,7 +8,7 @@ reading), Poisson solve phi(k) = rho(k) G(k), force field E = D * phi with the
 4-point difference of Eq. (diff) applied in real space (the paper's route,
 Sec. 2.2.2), and interpolation back with the same assignment function.
 
-Conventions (readings listed in the design doc):
+Conventions (readings of the paper where it is silent):
 
 * IOS (Sec. 2.3): particle p sits in IOS cell c (linear id, x fastest) with
   uint16 offsets; its fixed-point coordinate is X_d = c_d 2^16 + off_d, i.e.
