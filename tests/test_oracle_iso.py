@@ -12,6 +12,7 @@ of the pairwise force accuracy test of Sec. 3.1.
    images at large r, so a missing or wrong isolation factor fails.
 """
 import math
+import os
 
 import numpy as np
 import pytest
@@ -110,3 +111,22 @@ def test_periodic_table_feels_the_images(pairs):
     # percent (growing with r), the isolated table does not
     assert far[:, 3].mean() < -0.05
     assert abs(far[:, 1].mean()) < 0.02
+
+
+def _golden(name):
+    vals = {}
+    with open(os.path.join(os.path.dirname(__file__), "golden", name)) as f:
+        for line in f:
+            if line.strip() and not line.startswith("#"):
+                k, v = line.split()
+                vals[k] = float(v)
+    return vals
+
+
+def test_pairwise_accuracy_within_the_papers_reported_envelope(pairs):
+    # the paper's TSC, three-level test reports 2 % rms and 7 % max; the same
+    # test on this method's CIC two-level layout stays within 1.5x of both
+    ref = _golden("pairwise_accuracy.txt")
+    e = pairs[:, 1]
+    assert np.sqrt(np.mean(e ** 2)) <= 1.5 * ref["rms_relative_error"]
+    assert np.abs(e).max() <= 1.5 * ref["max_relative_error"]
