@@ -7,6 +7,7 @@ the pair's reference force) and, binned in separation, F.r_hat/R - 1 and the
 direction against the reference V_p R(r, b_PP)/(4 pi) of Eq. (force_decomp).
 The binned table is printed (pytest -s) for the record."""
 import math
+import os
 
 import numpy as np
 import pytest
@@ -109,3 +110,15 @@ def test_pairwise_force_accuracy(ctx):
         print(f"  [{lo:5.2f}, {hi:5.2f})   {m.sum():5d}   {e.mean():+.2e}     {e.std():.2e}     "
               f"{np.abs(e).max():.2e}     {th.max():.2e}")
         assert abs(e.mean()) < 0.02 and e.std() < 0.04 and np.abs(e).max() < 0.1 and th.max() < 0.1, (lo, hi)
+    # against the paper's reported accuracy of the same test (tests/golden): within 1.5x
+    ref = {}
+    with open(os.path.join(os.path.dirname(__file__), "golden", "pairwise_accuracy.txt")) as f:
+        for line in f:
+            if line.strip() and not line.startswith("#"):
+                k, v = line.split()
+                ref[k] = float(v)
+    e = rows[:, 1]
+    print(f"  all pairs: rms {np.sqrt(np.mean(e ** 2)):.2e}, max {np.abs(e).max():.2e} "
+          f"(paper: rms {ref['rms_relative_error']}, max {ref['max_relative_error']})")
+    assert np.sqrt(np.mean(e ** 2)) <= 1.5 * ref["rms_relative_error"]
+    assert np.abs(e).max() <= 1.5 * ref["max_relative_error"]
