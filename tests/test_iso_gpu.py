@@ -112,8 +112,8 @@ def test_pairwise_force_accuracy(ctx):
         assert abs(e.mean()) < 0.02 and e.std() < 0.04 and np.abs(e).max() < 0.1 and th.max() < 0.1, (lo, hi)
     # against the paper's reported accuracy of the same test (tests/golden): within 1.5x
     ref = {}
-    with open(os.path.join(os.path.dirname(__file__), "golden", "pairwise_accuracy.txt")) as f:
-        for line in f:
+    with open(os.path.join(os.path.dirname(__file__), "golden", "pairwise_accuracy.txt")) as fh:
+        for line in fh:
             if line.strip() and not line.startswith("#"):
                 k, v = line.split()
                 ref[k] = float(v)
