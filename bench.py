@@ -5,18 +5,25 @@ Workload (default): 256^3 particles in a 256 Mpc/h box, two PM levels (coarse
 128^3 + fine 512^3), FP32 velocities, seeded Zel'dovich ICs at z = 49
 (BBKS spectrum), the 50-step constant-Delta-a KDK schedule to z = 0.  A step is
 one kdk_step of that schedule over the whole box (drift + re-bin, deposit on
-both meshes, both Poisson solves, interpolation, PP, both kicks).  W warm-up
-steps run first from the ICs; the state is then reset to the ICs and K steps
-are timed with CUDA events on the library's stream (K > 50 restarts the
-schedule from the ICs inside the timed region).
+both meshes, both Poisson solves, interpolation, PP, both kicks).
+
+Timing: W warm-up steps from the ICs; then the whole schedule runs once from
+the ICs (untimed for the headline, reported as ``full_schedule``), keeping
+the states at K step indices spread evenly over it; the timed region runs
+those K steps, each from its kept state (restored outside its CUDA-event
+pair), so the headline covers the early (PM-bound) and late (PP-bound)
+parts of the schedule in proportion.  value = K N / summed step durations.
 
 Also reported on the same JSON line:
-  roofline      dominant kernel class: algorithmic bytes per launch / its mean
+  roofline      dominant kernel class: algorithmic work per launch / its mean
                 CUDA-event duration inside the timed region, against the
-                measured HBM copy bandwidth
-  e2e           the same metric through cube2_kdk_step_host with the particle
+                measured HBM copy bandwidth, or for PP the FP32 FMA rate the
+                library's probe kernel measures on this device
+  e2e           the same steps through cube2_kdk_step_host with the particle
                 state in pinned host memory (H2D + step + D2H every step)
-  cpu_baseline  the FP64 oracle on a bounded sample of the same recipe
+  adjoint       adjoint/forward time ratio of the differentiation workload
+  cpu_baseline  the FP64 oracle on all host cores, on a bounded sample of the
+                same recipe
   clocks        nvidia-smi samples taken during the timed region
 
 --impl reference times the FP64 oracle alone (this project's reference arm).
@@ -56,7 +63,7 @@ def parse_args():
     ap.add_argument("--workload", default="pm2-256c-128x512mesh")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-seconds", type=float, default=12.0, help="budget of the oracle sample")
+    ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint/forward sub-record")
     ap.add_argument("--streams", type=int, default=16, help="graph branches of the ensemble workload")
     return ap.parse_args()
 
@@ -226,17 +233,63 @@ def algorithmic_bytes(w, n_part, cls, level):
     return table[cls]
 
 
-# FP32 operations (an FMA counts 2) of one in-range PP pair: separation 3,
-# r^2 5, rsqrt and u = r/b, v = 1 - u 4, the two shell polynomials of R_PP with
-# their powers 24, the 1/r^3 scaling 3, accumulation of the three components 6;
-# and of one candidate test: separation 3 and r^2 - b^2 6
-PP_FLOPS_PAIR = 45
+# FP32 operations (an FMA counts 2) of one in-range PP pair, as the roofline
+# counts them: the separation 3, r^2 5, the reciprocal square root and the
+# scaled distance u = r / b 3, one shell polynomial of R_PP in Horner form 14,
+# the 1/r^3 scaling and the product with the force factor 2, accumulation of
+# the three components 3: 30.  The kernel as written also evaluates the second
+# shell polynomial and forms the powers of v = 1 - u (45 in all), and tests
+# every candidate (separation 3 and r^2 - b^2 6); both are reported beside it.
+PP_FLOPS_PAIR = 30
+PP_FLOPS_PAIR_AS_WRITTEN = 45
 PP_FLOPS_CANDIDATE = 9
 
 
-def fp32_peak_tflops(sm_mhz):
-    """152 SMs x 128 FP32 lanes x 2 (FMA) x clock."""
-    return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+def fp32_peak_derived(sms, sm_mhz):
+    """SMs x 128 FP32 lanes x 2 (FMA) x clock, TFLOP/s."""
+    return sms * 128 * 2 * sm_mhz * 1e6 / 1e12
+
+
+def measure_fp32_peak(cube2, torch, reps=3):
+    """FP32 FMA rate of this device from the library's probe kernel (8 blocks
+    of 256 threads per SM, 8 independent FMA chains per thread), timed with
+    CUDA events; the best of ``reps`` launches of ~20 ms, TFLOP/s."""
+    props = torch.cuda.get_device_properties(torch.cuda.current_device())
+    sms = props.multi_processor_count
+    out = torch.zeros(1, device="cuda")
+    stream = torch.cuda.current_stream()
+    blocks, threads = sms * 8, 256
+    cube2.fma_probe(out, blocks, threads, 64, stream)
+    iters = 2000
+    best = 0.0
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        flops = cube2.fma_probe(out, blocks, threads, iters, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        best = max(best, flops / (e0.elapsed_time(e1) / 1e3) / 1e12)
+    return best, sms
+
+
+def pp_roofline(pairs, cands, launches, per_launch_ms, peak_tflops, sms, sm_mhz, traffic=None):
+    """Roofline record of the PP kernel class: in-range pair work (PP_FLOPS_PAIR
+    per ordered pair) per launch over the mean launch time, against the FP32
+    FMA rate measured by the probe kernel."""
+    flops = pairs * PP_FLOPS_PAIR / launches
+    sec = per_launch_ms / 1e3
+    achieved = flops / sec / 1e12
+    return {"bound": "alu", "kernel": "pp_kernel (shared-stream and per-lane paths)", "achieved": achieved,
+            "peak": peak_tflops, "unit": "TFLOP/s", "frac": achieved / peak_tflops,
+            "peak_source": f"measured: FP32 FMA probe kernel (cube2_fma_probe), CUDA events, {sms} SMs",
+            "peak_derived": fp32_peak_derived(sms, sm_mhz), "peak_derived_note":
+            f"{sms} SMs x 128 lanes x 2 x {sm_mhz:.0f} MHz (median SM clock in the timed region)",
+            "flops_per_pair": PP_FLOPS_PAIR, "algorithmic_flops_per_launch": flops,
+            "achieved_as_written": pairs * PP_FLOPS_PAIR_AS_WRITTEN / launches / sec / 1e12,
+            "achieved_with_candidate_tests": (pairs * PP_FLOPS_PAIR_AS_WRITTEN + cands * PP_FLOPS_CANDIDATE)
+            / launches / sec / 1e12,
+            "pairs_per_launch": pairs / launches, "candidates_per_launch": cands / launches,
+            "mean_launch_ms": per_launch_ms, "traffic": traffic}
 
 
 def traffic_record(kernel):
@@ -256,85 +309,127 @@ def traffic_record(kernel):
 
 
 # ------------------------------------------------------------- CPU oracle
-def oracle_sample(w, steps_budget_s, min_steps=1, max_steps=None):
-    """Time the FP64 oracle on the workload's recipe at SAMPLE_NP^3 particles.
+def sampled_steps(n_steps, k):
+    """Indices of the k timed steps, spread evenly over the n_steps-step
+    schedule (the middle of k equal stretches); the whole schedule, repeated,
+    when k >= n_steps."""
+    reps, rest = divmod(k, n_steps)
+    idx = list(range(n_steps)) * reps
+    idx += [int((j + 0.5) * n_steps / rest) for j in range(rest)]
+    return sorted(idx)
 
-    Returns (particle-steps/s, steps, seconds, description)."""
+
+def oracle_sample_workload(w):
+    """The workload's recipe scaled to SAMPLE_NP^3 particles (same resolution)."""
     from inputs.workloads import Level
+    scale = SAMPLE_NP / w.n_p
+    return w.with_(name=w.name + "-sample", n_p=SAMPLE_NP, box=w.box * scale, n_ios=int(w.n_ios * scale),
+                   levels=tuple(Level(int(lv.n_mesh * scale), lv.beta) for lv in w.levels))
+
+
+def _oracle_worker(job):
+    """One host core: run the FP64 oracle through the schedule of the sample
+    workload ``sw`` (untimed), keep the states at the steps in ``idx``, then
+    time one oracle KDK step from each kept state.  Returns (seconds, steps,
+    particles per step)."""
+    sw, idx = job
     from inputs.zeldovich import zeldovich_ios
     from oracle import kdk as okdk
     from oracle import mesh as omesh
-    scale = SAMPLE_NP / w.n_p
-    sw = w.with_(name=w.name + "-sample", n_p=SAMPLE_NP, box=w.box * scale, n_ios=int(w.n_ios * scale),
-                 levels=tuple(Level(int(lv.n_mesh * scale), lv.beta) for lv in w.levels))
     st = zeldovich_ios(sw)
     greens = omesh.green_tables(sw)
     state = dict(off=st["off"], count=st["count"], start=st["start"], vel=st["vel"].astype("float64"))
     state["acc"] = okdk.total_force(st["off"], st["count"], st["start"], sw, greens)
     a = sw.scale_factors()
-    t0 = time.perf_counter()
-    k = 0
-    while True:
-        i = k % sw.n_steps
-        state = okdk.kdk_step(state, sw, a[i], a[i + 1], greens)
-        k += 1
-        el = time.perf_counter() - t0
-        if (k >= min_steps and el >= steps_budget_s) or (max_steps and k >= max_steps):
-            break
-    el = time.perf_counter() - t0
-    desc = (f"FP64 numpy oracle, {k} KDK steps of the same recipe scaled to {SAMPLE_NP}^3 particles "
-            f"(box {sw.box:g} Mpc/h, meshes {[lv.n_mesh for lv in sw.levels]}, IOS {sw.n_ios}^3), "
-            f"Green's tables built outside the timing")
-    return sw.n_particles * k / el, k, el, desc
+    keep = {}
+    last = max(idx)
+    for i in range(last + 1):
+        if i in idx:
+            keep[i] = dict(state)
+        if i < last:
+            state = okdk.kdk_step(state, sw, a[i], a[i + 1], greens)
+    el = 0.0
+    for i in idx:
+        t0 = time.perf_counter()
+        okdk.kdk_step(keep[i], sw, a[i], a[i + 1], greens)
+        el += time.perf_counter() - t0
+    return el, len(idx), sw.n_particles
+
+
+def host_cpu():
+    """(model name, logical cores) of this host, from lscpu."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    return model, os.cpu_count() or 1
+
+
+def oracle_timing(w, idx, procs=None):
+    """The FP64 oracle as it stands, timed on the host cores: ``procs``
+    independent processes (default: one per core), each an independent
+    realisation of the workload's recipe at SAMPLE_NP^3 particles timed on the
+    steps ``idx`` of its schedule (_oracle_worker).  Returns a dict with the
+    aggregate particle-steps/s (all particle-steps over the slowest process's
+    timed seconds), the single-core rate (median over processes), the core
+    count and CPU model, and the sample's description."""
+    import multiprocessing as mp
+    model, ncpu = host_cpu()
+    procs = procs or ncpu
+    sw = oracle_sample_workload(w)
+    jobs = [(sw.with_(seed=sw.seed + 7919 * j), list(idx)) for j in range(procs)]
+    for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[var] = "1"
+    with mp.get_context("spawn").Pool(procs) as pool:
+        res = pool.map(_oracle_worker, jobs)
+    slowest = max(r[0] for r in res)
+    units = sum(r[1] * r[2] for r in res)
+    single = statistics.median(r[1] * r[2] / r[0] for r in res)
+    desc = (f"FP64 numpy oracle as it stands: {procs} processes on {procs} host cores, each an independent "
+            f"realisation of the workload recipe scaled to {SAMPLE_NP}^3 particles (box {sw.box:g} Mpc/h, meshes "
+            f"{[lv.n_mesh for lv in sw.levels]}, IOS {sw.n_ios}^3), one KDK step timed from each of the schedule "
+            f"states {sorted(set(idx))} (reached untimed); Green's tables built outside the timing")
+    return {"value": units / slowest, "single_core_value": single, "cores": procs, "cpu_model": model,
+            "seconds": slowest, "steps_per_process": len(idx), "sample": desc}
 
 
 def run_reference(args, w):
     world, rank, _ = dist_env()
     if rank != 0:
         return
-    from inputs.workloads import Level
-    from inputs.zeldovich import zeldovich_ios
-    from oracle import kdk as okdk
-    from oracle import mesh as omesh
-    scale = SAMPLE_NP / w.n_p
-    sw = w.with_(name=w.name + "-sample", n_p=SAMPLE_NP, box=w.box * scale, n_ios=int(w.n_ios * scale),
-                 levels=tuple(Level(int(lv.n_mesh * scale), lv.beta) for lv in w.levels))
-    st = zeldovich_ios(sw)
-    greens = omesh.green_tables(sw)
-    base = dict(off=st["off"], count=st["count"], start=st["start"], vel=st["vel"].astype("float64"))
-    base["acc"] = okdk.total_force(st["off"], st["count"], st["start"], sw, greens)
-    a = sw.scale_factors()
-    state = dict(base)
-    for k in range(args.warmup):
-        i = k % sw.n_steps
-        state = okdk.kdk_step(state, sw, a[i], a[i + 1], greens)
-    state = dict(base)
-    t0 = time.perf_counter()
-    for k in range(args.steps):
-        i = k % sw.n_steps
-        if i == 0 and k > 0:
-            state = dict(base)
-        state = okdk.kdk_step(state, sw, a[i], a[i + 1], greens)
-    el = time.perf_counter() - t0
-    value = sw.n_particles * args.steps / el
-    sample = (f"each step: one FP64 oracle KDK step of the workload recipe at {SAMPLE_NP}^3 particles "
-              f"(box {sw.box:g}, meshes {[lv.n_mesh for lv in sw.levels]})")
+    idx = sampled_steps(w.n_steps, args.steps)
+    t = oracle_timing(w, idx)
+    value = t["value"]
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t["seconds"] / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic (seeded Zel'dovich ICs, BBKS spectrum)", "config": workload_config(w),
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "data": "synthetic (seeded Zel'dovich ICs, BBKS spectrum)", "config": workload_config(w, idx),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": t["cores"], "kind": "oracle", "sample": t["sample"],
+                         "cpu_model": t["cpu_model"], "single_core_value": t["single_core_value"]},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
 
 
-def workload_config(w):
-    return {"workload": w.name, "particles": w.n_particles, "box_mpc_h": w.box,
-            "meshes": [lv.n_mesh for lv in w.levels], "ios_cells": w.n_ios,
-            "schedule": f"{w.n_steps} KDK steps z={w.z_init:g}->{w.z_final:g}, constant Delta a",
-            "l2": "inputs larger than L2 (>= 2 GB resident working set)", "parallelism": "replicas"}
+def workload_config(w, idx=None):
+    cfg = {"workload": w.name, "particles": w.n_particles, "box_mpc_h": w.box,
+           "meshes": [lv.n_mesh for lv in w.levels], "ios_cells": w.n_ios,
+           "schedule": f"{w.n_steps} KDK steps z={w.z_init:g}->{w.z_final:g}, constant Delta a",
+           "l2": "inputs larger than L2 (>= 2 GB resident working set); each timed step starts after a "
+                 "checkpoint restore larger than L2", "parallelism": "replicas"}
+    if idx is not None:
+        a = w.scale_factors()
+        cfg["timed_steps"] = sorted(set(idx))
+        cfg["timed_a_range"] = [a[min(idx)], a[max(idx) + 1]]
+        cfg["timing"] = ("each timed step is one kdk_step of the schedule from the state the untimed run "
+                         "reached there; value = steps x particles / summed CUDA-event step durations")
+    return cfg
 
 
 # ------------------------------------------------------------------ main
@@ -450,24 +545,18 @@ def run_ensemble(args):
 ADJOINT = "c3-adjoint-128c-256mesh"
 
 
-def run_adjoint(args):
+def adjoint_measure(reps, warmup, breakdown=True):
     """Adjoint/forward time ratio on the differentiation workload (128^3
     particles, one 256^3 level, 10 KDK steps z = 9 -> 0): forward = the 10
     steps plus the final density loss; adjoint = the same steps with a
-    checkpoint and re-bin map per step, the loss gradient, and 10 reverse
-    steps (two force products each), giving dL/dx0 and dL/dv0.  The target is
-    the final overdensity of an independent realisation (seed 4).  Wall clock
-    with a device synchronisation on both sides, per repetition."""
-    import numpy as np
+    checkpoint and re-bin map per step, the loss gradient, and the reverse
+    sweep (one force product per step), giving dL/dx0 and dL/dv0.  The target
+    is the final overdensity of an independent realisation (seed 4).  Wall
+    clock with a device synchronisation on both sides, median per repetition.
+    Runs on the current device; returns a dict."""
     import torch
     from inputs.workloads import WORKLOADS
     from inputs.zeldovich import zeldovich_ios
-    world, rank, _ = dist_env()
-    if rank != 0:
-        return
-    torch.cuda.set_device(0)
-    from paper_2512_12629_gb300 import build as pkg_build
-    pkg_build.build()
     from paper_2512_12629_gb300 import cube2
     w = WORKLOADS["pm1-128c-256mesh"]
     a = w.scale_factors()
@@ -495,11 +584,11 @@ def run_adjoint(args):
     def adjoint():
         return cube2.loss_gradient(ctx, p0, target, a)
 
-    for _ in range(max(1, args.warmup)):
+    for _ in range(max(1, warmup)):
         forward()
         adjoint()
     tf, ta = [], []
-    for _ in range(max(1, args.steps)):
+    for _ in range(max(1, reps)):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         loss = forward()
@@ -511,25 +600,44 @@ def run_adjoint(args):
         ta.append(time.perf_counter() - t0)
     ctx.check()
     fwd, adj = statistics.median(tf), statistics.median(ta)
-    # per-class kernel time of one more repetition of each, CUDA events, outside the timing
-    breakdown = {}
-    for name, fn in (("forward", forward), ("adjoint", adjoint)):
-        ctx.profile(capacity=5000)
-        fn()
-        prof = ctx.profile_read()
-        ctx.profile(0)
-        breakdown[name] = {f"{c}/{l}": round(ms, 3) for (c, l), (ms, _n) in
-                           sorted(prof.items(), key=lambda kv: -kv[1][0])}
+    out = {"ratio": adj / fwd, "forward_ms": 1e3 * fwd, "adjoint_ms": 1e3 * adj, "loss": loss,
+           "loss_in_adjoint_run": loss_a, "grad_x_rms": float(gx.pow(2).mean().sqrt()),
+           "grad_v_rms": float(gv.pow(2).mean().sqrt()), "particles": n_part, "mesh": 256, "kdk_steps": len(a) - 1,
+           "z": f"{w.z_init:g} -> {w.z_final:g}", "repetitions": len(tf),
+           "timing": "median wall clock per repetition, synchronised"}
+    if breakdown:
+        # per-class kernel time of one more repetition of each, CUDA events, outside the timing
+        bd = {}
+        for name, fn in (("forward", forward), ("adjoint", adjoint)):
+            ctx.profile(capacity=5000)
+            fn()
+            prof = ctx.profile_read()
+            ctx.profile(0)
+            bd[name] = {f"{c}/{l}": round(ms, 3) for (c, l), (ms, _n) in sorted(prof.items(), key=lambda kv: -kv[1][0])}
+        out["kernels_ms_per_repetition"] = bd
+    ctx.close()
+    return out
+
+
+def run_adjoint(args):
+    """The differentiation workload alone (see adjoint_measure)."""
+    import torch
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return
+    torch.cuda.set_device(0)
+    from paper_2512_12629_gb300 import build as pkg_build
+    pkg_build.build()
+    r = adjoint_measure(args.steps, args.warmup)
     line = {
         "metric": "adjoint/forward time ratio (128^3 particles, 256^3 mesh, 10 KDK steps, density MSE loss)",
-        "value": adj / fwd, "unit": "ratio", "higher_is_better": False, "n_gpus": 1, "steps": args.steps,
-        "warmup": args.warmup, "forward_ms": 1e3 * fwd, "adjoint_ms": 1e3 * adj, "loss": loss,
-        "loss_in_adjoint_run": loss_a, "grad_x_rms": float(gx.pow(2).mean().sqrt()),
-        "grad_v_rms": float(gv.pow(2).mean().sqrt()), "kernels_ms_per_repetition": breakdown, "dtype": "f32",
+        "value": r["ratio"], "unit": "ratio", "higher_is_better": False, "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "forward_ms": r["forward_ms"], "adjoint_ms": r["adjoint_ms"], "loss": r["loss"],
+        "loss_in_adjoint_run": r["loss_in_adjoint_run"], "grad_x_rms": r["grad_x_rms"], "grad_v_rms": r["grad_v_rms"],
+        "kernels_ms_per_repetition": r.get("kernels_ms_per_repetition"), "dtype": "f32",
         "data": "synthetic (seeded Zel'dovich ICs, BBKS spectrum; target = seed 4 final overdensity)",
-        "config": {"workload": ADJOINT, "particles": n_part, "mesh": 256, "kdk_steps": len(a) - 1,
-                   "z": f"{w.z_init:g} -> {w.z_final:g}", "gradient": "dL/dx0 and dL/dv0",
-                   "timing": "median wall clock per repetition, synchronised"},
+        "config": {"workload": ADJOINT, "particles": r["particles"], "mesh": 256, "kdk_steps": r["kdk_steps"],
+                   "z": r["z"], "gradient": "dL/dx0 and dL/dv0", "timing": r["timing"]},
     }
     print(json.dumps(line), flush=True)
 
@@ -595,11 +703,8 @@ def run_large(args):
     per_launch_ms = dms / dcount
     if cls == "pp":
         mhz = (clk or {}).get("sm_mhz") or 2070.0
-        fpk = fp32_peak_tflops(mhz)
-        achieved = pairs * PP_FLOPS_PAIR / dcount / (per_launch_ms / 1e3) / 1e12
-        roofline = {"bound": "alu", "kernel": "pp_kernel", "achieved": achieved, "peak": fpk, "unit": "TFLOP/s",
-                    "frac": achieved / fpk, "pairs_per_launch": pairs / dcount, "mean_launch_ms": per_launch_ms,
-                    "traffic": None}
+        fpk, sms = measure_fp32_peak(cube2, torch)
+        roofline = pp_roofline(pairs, cands, dcount, per_launch_ms, fpk, sms, mhz)
     else:
         peak, kind = peaks()
         alg = algorithmic_bytes(w, n_part, cls, lvl)
@@ -646,7 +751,6 @@ def main():
     if args.impl == "reference":
         run_reference(args, w)
         return
-    import numpy as np
     import torch
     world, rank, local = dist_env()
     if world > 1:
@@ -676,41 +780,58 @@ def main():
     p = p0.clone()
     a = w.scale_factors()
     S = w.n_steps
+    idx = sampled_steps(S, args.steps)
+    stream = ctx.stream
 
-    def reset(dst):
+    def load(dst, src):
         for x, y in zip((dst.off, dst.count, dst.start, dst.vel, dst.acc),
-                        (p0.off, p0.count, p0.start, p0.vel, p0.acc)):
+                        (src.off, src.count, src.start, src.vel, src.acc)):
             x.copy_(y)
 
+    # warm-up: W steps from the initial conditions
     for k in range(args.warmup):
         i = k % S
         ctx.kdk_step(p, a[i], a[i + 1])
-    reset(p)
+    ctx.check()
+    # the whole schedule from the initial conditions (untimed for the headline):
+    # per-step CUDA events and PP pair counts, and the states the timed steps start from
+    load(p, p0)
+    ckpt = {}
+    sched_ms, sched_pairs = [], []
+    ctx.pp_stats()
+    for i in range(S):
+        if i in idx:
+            ckpt[i] = p.clone()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ctx.kdk_step(p, a[i], a[i + 1])
+        e1.record(stream)
+        e1.synchronize()
+        sched_ms.append(e0.elapsed_time(e1))
+        sched_pairs.append(ctx.pp_stats()[0])
     ctx.check()
     torch.cuda.synchronize()
 
-    stream = ctx.stream
-    ev0 = torch.cuda.Event(enable_timing=True)
-    ev1 = torch.cuda.Event(enable_timing=True)
+    # timed region: K steps, each from its checkpoint (the restore is outside the event pair)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in idx]
     ctx.profile(capacity=64 * (args.steps + 2))
     ctx.pp_stats()
-    launches0 = ctx.launch_count()
+    launches = 0
     clocks = ClockSampler(bus_id_of(torch.cuda.current_device()))
     clocks.start()
     ranks.barrier()
     torch.cuda.synchronize()
-    ev0.record(stream)
-    for k in range(args.steps):
-        i = k % S
-        if i == 0 and k > 0:
-            reset(p)
+    for (e0, e1), i in zip(evs, idx):
+        load(p, ckpt[i])
+        l0 = ctx.launch_count()
+        e0.record(stream)
         ctx.kdk_step(p, a[i], a[i + 1])
-    ev1.record(stream)
+        e1.record(stream)
+        launches += ctx.launch_count() - l0
     torch.cuda.synchronize()
     ranks.barrier()
     clk = clocks.stop()
-    launches = ctx.launch_count() - launches0
-    ms = ev0.elapsed_time(ev1)
+    ms = sum(e0.elapsed_time(e1) for e0, e1 in evs)
     prof = ctx.profile_read()
     ctx.profile(0)
     ctx.check()
@@ -722,23 +843,13 @@ def main():
     # dominant kernel class -> roofline (PP counts both of its kernels)
     peak, peak_kind = peaks()
     total_prof = sum(v[0] for v in prof.values())
-    dom = max(prof.items(), key=lambda kv: kv[1][0])
-    (cls, lvl), (dms, dcount) = dom
+    (cls, lvl), (dms, dcount) = max(prof.items(), key=lambda kv: kv[1][0])
     per_launch_ms = dms / dcount
     kname = f"{cls}[level {lvl}]" if cls.startswith("fft") else cls
+    mhz = (clk or {}).get("sm_mhz") or 2070.0
+    fpk, sms = measure_fp32_peak(cube2, torch)
     if cls == "pp":
-        mhz = (clk or {}).get("sm_mhz") or 2070.0
-        fpk = fp32_peak_tflops(mhz)
-        flops = pp_pairs * PP_FLOPS_PAIR / dcount
-        achieved = flops / (per_launch_ms / 1e3) / 1e12
-        roofline = {"bound": "alu", "kernel": "pp_kernel (shared-stream and per-lane paths)", "achieved": achieved, "peak": fpk,
-                    "unit": "TFLOP/s", "frac": achieved / fpk,
-                    "peak_source": f"derived: 152 SMs x 128 FP32 lanes x 2 x {mhz:.0f} MHz",
-                    "algorithmic_flops_per_launch": flops,
-                    "pairs_per_launch": pp_pairs / dcount, "candidates_per_launch": pp_cands / dcount,
-                    "with_candidate_tests_TFLOPs": (pp_pairs * PP_FLOPS_PAIR + pp_cands * PP_FLOPS_CANDIDATE)
-                    / dcount / (per_launch_ms / 1e3) / 1e12,
-                    "mean_launch_ms": per_launch_ms, "traffic": traffic_record("pp")}
+        roofline = pp_roofline(pp_pairs, pp_cands, dcount, per_launch_ms, fpk, sms, mhz, traffic_record("pp"))
     else:
         alg = algorithmic_bytes(w, n_part, cls, lvl)
         achieved = alg / (per_launch_ms / 1e3) / 1e9
@@ -750,35 +861,38 @@ def main():
     for (c, l), (kms, kc) in sorted(prof.items(), key=lambda kv: -kv[1][0]):
         b = algorithmic_bytes(w, n_part, c, l)
         kernels[f"{c}/{l}"] = {"share": kms / total_prof, "ms_per_launch": kms / kc, "launches": kc,
-                               "GBps_alg": b / (kms / kc / 1e3) / 1e9}
+                               "GBps_alg": b / (kms / kc / 1e3) / 1e9, "frac_hbm": b / (kms / kc / 1e3) / 1e9 / peak}
     kernels["pp_work"] = {"pairs_per_step": pp_pairs / args.steps, "candidates_per_step": pp_cands / args.steps}
+    full = {"steps": S, "ms_per_step": sum(sched_ms) / S, "value": n_part * S / (sum(sched_ms) / 1e3),
+            "ms_first_last_10": [sum(sched_ms[:10]) / 10, sum(sched_ms[-10:]) / 10],
+            "pp_pairs_first_last_step": [sched_pairs[0], sched_pairs[-1]],
+            "what": "the whole schedule from the initial conditions, per-step CUDA events (untimed run)"}
 
-    # end to end through the host-buffer entry point
+    # end to end through the host-buffer entry point, on the same steps
     e2e = None
     if not args.no_e2e:
         host = cube2.IOSState(*(x.cpu().pin_memory() for x in (p0.off, p0.count, p0.start, p0.vel, p0.acc)))
         pe = p0.clone()
         bytes_step = sum(x.numel() * x.element_size() for x in (host.off, host.count, host.start, host.vel, host.acc))
         ctx.kdk_step_host(pe, host, a[0], a[1])                # warm
-        host = cube2.IOSState(*(x.cpu().pin_memory() for x in (p0.off, p0.count, p0.start, p0.vel, p0.acc)))
-        torch.cuda.synchronize()
+        el = 0.0
         ranks.barrier()
-        t0 = time.perf_counter()
-        for k in range(args.steps):
-            i = k % S
-            if i == 0 and k > 0:
-                for x, y in zip((host.off, host.count, host.start, host.vel, host.acc),
-                                (p0.off, p0.count, p0.start, p0.vel, p0.acc)):
-                    x.copy_(y)
+        for i in idx:
+            load(host, ckpt[i])
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
             ctx.kdk_step_host(pe, host, a[i], a[i + 1])
-        el = ranks.max(time.perf_counter() - t0)
+            el += time.perf_counter() - t0
+        el = ranks.max(el)
         e2e = {"value": job_throughput(units, el), "unit": UNIT,
                "h2d_bytes_per_step": bytes_step, "d2h_bytes_per_step": bytes_step,
-               "api": "cube2_kdk_step_host (pinned host state, H2D + step + D2H each step)"}
+               "api": "cube2_kdk_step_host (pinned host state, H2D + step + D2H each step), the same steps"}
+    del ckpt
 
     # cuFFT (through torch.fft), timed only as a comparison with the library's own
     # FFT passes of the finest level: r2c + c2r of the same n^3 FP32 grid
     cufft = None
+    adjoint = None
     if rank == 0:
         nf = w.levels[-1].n_mesh
         own = sum(kms / kc for (c, l), (kms, kc) in prof.items() if c.startswith("fft_") and l == len(w.levels) - 1)
@@ -795,21 +909,25 @@ def main():
         cufft = {"n": nf, "torch_cufft_r2c_c2r_ms": e0.elapsed_time(e1) / reps, "own_fft_passes_ms": own,
                  "note": "own passes include the Green's multiply (fused into the z pass); cuFFT is not on the path"}
         del grid
+        if not args.no_adjoint:
+            adjoint = adjoint_measure(5, 3, breakdown=False)
+            adjoint["workload"] = ADJOINT
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        v, k, el, desc = oracle_sample(w, args.cpu_seconds)
-        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc,
-               "seconds": el}
+        t = oracle_timing(w, sampled_steps(w.n_steps, min(args.steps, 6)))
+        cpu = {"value": t["value"], "unit": UNIT, "cores": t["cores"], "kind": "oracle", "sample": t["sample"],
+               "cpu_model": t["cpu_model"], "single_core_value": t["single_core_value"], "seconds": t["seconds"]}
 
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-            "data": "synthetic (seeded Zel'dovich ICs, BBKS spectrum)", "config": workload_config(w),
+            "data": "synthetic (seeded Zel'dovich ICs, BBKS spectrum)", "config": workload_config(w, idx),
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-            "clocks": clk, "kernels": kernels, "cufft_comparison": cufft,
+            "clocks": clk, "full_schedule": full, "adjoint": adjoint, "kernels": kernels,
+            "cufft_comparison": cufft,
         }
         print(json.dumps(line), flush=True)
     if dist:

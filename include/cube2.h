@@ -214,16 +214,31 @@ int cube2_debug_forward_fft(cube2_ctx *ctx, int level, float *out);
  * application, or code that must not let cudaMalloc/cudaFree synchronise the
  * device).  rho: device FP32 [n][n][n] overdensity (as cube2_get_density
  * gives); green: device FP32 [n][n][n/2+1] table with 1/n^3 folded in (as
- * cube2_get_green gives); phi: device FP32 [n][n][n] output.  Same kernels
- * and result as cube2_solve_pm.  Working memory is one file-scope device array
- * of 15.7 MB that every GPU loading the library holds until exit; n must be a
- * supported size no larger than 128 (else CUBE2_ERR_UNSUPPORTED_SIZE, message
- * in cube2_last_error(NULL)).  The first call on a device looks up that
- * array's address (cudaGetSymbolAddress) with the device current; make that
- * first call before any stream capture.  All calls share the array and keep
- * the last call's contents, so calls that overlap on the GPU (different
- * streams or threads without ordering) race.  No allocation takes place. */
+ * cube2_get_green gives); phi: device FP32 [n][n][n] output, all on the
+ * current device.  The same FFT passes as cube2_solve_pm, with the Green's
+ * table read from the caller's full half-spectrum layout instead of the
+ * context's symmetry-reduced one: the same result up to FP32 rounding.
+ * Working memory is one file-scope device array of 15.7 MB that every GPU
+ * loading the library holds until exit; n must be a supported size no larger
+ * than 128 (else CUBE2_ERR_UNSUPPORTED_SIZE, message in
+ * cube2_last_error(NULL)).  The first call on a device looks up that array's
+ * address (cudaGetSymbolAddress) with the device current and keeps it for the
+ * life of the process; make that first call before any stream capture, and
+ * do not call this entry point on a device after cudaDeviceReset.  All calls
+ * share the array and keep the last call's contents, so calls that overlap
+ * on the GPU (different streams or threads without ordering) race.  No
+ * allocation takes place. */
 int cube2_solve_pm_noalloc(const float *rho, const float *green, float *phi, int32_t n, void *stream);
+
+/* FP32 pipe probe (the ceiling of the PP force, Sec. 2.2.3 / Eq. PP, which is
+ * plain FP32 arithmetic): launches blocks x threads threads (threads a
+ * multiple of 32, at most 1024), each running 8 independent chains of 16 * iters
+ * dependent FMAs, on `stream` (a cudaStream_t).  The work is
+ * 2 * 8 * 16 * iters * blocks * threads FP32 operations; the caller times the
+ * launch (CUDA events) to obtain the device's FMA rate.  out: one device
+ * float, never written in practice (it keeps the chains from being removed).
+ * Returns CUBE2_ERR_BAD_ARG for bad sizes, CUBE2_ERR_CUDA if the launch fails. */
+int cube2_fma_probe(float *out, int blocks, int threads, int iters, void *stream);
 
 /* Host helper: out = {K(a0,ah), Dr(a0,a1), K(ah,a1)} for cfg's cosmology. */
 int cube2_kdk_factors(const cube2_config *cfg, double a0, double a1, double out[3]);

@@ -233,3 +233,47 @@ def green_at(n, modes, b_soft, b_trunc=None, alias=2, order=2, iso=None):
     ok = d2 > 0
     out[ok] = num[ok] / (d2[ok] * den[ok] ** 2)
     return out
+
+
+def sorted_mode_triples(n):
+    """Every triple 0 <= a <= b <= c <= n/2 of absolute mode numbers, (K, 3)
+    int64, in the order c-major, then b, then a."""
+    m = n // 2
+    c, b, a = [], [], []
+    for cc in range(m + 1):
+        bb, aa = np.tril_indices(cc + 1)
+        c.append(np.full(bb.size, cc))
+        b.append(bb)
+        a.append(aa)
+    return np.stack([np.concatenate(a), np.concatenate(b), np.concatenate(c)], axis=1).astype(np.int64)
+
+
+def green_by_symmetry(n, b_soft, b_trunc=None, alias=2, order=2, iso=None, chunk=65536, mapper=map):
+    """Eq. (Gk) on the whole rfftn half spectrum [kz][ky][kx] of an n^3 mesh,
+    evaluated once per sorted triple of |m_x|, |m_y|, |m_z| with ``green_at``
+    and copied to every mode of that class.
+
+    G is even in each k_d and symmetric under permutations of the axes (the
+    alias sum runs over a set of images closed under both, and W, |D|^2 and
+    D.k_n are symmetric functions of the components), which tests pin on the
+    full table; this is the way to the table at meshes where ``green`` itself
+    is too slow.  ``mapper`` maps a function over the chunks of triples (for
+    instance the map of a process pool); chunks are evaluated independently."""
+    tri = sorted_mode_triples(n)
+    parts = [tri[i:i + chunk] for i in range(0, len(tri), chunk)]
+    args = [(n, p, b_soft, b_trunc, alias, order, iso) for p in parts]
+    vals = np.concatenate(list(mapper(_green_chunk, args)))
+    # class index of every half-spectrum mode, by sorting its absolute mode numbers
+    mx, my, mz = half_spectrum_modes(n)
+    ax = np.broadcast_to(np.abs(mx), (n, n, n // 2 + 1))
+    ay = np.broadcast_to(np.abs(my), (n, n, n // 2 + 1))
+    az = np.broadcast_to(np.abs(mz), (n, n, n // 2 + 1))
+    s = np.sort(np.stack([ax, ay, az]), axis=0)
+    a, b, c = s[0], s[1], s[2]
+    cls = c * (c + 1) * (c + 2) // 6 + b * (b + 1) // 2 + a
+    return vals[cls]
+
+
+def _green_chunk(args):
+    n, modes, b_soft, b_trunc, alias, order, iso = args
+    return green_at(n, modes, b_soft, b_trunc, alias=alias, order=order, iso=iso)

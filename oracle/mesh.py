@@ -313,3 +313,41 @@ def pm_force_level_tsc(off, count, n_ios, n_mesh, h, g):
     phi = solve_potential(rho, g)
     e = fd_gradient(phi)
     return -h * interpolate_tsc(e, off, count, n_ios), dict(rho=rho, phi=phi)
+
+
+# ------------------------------------------- point evaluation of a level
+def particle_cells(count, start, targets):
+    """IOS cell of each selected particle (flat ids), from counts and starts."""
+    ends = start.astype(np.int64) + count.astype(np.int64)
+    return np.searchsorted(ends, np.asarray(targets, dtype=np.int64), side="right")
+
+
+def pm_force_level_at(phi, off, count, start, n_ios, h, targets):
+    """F = -H interp(D * phi) of one level at selected particles only, (3, K).
+
+    The same steps as ``pm_force_level`` after the solve (Eq. diff as the
+    real-space 4-point difference, then the CIC gather with the deposit's
+    integer weights), but the difference is formed only at the 8 cells each
+    selected particle gathers from: E_d(c) = 2/3 [phi(c+e_d) - phi(c-e_d)] -
+    1/12 [phi(c+2e_d) - phi(c-2e_d)], periodic."""
+    n = phi.shape[0]
+    targets = np.asarray(targets, dtype=np.int64)
+    c = particle_cells(count, start, targets)
+    cc = np.stack([c % n_ios, (c // n_ios) % n_ios, c // (n_ios * n_ios)])
+    X = cc * FIX + off[:, targets].astype(np.int64)
+    s = level_shift(n_ios, n)
+    parts = [cic_integer_weights(X[d], s) for d in range(3)]
+    out = np.zeros((3, len(targets)))
+    for oz in (0, 1):
+        for oy in (0, 1):
+            for ox in (0, 1):
+                idx = [parts[0][0] + ox, parts[1][0] + oy, parts[2][0] + oz]
+                wgt = (parts[0][1 + ox] * parts[1][1 + oy] * parts[2][1 + oz]).astype(np.float64) * 2.0 ** -48
+                for d in range(3):
+                    def at(step):
+                        j = list(idx)
+                        j[d] = j[d] + step
+                        return phi[j[2] % n, j[1] % n, j[0] % n]
+                    e = 2.0 / 3.0 * (at(1) - at(-1)) - 1.0 / 12.0 * (at(2) - at(-2))
+                    out[d] += wgt * e
+    return -h * out

@@ -454,11 +454,10 @@ __global__ void noalloc_twiddle_kernel(float2 *tw, int n) {
 }
 
 template <int N>
-cudaError_t noalloc_passes(const float *rho, float2 *spec, const float *gpad, float *phi, const float2 *tw,
+cudaError_t noalloc_passes(const float *rho, float2 *spec, const float *gpad, float *phi, const float2 *tw, int kxp,
                            cudaStream_t st) {
     Launcher<N>::setup();
     constexpr int L = Tile<N>::L;
-    const int kxp = NOALLOC_KXP;
     const int64_t nrows = (int64_t)N * N;
     const unsigned bx = (unsigned)((nrows + 2 * L - 1) / (2 * L));
     const unsigned by = (unsigned)((int64_t)N * (kxp / L));
@@ -489,8 +488,13 @@ extern "C" int cube2_solve_pm_noalloc(const float *rho, const float *green, floa
     }
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess || dev < 0 || dev >= NOALLOC_MAX_DEVICES) {
+    if (e != cudaSuccess) {
         set_context_free_error(std::string("cube2_solve_pm_noalloc: no usable device: ") + cudaGetErrorString(e));
+        return CUBE2_ERR_CUDA;
+    }
+    if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) {
+        set_context_free_error("cube2_solve_pm_noalloc: device index " + std::to_string(dev) + " beyond the " +
+                               std::to_string(NOALLOC_MAX_DEVICES) + " devices this entry point serves");
         return CUBE2_ERR_CUDA;
     }
     void *base = nullptr;
@@ -513,28 +517,30 @@ extern "C" int cube2_solve_pm_noalloc(const float *rho, const float *green, floa
     float *gpad = reinterpret_cast<float *>(b + NOALLOC_SPEC_BYTES);
     float2 *tw = reinterpret_cast<float2 *>(b + NOALLOC_SPEC_BYTES + NOALLOC_GREEN_BYTES);
     const size_t nh = (size_t)(n / 2 + 1);
+    // rows of the half spectrum padded to a multiple of 16 columns, as in a
+    // context; the array holds the 128^3 layout, so every smaller mesh fits
+    const int kxp = (int)((nh + 15) / 16 * 16);
     // the caller's compact [n][n][n/2+1] table into the padded layout; the
     // padding columns, left from earlier calls, are cleared
-    e = cudaMemcpy2DAsync(gpad, NOALLOC_KXP * sizeof(float), green, nh * sizeof(float), nh * sizeof(float),
+    e = cudaMemcpy2DAsync(gpad, kxp * sizeof(float), green, nh * sizeof(float), nh * sizeof(float),
                           (size_t)n * n, cudaMemcpyDeviceToDevice, st);
-    if (e == cudaSuccess)
-        e = cudaMemset2DAsync(gpad + nh, NOALLOC_KXP * sizeof(float), 0, (NOALLOC_KXP - nh) * sizeof(float),
-                              (size_t)n * n, st);
+    if (e == cudaSuccess && (size_t)kxp > nh)
+        e = cudaMemset2DAsync(gpad + nh, kxp * sizeof(float), 0, (kxp - nh) * sizeof(float), (size_t)n * n, st);
     if (e == cudaSuccess) {
         noalloc_twiddle_kernel<<<(n + 127) / 128, 128, 0, st>>>(tw, n);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) {
         switch (n) {
-            case 8: e = noalloc_passes<8>(rho, spec, gpad, phi, tw, st); break;
-            case 12: e = noalloc_passes<12>(rho, spec, gpad, phi, tw, st); break;
-            case 16: e = noalloc_passes<16>(rho, spec, gpad, phi, tw, st); break;
-            case 24: e = noalloc_passes<24>(rho, spec, gpad, phi, tw, st); break;
-            case 32: e = noalloc_passes<32>(rho, spec, gpad, phi, tw, st); break;
-            case 48: e = noalloc_passes<48>(rho, spec, gpad, phi, tw, st); break;
-            case 64: e = noalloc_passes<64>(rho, spec, gpad, phi, tw, st); break;
-            case 96: e = noalloc_passes<96>(rho, spec, gpad, phi, tw, st); break;
-            case 128: e = noalloc_passes<128>(rho, spec, gpad, phi, tw, st); break;
+            case 8: e = noalloc_passes<8>(rho, spec, gpad, phi, tw, kxp, st); break;
+            case 12: e = noalloc_passes<12>(rho, spec, gpad, phi, tw, kxp, st); break;
+            case 16: e = noalloc_passes<16>(rho, spec, gpad, phi, tw, kxp, st); break;
+            case 24: e = noalloc_passes<24>(rho, spec, gpad, phi, tw, kxp, st); break;
+            case 32: e = noalloc_passes<32>(rho, spec, gpad, phi, tw, kxp, st); break;
+            case 48: e = noalloc_passes<48>(rho, spec, gpad, phi, tw, kxp, st); break;
+            case 64: e = noalloc_passes<64>(rho, spec, gpad, phi, tw, kxp, st); break;
+            case 96: e = noalloc_passes<96>(rho, spec, gpad, phi, tw, kxp, st); break;
+            case 128: e = noalloc_passes<128>(rho, spec, gpad, phi, tw, kxp, st); break;
             default: e = cudaErrorInvalidValue; break;
         }
     }

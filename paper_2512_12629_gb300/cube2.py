@@ -95,6 +95,7 @@ def _load():
         "cube2_profile_class_name": (ctypes.c_char_p, [I]),
         "cube2_pp_stats": (I, [P, ctypes.POINTER(ctypes.c_int64)]),
         "cube2_solve_pm_noalloc": (I, [P, P, P, ctypes.c_int32, P]),
+        "cube2_fma_probe": (I, [P, I, I, I, P]),
         "cube2_adjoint_init": (I, [P]),
         "cube2_force_vjp": (I, [P, ctypes.POINTER(Particles), P, P]),
         "cube2_kdk_permutation": (I, [P, P]),
@@ -385,12 +386,34 @@ def solve_pm_noalloc(rho: torch.Tensor, green: torch.Tensor, phi: torch.Tensor, 
 
     For callers that cannot allocate where they need a solve; the library keeps
     its working memory in a fixed device array (meshes up to 128^3).  rho and
-    phi are [n][n][n] FP32, green the [n][n][n/2+1] table of ``get_green``."""
-    n = rho.shape[0]
-    st = torch.cuda.current_stream() if stream is None else stream
-    code = _lib.cube2_solve_pm_noalloc(rho.data_ptr(), green.data_ptr(), phi.data_ptr(), n, st.cuda_stream)
+    phi are contiguous FP32 [n][n][n], green the contiguous FP32 [n][n][n/2+1]
+    table of ``get_green``, all on one CUDA device; the call runs on that
+    device's current stream (or ``stream``).  Raises ValueError before calling
+    into the library when a tensor does not match."""
+    if rho.dim() != 3 or len(set(rho.shape)) != 1:
+        raise ValueError("rho must be an (n, n, n) tensor")
+    n = int(rho.shape[0])
+    for name, t, shape in (("rho", rho, (n, n, n)), ("phi", phi, (n, n, n)), ("green", green, (n, n, n // 2 + 1))):
+        if t.dtype != torch.float32 or tuple(t.shape) != shape or not t.is_contiguous() or not t.is_cuda:
+            raise ValueError(f"{name} must be a contiguous float32 CUDA tensor of shape {shape}")
+    if not (rho.device == phi.device == green.device):
+        raise ValueError("rho, green and phi must be on one device")
+    with torch.cuda.device(rho.device):
+        st = torch.cuda.current_stream(rho.device) if stream is None else stream
+        code = _lib.cube2_solve_pm_noalloc(rho.data_ptr(), green.data_ptr(), phi.data_ptr(), n,
+                                           ctypes.c_void_p(st.cuda_stream))
     if code != OK:
         raise Cube2Error(code, _lib.cube2_last_error(None).decode())
+
+
+def fma_probe(out: torch.Tensor, blocks, threads, iters, stream=None):
+    """Launch the FP32 FMA probe (cube2_fma_probe) on ``stream``; returns the
+    FP32 operations it performs (2 * 8 * 16 * iters * blocks * threads)."""
+    st = torch.cuda.current_stream() if stream is None else stream
+    code = _lib.cube2_fma_probe(out.data_ptr(), int(blocks), int(threads), int(iters), ctypes.c_void_p(st.cuda_stream))
+    if code != OK:
+        raise Cube2Error(code, "fma_probe")
+    return 2 * 8 * 16 * int(iters) * int(blocks) * int(threads)
 
 
 def config_cost(cfg: Config):

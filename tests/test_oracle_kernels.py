@@ -128,3 +128,16 @@ def test_green_continuum_limit():
     k = kx[0, 0, 1]
     ref = -(K.profile_transform(k, b) ** 2 - K.profile_transform(k, 14.0) ** 2) / k ** 2
     assert abs(gt[0, 0, 1] / ref - 1) < 0.25 * k * k
+
+
+@pytest.mark.parametrize("n,order,iso", [(16, 2, None), (24, 2, None), (12, 3, 4.0)])
+def test_green_by_symmetry_equals_full_table(n, order, iso):
+    # the table built once per sorted |m| triple and expanded by the symmetries
+    # equals the mode-by-mode table up to the order of the alias sum
+    tri = K.sorted_mode_triples(n)
+    m = n // 2
+    assert len(tri) == (m + 1) * (m + 2) * (m + 3) // 6
+    assert np.all((tri[:, 0] <= tri[:, 1]) & (tri[:, 1] <= tri[:, 2]) & (tri[:, 2] <= m))
+    g = K.green(n, 2.0, 7.0, order=order, iso=iso)
+    gs = K.green_by_symmetry(n, 2.0, 7.0, order=order, iso=iso, chunk=37)
+    assert np.abs(gs - g).max() <= 1e-13 * np.abs(g).max()

@@ -147,3 +147,18 @@ def test_point_green_equals_full_table():
     modes = np.stack([rng.integers(0, 13, 80), rng.integers(0, 24, 80), rng.integers(0, 24, 80)], 1)
     modes[:4] = [[12, 12, 12], [0, 0, 0], [12, 0, 5], [3, 12, 12]]
     assert np.array_equal(K.green_at(24, modes, 2.0, 9.0), g[modes[:, 2], modes[:, 1], modes[:, 0]])
+
+
+@pytest.mark.parametrize("n_ios,n_mesh", [(16, 32), (16, 8), (12, 24), (16, 16)])
+def test_point_level_force_equals_full_gather(n_ios, n_mesh):
+    # pm_force_level_at forms the 4-point difference only at the gathered
+    # cells; it must equal the whole-mesh difference followed by the gather,
+    # wrapped cells and every level ratio included
+    st = random_ios(3000, n_ios, float(n_ios), seed=5, clustered=0.4)
+    acc = M.deposit_u64(st["off"], st["count"], n_ios, n_mesh)
+    phi = M.solve_potential(M.density(acc, 3000), K.green(n_mesh, 2.0, None))
+    h = n_ios / n_mesh
+    full = -h * M.interpolate(M.fd_gradient(phi), st["off"], st["count"], n_ios)
+    t = np.random.default_rng(0).integers(0, 3000, 200)
+    at = M.pm_force_level_at(phi, st["off"], st["count"], st["start"], n_ios, h, t)
+    assert np.array_equal(at, full[:, t])

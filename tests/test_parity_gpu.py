@@ -64,8 +64,9 @@ def _state(name):
         w = c4_ensemble(n_boxes=1, seed=41, sizes=(24,))[0]
         return w, zeldovich_ios(w)
     if name == "DENSE":
-        # a 4500-particle clump: its brick holds more particles than the brick
-        # kernel stages, so its cells go through the tiled PP kernel
+        # a 4500-particle clump: cells of hundreds of particles (the PP kernel's
+        # sub-cell ordering of dense cells and its shared-stream path, the
+        # deposit's heavily loaded bricks)
         from inputs.zeldovich import ios_from_positions
         rng = np.random.Generator(np.random.Philox(33))
         clump = 32.0 + rng.normal(0.0, 2.0, size=(3, 4500))
