@@ -230,7 +230,9 @@ def algorithmic_bytes(w, n_part, cls, level):
         "pp_order": 4 * C + 26 * N,
         "sort_big": 8 * N,
     }
-    return table[cls]
+    # the third level's classes move data-dependent amounts (the refined
+    # subtiles' local boxes): no algorithmic figure
+    return table.get(cls)
 
 
 # FP32 operations (an FMA counts 2) of one in-range PP pair, as the roofline
@@ -775,6 +777,8 @@ def main():
     ctx = cube2.init_mesh(cube2.make_config(w, n_particles=n_part))
     for l in range(len(w.levels)):
         ctx.set_green(l)
+    if w.pm3 is not None:
+        ctx.set_green(cube2.LEVEL_PM3)
     p0 = cube2.IOSState.from_numpy(st)
     ctx.force(p0)
     p = p0.clone()
@@ -797,7 +801,7 @@ def main():
     # per-step CUDA events and PP pair counts, and the states the timed steps start from
     load(p, p0)
     ckpt = {}
-    sched_ms, sched_pairs = [], []
+    sched_ms, sched_pairs, sched_pm3 = [], [], []
     ctx.pp_stats()
     for i in range(S):
         if i in idx:
@@ -809,6 +813,8 @@ def main():
         e1.synchronize()
         sched_ms.append(e0.elapsed_time(e1))
         sched_pairs.append(ctx.pp_stats()[0])
+        if w.pm3 is not None:
+            sched_pm3.append(ctx.pm3_stats()[0])
     ctx.check()
     torch.cuda.synchronize()
 
@@ -860,12 +866,20 @@ def main():
     kernels = {}
     for (c, l), (kms, kc) in sorted(prof.items(), key=lambda kv: -kv[1][0]):
         b = algorithmic_bytes(w, n_part, c, l)
+        gbps = None if b is None else b / (kms / kc / 1e3) / 1e9
         kernels[f"{c}/{l}"] = {"share": kms / total_prof, "ms_per_launch": kms / kc, "launches": kc,
-                               "GBps_alg": b / (kms / kc / 1e3) / 1e9, "frac_hbm": b / (kms / kc / 1e3) / 1e9 / peak}
+                               "GBps_alg": gbps, "frac_hbm": None if gbps is None else gbps / peak}
     kernels["pp_work"] = {"pairs_per_step": pp_pairs / args.steps, "candidates_per_step": pp_cands / args.steps}
-    full = {"steps": S, "ms_per_step": sum(sched_ms) / S, "value": n_part * S / (sum(sched_ms) / 1e3),
+    if sched_pm3:
+        full_pm3 = {"refined_subtiles_each": sched_pm3, "subtile_ios_cells": w.pm3.tile,
+                    "rho_min": w.pm3.rho_min, "refine": w.pm3.refine, "beta3": w.pm3.beta}
+    else:
+        full_pm3 = None
+    full = {"steps": S, "pm3": full_pm3, "ms_per_step": sum(sched_ms) / S, "value": n_part * S / (sum(sched_ms) / 1e3),
             "ms_first_last_10": [sum(sched_ms[:10]) / 10, sum(sched_ms[-10:]) / 10],
             "pp_pairs_first_last_step": [sched_pairs[0], sched_pairs[-1]],
+            "ms_per_step_each": [round(x, 3) for x in sched_ms],
+            "pp_pairs_each": sched_pairs,
             "what": "the whole schedule from the initial conditions, per-step CUDA events (untimed run)"}
 
     # end to end through the host-buffer entry point, on the same steps

@@ -91,7 +91,28 @@ typedef struct {
                                         * every alias image; at most box/2, so a
                                         * pair closer than iso_length - b_coarse
                                         * feels no periodic image             */
+    /* Adaptive third PM level (Sec. 2.1.1 Eq. PM3, Sec. 2.2.3), CIC only.
+     * pm3_tile = 0 switches it off (the fields below are then ignored).  The
+     * box is cut into subtiles of pm3_tile^3 IOS cells (pm3_tile divides
+     * n_ios); a subtile whose densest IOS cell holds >= pm3_rho_min particles
+     * gets a local periodic mesh of spacing H_3 = H_finest / pm3_refine over
+     * the subtile plus a buffer of B = ceil(b_finest / H_3) + 4 cells on each
+     * side (m = the smallest 2^a 3^b >= pm3_tile s_ios / H_3 + 2 B cells, which
+     * must be a supported mesh size), softening b_3 = pm3_beta H_3 and the
+     * kernel R(r, b_3) - R(r, b_finest); its own particles get that force and
+     * a PP range of b_3 instead of b_finest.  pm3_refine: a power of two with
+     * H_3 <= s_ios; b_pp < b_3 < b_finest.  At most pm3_max_tiles subtiles are
+     * refined per force evaluation (the first in subtile order, x fastest);
+     * the rest keep the two-level method.                                    */
+    int32_t pm3_tile;
+    int32_t pm3_refine;
+    double  pm3_beta;
+    int32_t pm3_rho_min;
+    int32_t pm3_max_tiles;
 } cube2_config;
+
+/* Level index of the adaptive third level in cube2_set_green / cube2_get_green. */
+#define CUBE2_LEVEL_PM3 2
 
 /* Particle set in IOS form; every pointer is a device pointer (see above). */
 typedef struct {
@@ -126,6 +147,29 @@ int cube2_init_mesh(cube2_ctx **ctx, const cube2_config *cfg, void *stream);
  * otherwise the computed table is written there (Sec. 2.1.2: tables may be
  * stored as files).  Synchronises the stream when a file is used. */
 int cube2_set_green(cube2_ctx *ctx, int level, const char *cache_path);
+
+/* The adaptive third level (cfg.pm3_tile > 0) is part of cube2_force and
+ * cube2_kdk_step once its table is built: cube2_set_green(ctx,
+ * CUBE2_LEVEL_PM3, path) evaluates Eq. (Gk) for the local m^3 mesh with
+ * softening pm3_beta and truncation b_finest / H_3 (local cells).  Each force
+ * evaluation then builds the refinement map from the counts, deposits the
+ * refined subtiles' local boxes (exact integer CIC, FP32 density
+ * V_p / H_3^3 sum W), solves all local meshes in one batch of FFT passes,
+ * adds -H_3 (D * phi) gathered at each refined subtile's own particles to acc
+ * and runs PP with the per-target range.  cube2_pp_force alone uses the map
+ * of the counts it is given as well.  The adjoint entry points reject a
+ * context with the third level (CUBE2_ERR_STATE).
+ *
+ * cube2_pm3_info: out = {pm3_tile, subtiles per dimension, refinement r,
+ * buffer B, mesh m, H_3 [Mpc/h], b_3 [Mpc/h], pm3_max_tiles} (host only;
+ * CUBE2_ERR_STATE when the third level is off).
+ * cube2_pm3_stats: synchronises; out = {local meshes in use, subtiles that
+ * asked for refinement} of the last force or PP call.
+ * cube2_pm3_map: out (device int32 [subtiles^3], x fastest) = the local mesh
+ * index of each subtile in the last force or PP call, -1 where unrefined. */
+int cube2_pm3_info(cube2_ctx *ctx, double out[8]);
+int cube2_pm3_stats(cube2_ctx *ctx, int64_t out[2]);
+int cube2_pm3_map(cube2_ctx *ctx, int32_t *out);
 
 /* CIC mass assignment (Eq. filter, CIC reading) of the particles onto level
  * `level` (or every level in one particle pass when level = -1).  Integer
@@ -261,7 +305,7 @@ const char *cube2_last_error(cube2_ctx *ctx);
  * counts[...] (arrays of CUBE2_PROFILE_CLASSES * CUBE2_MAX_LEVELS), clears the
  * records, and returns CUBE2_ERR_CAPACITY if the pool overflowed.  Class
  * names: cube2_profile_class_name. */
-#define CUBE2_PROFILE_CLASSES 23
+#define CUBE2_PROFILE_CLASSES 27
 int cube2_profile(cube2_ctx *ctx, int cap);
 int cube2_profile_read(cube2_ctx *ctx, double *ms, int64_t *counts);
 const char *cube2_profile_class_name(int cls);

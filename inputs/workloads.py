@@ -24,6 +24,19 @@ class Level:
 
 
 @dataclass(frozen=True)
+class PM3Spec:
+    """Adaptive third PM level: subtiles of ``tile``^3 IOS cells; a subtile
+    whose densest IOS cell holds >= ``rho_min`` particles gets a local mesh of
+    spacing H_finest / ``refine`` with softening ``beta`` local cells (its PP
+    range); at most ``max_tiles`` refined subtiles per force evaluation."""
+    tile: int
+    refine: int
+    beta: float
+    rho_min: int
+    max_tiles: int = 4096
+
+
+@dataclass(frozen=True)
 class Workload:
     name: str
     n_p: int                     # particles per dimension on the Lagrangian lattice
@@ -44,6 +57,7 @@ class Workload:
     displace_to_a: float | None = None
     assign_order: int = 2        # mass assignment: 2 = CIC (the workload's), 3 = TSC (the paper's)
     iso_length: float = 0.0      # > 0: isolated boundary conditions, force truncated at this r [Mpc/h]
+    pm3: PM3Spec | None = None   # adaptive third PM level (None: the global levels only)
 
     @property
     def n_particles(self) -> int:
@@ -143,4 +157,11 @@ def c4_ensemble(n_boxes=64, seed=100, n_steps=20, sizes=(32, 48, 64, 96)):
             for b, (n, sg) in enumerate(zip(n_ps, s8))]
 
 
-WORKLOADS = {w.name: w for w in (C1, C2, C2_SMALL, C2_MID, C3, C5, C2_SMALL_TSC, C2_TSC, ISO_PAIRS)}
+# The 256^3 run with the adaptive third PM level: subtiles of 8^3 IOS cells
+# (8 Mpc/h) whose densest IOS cell holds >= 24 particles get a local mesh of
+# 0.25 Mpc/h cells (48^3 with its buffer) and softening 2 local cells, which
+# halves their PP range.
+C2_PM3 = C2.with_(name="pm2-256c-128x512mesh-pm3", pm3=PM3Spec(tile=8, refine=2, beta=2.0, rho_min=24,
+                                                                max_tiles=8192))
+
+WORKLOADS = {w.name: w for w in (C1, C2, C2_SMALL, C2_MID, C3, C5, C2_SMALL_TSC, C2_TSC, ISO_PAIRS, C2_PM3)}

@@ -137,27 +137,38 @@ def subtile_of(off, count, n_ios, T):
 def adaptive_force(off, count, start, w, T, refine, beta3, greens=None, alias=2):
     """Total force (3, N) with the adaptive third level: the global levels of
     ``w``, PM3 per subtile with refinement refine[sz, sy, sx] and softening
-    beta3 cells, PP per subtile with range b_3 = beta3 H_3."""
+    beta3 cells, PP per subtile with range b_3 = beta3 H_3.
+
+    A subtile whose b_3 equals the finest global softening has the kernel
+    R(r, b_3) - R(r, b_fine) = 0: its PM3 force is zero and is not formed.
+    The PP force is evaluated once per distinct range over all the targets
+    that have it (each target's sum is independent of the others')."""
     if w.n_ios % T:
         raise ValueError("T must divide n_ios")
     n_part = int(count.sum())
     pos = positions(off, count, w.n_ios, w.box)
     total = pm_force(off, count, w, greens)
-    b_pp, _ = pp_params(w)
+    b_pp, b_fine = pp_params(w)
     sub = subtile_of(off, count, w.n_ios, T)
     ns = w.n_ios // T
     refine = np.asarray(refine).reshape(ns, ns, ns)
-    tables = {r: pm3_green(w, T, int(r), beta3, alias) for r in np.unique(refine)}
+    geo = {int(r): local_mesh(w, T, int(r), beta3) for r in np.unique(refine)}
+    vanishes = {r: abs(g[1] - b_fine) <= 1e-12 * b_fine for r, g in geo.items()}
+    tables = {r: pm3_green(w, T, r, beta3, alias) for r in geo if not vanishes[r]}
+    by_range = {}
     for sz in range(ns):
         for sy in range(ns):
             for sx in range(ns):
                 r = int(refine[sz, sy, sx])
-                f3, idx = pm3_force_subtile(pos, w, T, (sx, sy, sz), r, beta3, n_part, alias, tables[r])
-                _h3, b3, _B, _m = local_mesh(w, T, r, beta3)
                 mine = np.nonzero((sub[0] == sx) & (sub[1] == sy) & (sub[2] == sz))[0]
-                assert np.array_equal(np.sort(idx), mine)
                 if mine.size == 0:
                     continue
-                total[:, idx] += f3
-                total[:, mine] += pp_force(off, count, start, w.n_ios, w.box, b_pp, b3, targets=mine)
+                if not vanishes[r]:
+                    f3, idx = pm3_force_subtile(pos, w, T, (sx, sy, sz), r, beta3, n_part, alias, tables[r])
+                    assert np.array_equal(np.sort(idx), mine)
+                    total[:, idx] += f3
+                by_range.setdefault(geo[r][1], []).append(mine)
+    for b3, parts in by_range.items():
+        t = np.concatenate(parts)
+        total[:, t] += pp_force(off, count, start, w.n_ios, w.box, b_pp, b3, targets=t)
     return total

@@ -22,7 +22,7 @@ int set_error(cube2_ctx *ctx, int code, const std::string &msg) {
 }
 
 int prof_begin(cube2_ctx *ctx, int cls, int level) {
-    if (!ctx->prof) return -1;
+    if (!ctx->prof || cls < 0) return -1;
     if (ctx->prof_used >= ctx->prof_cap) { ctx->prof_overflow = 1; return -1; }
     const int slot = ctx->prof_used++;
     ctx->prof_cls[slot] = cls * CUBE2_MAX_LEVELS + level;
@@ -136,6 +136,15 @@ void free_ctx(cube2_ctx *c) {
     cudaFree(c->vjp_u);
     cudaFree(c->vjp_sq);
     cudaFree(c->pp_stats);
+    cudaFree(c->pm3.lev.real);
+    cudaFree(c->pm3.lev.spec);
+    cudaFree(c->pm3.lev.green);
+    cudaFree(c->pm3.lev.tw);
+    cudaFree(c->pm3.acc);
+    cudaFree(c->pm3.rho_max);
+    cudaFree(c->pm3.slot);
+    cudaFree(c->pm3.list);
+    cudaFree(c->pm3.count);
     cudaFree(c->dev_status);
     cudaFreeHost(c->host_status);
     if (c->aux_event) cudaEventDestroy(c->aux_event);
@@ -159,6 +168,59 @@ int level_ok(cube2_ctx *ctx, int level, bool allow_all) {
     if (allow_all && level == -1) return CUBE2_OK;
     if (level < 0 || level >= ctx->nl) return set_error(ctx, CUBE2_ERR_BAD_ARG, "level out of range");
     return CUBE2_OK;
+}
+
+// Geometry of the adaptive third level from the config (after the global
+// levels are set up).  Returns "" when valid, else 'U' (unsupported size) or
+// 'B' (bad argument) followed by the message.
+std::string pm3_geometry(cube2_ctx *c) {
+    const cube2_config *cfg = &c->cfg;
+    PM3 &M = c->pm3;
+    const Level &F = c->lev[c->nl - 1];
+    if (c->cfg.assign_order != 2) return "Bthe adaptive third level uses CIC assignment";
+    if (c->n_ios % cfg->pm3_tile) return "Bpm3_tile must divide n_ios";
+    const int r = cfg->pm3_refine;
+    if (r < 1 || (r & (r - 1))) return "Bpm3_refine must be a power of two";
+    int lr = 0;
+    while ((1 << lr) < r) ++lr;
+    // H_finest / s_ios = n_ios / n_finest = 2^F.shift, so H_3 / s_ios = 2^-(lr - F.shift)
+    const int q_shift = lr - F.shift;
+    if (q_shift < 0 || q_shift > 12) return "Bthe third level's cell must be at most the IOS cell (and >= 2^-12 of it)";
+    if (cfg->pm3_rho_min < 1 || cfg->pm3_max_tiles < 1) return "Bpm3_rho_min and pm3_max_tiles must be positive";
+    M.T = cfg->pm3_tile;
+    M.ns = c->n_ios / M.T;
+    M.n_sub = (int64_t)M.ns * M.ns * M.ns;
+    M.r = r;
+    M.q_shift = q_shift;
+    M.rho_min = cfg->pm3_rho_min;
+    M.max_tiles = cfg->pm3_max_tiles;
+    M.H = F.H / r;
+    M.b3 = cfg->pm3_beta * M.H;
+    if (!(M.b3 < c->b_range) || !(M.b3 > cfg->b_pp)) return "Bthe third level's softening must lie between b_pp and the PP range";
+    M.B = (int)ceil(c->b_range / M.H - 1e-12) + 4;
+    const int64_t need = ((int64_t)M.T << q_shift) + 2 * M.B;
+    int64_t best = -1;
+    for (int64_t a = 1; a <= (int64_t)1 << 20; a *= 2)
+        for (int64_t v = a; v <= (int64_t)1 << 22; v *= 3)
+            if (v >= need && (best < 0 || v < best)) best = v;
+    if (best < 0 || !fft_size_supported((int)best)) return "Uthe third level's local mesh size is not supported";
+    M.m = (int)best;
+    if (M.m * M.H > cfg->box * (1.0 + 1e-12)) return "Bthe third level's local box exceeds the simulation box";
+    const int64_t m3 = (int64_t)M.m * M.m * M.m;
+    if ((int64_t)M.max_tiles * m3 > ((int64_t)1 << 31) * 8) return "Bpm3_max_tiles x local mesh too large";
+    Level &L = M.lev;
+    L.index = 0;
+    L.n = M.m;
+    L.kxp = ((L.n / 2 + 1) + 15) / 16 * 16;
+    L.H = M.H;
+    L.b_soft = cfg->pm3_beta;
+    L.b_trunc = c->b_range / M.H;
+    L.iso = 0.0;
+    L.batch = M.max_tiles;
+    const double vp = cfg->box * cfg->box * cfg->box / (double)(c->N > 0 ? c->N : 1);
+    M.dens_scale = (float)(vp / (M.H * M.H * M.H) * ldexp(1.0, -48));
+    M.on = true;
+    return "";
 }
 
 }  // namespace
@@ -227,6 +289,13 @@ int cube2_init_mesh(cube2_ctx **out, const cube2_config *cfg, void *stream) {
         delete c;
         return fail(CUBE2_ERR_BAD_ARG, "b_pp must be below the PP range");
     }
+    if (cfg->pm3_tile > 0) {
+        const std::string why = pm3_geometry(c);
+        if (!why.empty()) {
+            delete c;
+            return fail(why[0] == 'U' ? CUBE2_ERR_UNSUPPORTED_SIZE : CUBE2_ERR_BAD_ARG, why.substr(1));
+        }
+    }
     cudaError_t e = cudaSuccess;
     auto alloc = [&](void **ptr, size_t bytes) {
         if (e != cudaSuccess) return;
@@ -259,6 +328,28 @@ int cube2_init_mesh(cube2_ctx **out, const cube2_config *cfg, void *stream) {
     alloc((void **)&c->pp_perm, N * 4);
     alloc((void **)&c->pp_stats, 2 * sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaMemsetAsync(c->pp_stats, 0, 2 * sizeof(unsigned long long), c->stream);
+    if (c->pm3.on) {
+        PM3 &M = c->pm3;
+        Level &L = M.lev;
+        const size_t m3 = (size_t)L.n * L.n * L.n;
+        const size_t nh = (size_t)L.n * L.n * L.kxp;
+        alloc((void **)&L.real, (size_t)M.max_tiles * m3 * sizeof(float));
+        alloc((void **)&L.spec, (size_t)M.max_tiles * nh * sizeof(float2));
+        L.green_len = green_table_len(L.n);
+        alloc((void **)&L.green, (size_t)L.green_len * sizeof(float));
+        alloc((void **)&L.tw, (size_t)L.n * sizeof(float2));
+        alloc((void **)&M.acc, (size_t)M.max_tiles * m3 * sizeof(unsigned long long));
+        alloc((void **)&M.rho_max, (size_t)M.n_sub * 4);
+        alloc((void **)&M.slot, (size_t)M.n_sub * 4);
+        alloc((void **)&M.list, (size_t)M.max_tiles * 4);
+        alloc((void **)&M.count, 2 * sizeof(int));
+        if (e == cudaSuccess) e = cudaMemsetAsync(L.spec, 0, (size_t)M.max_tiles * nh * sizeof(float2), c->stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(M.acc, 0, (size_t)M.max_tiles * m3 * 8, c->stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(M.count, 0, 2 * sizeof(int), c->stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(M.slot, 0xff, (size_t)M.n_sub * 4, c->stream);
+        L.active = M.count;
+        if (e == cudaSuccess) e = launch_init_twiddles(c, L);
+    }
     cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device);
     c->scan_tmp_len = scan_scratch_len(c->n_cells);
     alloc((void **)&c->scan_tmp, (size_t)c->scan_tmp_len * 4);
@@ -280,9 +371,10 @@ int cube2_init_mesh(cube2_ctx **out, const cube2_config *cfg, void *stream) {
 
 int cube2_set_green(cube2_ctx *ctx, int level, const char *cache_path) {
     if (!ctx) return CUBE2_ERR_BAD_ARG;
-    int r = level_ok(ctx, level, false);
+    const bool pm3 = level == CUBE2_LEVEL_PM3 && ctx->pm3.on;
+    int r = pm3 ? CUBE2_OK : level_ok(ctx, level, false);
     if (r) return r;
-    Level &L = ctx->lev[level];
+    Level &L = pm3 ? ctx->pm3.lev : ctx->lev[level];
     const size_t nh = (size_t)L.green_len;
     // cache header: magic, n, entries (reduced layout), alias, assignment order, b_soft, b_trunc, isolation length
     struct Header { char magic[8]; int32_t n, len, alias, order; double b_soft, b_trunc, iso; } hdr{};
@@ -414,6 +506,7 @@ int cube2_pp_force(cube2_ctx *ctx, const cube2_particles *p, int accumulate) {
     if (!ctx) return CUBE2_ERR_BAD_ARG;
     if (!particles_ok(ctx, p, false, true)) return set_error(ctx, CUBE2_ERR_BAD_ARG, "bad particle arrays");
     cudaError_t e = launch_cellid(ctx, p);
+    if (e == cudaSuccess && ctx->pm3.on) e = launch_pm3_map(ctx, p);
     if (e == cudaSuccess) e = launch_pp(ctx, p, accumulate, 0.0f);
     if (e != cudaSuccess) return cuda_error(ctx, e, "pp_force");
     return CUBE2_OK;
@@ -423,6 +516,8 @@ int cube2_pp_force(cube2_ctx *ctx, const cube2_particles *p, int accumulate) {
 static int force_core(cube2_ctx *ctx, const cube2_particles *p, float kick) {
     for (int l = 0; l < ctx->nl; ++l)
         if (!ctx->lev[l].has_green) return set_error(ctx, CUBE2_ERR_STATE, "force needs every level's Green's table");
+    if (ctx->pm3.on && !ctx->pm3.lev.has_green)
+        return set_error(ctx, CUBE2_ERR_STATE, "force needs the third level's Green's table (CUBE2_LEVEL_PM3)");
     cudaError_t e = deposit_levels(ctx, -1, p);
     for (int l = 0; l < ctx->nl && e == cudaSuccess; ++l) {
         e = launch_fft_forward(ctx, ctx->lev[l]);
@@ -432,6 +527,7 @@ static int force_core(cube2_ctx *ctx, const cube2_particles *p, float kick) {
         ctx->lev[l].has_potential = true;
     }
     if (e == cudaSuccess) e = interp_levels(ctx, -1, p, 0);
+    if (e == cudaSuccess && ctx->pm3.on) e = launch_pm3(ctx, p);
     if (e == cudaSuccess) e = launch_pp(ctx, p, 1, kick);
     if (e != cudaSuccess) return cuda_error(ctx, e, "force");
     return CUBE2_OK;
@@ -492,6 +588,7 @@ int cube2_ios_from_positions(cube2_ctx *ctx, const double *const pos[3], const f
 
 int cube2_adjoint_init(cube2_ctx *ctx) {
     if (!ctx) return CUBE2_ERR_BAD_ARG;
+    if (ctx->pm3.on) return set_error(ctx, CUBE2_ERR_STATE, "the adjoint does not cover the adaptive third level");
     if (ctx->vjp_mu) return CUBE2_OK;
     int64_t m = 0;
     for (int l = 0; l < ctx->nl; ++l) m = std::max(m, (int64_t)ctx->lev[l].n * ctx->lev[l].n * ctx->lev[l].n);
@@ -729,10 +826,11 @@ int cube2_get_potential(cube2_ctx *ctx, int level, float *out) {
 
 int cube2_get_green(cube2_ctx *ctx, int level, float *out) {
     if (!ctx) return CUBE2_ERR_BAD_ARG;
-    int r = level_ok(ctx, level, false);
+    const bool pm3 = level == CUBE2_LEVEL_PM3 && ctx->pm3.on;
+    int r = pm3 ? CUBE2_OK : level_ok(ctx, level, false);
     if (r) return r;
     if (!out) return set_error(ctx, CUBE2_ERR_BAD_ARG, "null out");
-    const Level &L = ctx->lev[level];
+    const Level &L = pm3 ? ctx->pm3.lev : ctx->lev[level];
     if (!L.has_green) return set_error(ctx, CUBE2_ERR_STATE, "no Green's table");
     const cudaError_t e = launch_green_expand(ctx, L, out);
     return e == cudaSuccess ? CUBE2_OK : cuda_error(ctx, e, "green expand");
@@ -819,7 +917,8 @@ const char *cube2_profile_class_name(int cls) {
     static const char *names[CUBE2_PROFILE_CLASSES] = {
         "deposit", "fft_x_fwd", "fft_y_fwd", "fft_z_green", "fft_y_inv", "fft_x_inv", "interp", "pp",
         "kick", "kick_drift", "scan", "scatter", "sort", "gather", "cellid", "green", "pp_order", "prep",
-        "sort_big", "vjp_gather", "vjp_source", "pp_vjp", "adj_kdk"};
+        "sort_big", "vjp_gather", "vjp_source", "pp_vjp", "adj_kdk", "pm3_map", "pm3_deposit", "pm3_fft",
+        "pm3_gather"};
     return (cls >= 0 && cls < CUBE2_PROFILE_CLASSES) ? names[cls] : "";
 }
 
@@ -833,6 +932,36 @@ int cube2_pp_stats(cube2_ctx *ctx, int64_t out[2]) {
     out[0] = (int64_t)h[0];
     out[1] = (int64_t)h[1];
     return CUBE2_OK;
+}
+
+int cube2_pm3_info(cube2_ctx *ctx, double out[8]) {
+    if (!ctx || !out) return CUBE2_ERR_BAD_ARG;
+    const PM3 &M = ctx->pm3;
+    if (!M.on) return set_error(ctx, CUBE2_ERR_STATE, "the adaptive third level is off");
+    const double v[8] = {(double)M.T, (double)M.ns, (double)M.r, (double)M.B, (double)M.m, M.H, M.b3,
+                         (double)M.max_tiles};
+    for (int i = 0; i < 8; ++i) out[i] = v[i];
+    return CUBE2_OK;
+}
+
+int cube2_pm3_stats(cube2_ctx *ctx, int64_t out[2]) {
+    if (!ctx || !out) return CUBE2_ERR_BAD_ARG;
+    if (!ctx->pm3.on) return set_error(ctx, CUBE2_ERR_STATE, "the adaptive third level is off");
+    int h[2] = {0, 0};
+    cudaError_t e = cudaMemcpyAsync(h, ctx->pm3.count, sizeof h, cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return cuda_error(ctx, e, "pm3 stats");
+    out[0] = h[0];
+    out[1] = h[1];
+    return CUBE2_OK;
+}
+
+int cube2_pm3_map(cube2_ctx *ctx, int32_t *out) {
+    if (!ctx || !out) return CUBE2_ERR_BAD_ARG;
+    if (!ctx->pm3.on) return set_error(ctx, CUBE2_ERR_STATE, "the adaptive third level is off");
+    const cudaError_t e = cudaMemcpyAsync(out, ctx->pm3.slot, (size_t)ctx->pm3.n_sub * 4, cudaMemcpyDeviceToDevice,
+                                          ctx->stream);
+    return e == cudaSuccess ? CUBE2_OK : cuda_error(ctx, e, "pm3 map");
 }
 
 const char *cube2_last_error(cube2_ctx *ctx) { return ctx ? ctx->err.c_str() : g_init_error.c_str(); }

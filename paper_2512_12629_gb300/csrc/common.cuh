@@ -30,6 +30,8 @@ enum ProfClass : int {
     P_INTERP, P_PP, P_KICK, P_KICK_DRIFT, P_SCAN, P_SCATTER, P_SORT, P_GATHER, P_CELLID, P_GREEN,
     P_PP_ORDER, P_PREP, P_SORT_BIG,
     P_VJP_GATHER, P_VJP_SOURCE, P_PP_VJP, P_ADJ_KDK,   // adjoint: PM gathers, cotangent source, PP product, reverse KDK
+    P_PM3_MAP, P_PM3_DEPOSIT, P_PM3_FFT, P_PM3_GATHER, // adaptive third level: refinement map, local deposit,
+                                                       // batched local solves, gather
     P_NCLASS
 };
 
@@ -50,6 +52,34 @@ struct Level {
     uint64_t mean_int = 0;   // M = floor(N 2^48 / n^3)
     float dens_scale = 0;    // RN32(n^3/N 2^-48)
     bool has_green = false, has_density = false, has_potential = false;
+    // batched meshes (the adaptive third level): real/spec hold `batch` meshes
+    // back to back; FFT blocks of mesh index >= *active (device) return at once
+    int batch = 1;
+    const int *active = nullptr;
+};
+
+// Adaptive third PM level (Sec. 2.1.1 Eq. PM3, Sec. 2.2.3): local periodic
+// meshes over the subtiles whose densest IOS cell is dense enough.
+struct PM3 {
+    bool on = false;
+    int T = 0;               // subtile edge [IOS cells]
+    int ns = 0;              // subtiles per dimension (n_ios / T)
+    int64_t n_sub = 0;       // ns^3
+    int r = 0;               // refinement: H_3 = H_finest / r
+    int B = 0;               // buffer [local cells] on each side of the subtile
+    int m = 0;               // local mesh cells per dimension
+    int q_shift = 0;         // local cell = 2^(16 - q_shift) fixed-point units
+    int rho_min = 0;         // refine when max count over the subtile's IOS cells >= rho_min
+    int max_tiles = 0;       // capacity of local meshes per force evaluation
+    double H = 0;            // local cell [Mpc/h]
+    double b3 = 0;           // softening b_3 = beta_3 H_3 [Mpc/h]; PP range of refined subtiles
+    float dens_scale = 0;    // RN32(V_p / H_3^3 2^-48)
+    Level lev;               // batched meshes: real/spec [max_tiles] meshes, Green's table, twiddles
+    unsigned long long *acc = nullptr;   // [max_tiles][m^3] exact CIC accumulators (kept zero between uses)
+    int32_t *rho_max = nullptr;          // [n_sub] densest IOS cell per subtile
+    int32_t *slot = nullptr;             // [n_sub] local mesh of each subtile, -1 = not refined
+    int32_t *list = nullptr;             // [max_tiles] subtile of each local mesh
+    int *count = nullptr;                // [2] meshes in use, subtiles asking for refinement
 };
 
 }  // namespace cube2
@@ -100,6 +130,7 @@ struct cube2_ctx {
     float *vjp_t = nullptr;        // [3][N] a force product
     float *vjp_u = nullptr;        // [12][N] reverse-step scratch
     double *vjp_sq = nullptr;      // [1] loss accumulator
+    cube2::PM3 pm3;                // adaptive third level (cfg.pm3_tile > 0)
 };
 
 namespace cube2 {
@@ -149,6 +180,9 @@ cudaError_t launch_fft_inverse(cube2_ctx *ctx, Level &L);          // spec -> re
 cudaError_t launch_cellid(cube2_ctx *ctx, const cube2_particles *p);
 cudaError_t launch_interp(cube2_ctx *ctx, int level, const cube2_particles *p, int accumulate);
 cudaError_t launch_pp(cube2_ctx *ctx, const cube2_particles *p, int accumulate, float kick);
+cudaError_t launch_fft_batched_solve(cube2_ctx *ctx, Level &L);     // forward, z * G * z^-1, inverse
+cudaError_t launch_pm3(cube2_ctx *ctx, const cube2_particles *p);    // map, local deposit + solve, gather (acc +=)
+cudaError_t launch_pm3_map(cube2_ctx *ctx, const cube2_particles *p);  // refinement map only
 cudaError_t launch_kick(cube2_ctx *ctx, const cube2_particles *p, float kick);
 cudaError_t launch_kick_drift(cube2_ctx *ctx, const cube2_particles *p, float kick, float drift_fix);
 cudaError_t launch_scan(cube2_ctx *ctx, const int32_t *in, int32_t *out, int64_t n);

@@ -182,10 +182,12 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 // ---------------------------------------------------------------- X passes
 template <int N>
 __global__ void __launch_bounds__(Tile<N>::T) fft_x_r2c(const float *__restrict__ in, float2 *__restrict__ out,
-                                                       int64_t nrows, int kxp, const float2 *__restrict__ tw) {
+                                                       int64_t nrows, int kxp, const float2 *__restrict__ tw,
+                                                       const int *__restrict__ active) {
     constexpr int L = Tile<N>::L, LP = Tile<N>::LP, T = Tile<N>::T;
     extern __shared__ float2 S[];
     const int64_t row0 = (int64_t)blockIdx.x * 2 * L;
+    if (active && row0 / ((int64_t)N * N) >= *active) return;   // batched meshes not in use
     for (int i = threadIdx.x; i < 2 * L * N; i += T) {
         const int r = i / N, x = i % N;
         const int64_t row = row0 + r;
@@ -209,10 +211,12 @@ __global__ void __launch_bounds__(Tile<N>::T) fft_x_r2c(const float *__restrict_
 
 template <int N>
 __global__ void __launch_bounds__(Tile<N>::T) fft_x_c2r(const float2 *__restrict__ in, float *__restrict__ out,
-                                                       int64_t nrows, int kxp, const float2 *__restrict__ tw) {
+                                                       int64_t nrows, int kxp, const float2 *__restrict__ tw,
+                                                       const int *__restrict__ active) {
     constexpr int L = Tile<N>::L, LP = Tile<N>::LP, T = Tile<N>::T;
     extern __shared__ float2 S[];
     const int64_t row0 = (int64_t)blockIdx.x * 2 * L;
+    if (active && row0 / ((int64_t)N * N) >= *active) return;
     constexpr int NH = N / 2 + 1;
     for (int i = threadIdx.x; i < L * NH; i += T) {
         const int l = i / NH, k = i % NH;
@@ -234,12 +238,14 @@ __global__ void __launch_bounds__(Tile<N>::T) fft_x_c2r(const float2 *__restrict
 
 // ---------------------------------------------------------------- Y passes
 template <int N, bool INV>
-__global__ void __launch_bounds__(Tile<N>::T) fft_y(float2 *__restrict__ data, int kxp, const float2 *__restrict__ tw) {
+__global__ void __launch_bounds__(Tile<N>::T) fft_y(float2 *__restrict__ data, int kxp, const float2 *__restrict__ tw,
+                                                   const int *__restrict__ active) {
     constexpr int L = Tile<N>::L, LP = Tile<N>::LPY, T = Tile<N>::T;
     extern __shared__ __align__(16) float2 S[];
     const int tiles_x = kxp / L;
     const int tx = blockIdx.x % tiles_x;
-    const int64_t z = blockIdx.x / tiles_x;
+    const int64_t z = blockIdx.x / tiles_x;             // plane over all batched meshes
+    if (active && z / N >= *active) return;
     float2 *base = data + z * N * kxp + tx * L;
     for (int i = threadIdx.x; i < N * L / 2; i += T) {
         const int y = i / (L / 2), l2 = 2 * (i % (L / 2));
@@ -259,14 +265,17 @@ __global__ void __launch_bounds__(Tile<N>::T) fft_y(float2 *__restrict__ data, i
 // from the symmetry-reduced table (green_index).
 template <int N, int GMODE>
 __global__ void __launch_bounds__(Tile<N>::T, Tile<N>::ZMINB) fft_z(float2 *__restrict__ data, const float *__restrict__ green,
-                                                   int kxp, const float2 *__restrict__ tw) {
+                                                   int kxp, const float2 *__restrict__ tw, const int *__restrict__ active) {
     constexpr int L = Tile<N>::L, LP = Tile<N>::LPY, T = Tile<N>::T;
     extern __shared__ __align__(16) float2 S[];
     const int tiles_x = kxp / L;
     const int tx = blockIdx.x % tiles_x;
-    const int64_t ky = blockIdx.x / tiles_x;
+    const int64_t row = blockIdx.x / tiles_x;             // (mesh, ky) over all batched meshes
+    const int64_t mesh = row / N;
+    const int64_t ky = row - mesh * N;
+    if (active && mesh >= *active) return;
     const int64_t zstride = (int64_t)N * kxp;
-    float2 *base = data + ky * kxp + tx * L;
+    float2 *base = data + mesh * N * zstride + ky * kxp + tx * L;
     for (int i = threadIdx.x; i < N * L / 2; i += T) {
         const int z = i / (L / 2), l2 = 2 * (i % (L / 2));
         cp_async16(&S[z * LP + l2], &base[z * zstride + l2]);
@@ -306,43 +315,47 @@ template <int N>
 struct Launcher {
     static cudaError_t forward(cube2_ctx *ctx, Level &Lv) {
         setup();
-        const int64_t nrows = (int64_t)N * N;
+        const int64_t nrows = (int64_t)Lv.batch * N * N;
         const unsigned bx = (unsigned)((nrows + 2 * Tile<N>::L - 1) / (2 * Tile<N>::L));
+        const int cls = Lv.active ? -1 : 0;   // batched meshes are profiled as one group by the caller
         {
-            ProfScope prof(ctx, P_FFT_X_FWD, Lv.index);
-            fft_x_r2c<N><<<bx, Tile<N>::T, Tile<N>::SMEM, ctx->stream>>>(Lv.real, Lv.spec, nrows, Lv.kxp, Lv.tw);
+            ProfScope prof(ctx, cls < 0 ? -1 : P_FFT_X_FWD, Lv.index);
+            fft_x_r2c<N><<<bx, Tile<N>::T, Tile<N>::SMEM, ctx->stream>>>(Lv.real, Lv.spec, nrows, Lv.kxp, Lv.tw,
+                                                                         Lv.active);
         }
-        const unsigned by = (unsigned)((int64_t)N * (Lv.kxp / Tile<N>::L));
+        const unsigned by = (unsigned)((int64_t)Lv.batch * N * (Lv.kxp / Tile<N>::L));
         {
-            ProfScope prof(ctx, P_FFT_Y_FWD, Lv.index);
-            fft_y<N, false><<<by, Tile<N>::T, Tile<N>::SMEMY, ctx->stream>>>(Lv.spec, Lv.kxp, Lv.tw);
+            ProfScope prof(ctx, cls < 0 ? -1 : P_FFT_Y_FWD, Lv.index);
+            fft_y<N, false><<<by, Tile<N>::T, Tile<N>::SMEMY, ctx->stream>>>(Lv.spec, Lv.kxp, Lv.tw, Lv.active);
         }
         ctx->launches += 2;
         return cudaGetLastError();
     }
     static cudaError_t z_pass(cube2_ctx *ctx, Level &Lv, bool green) {
         setup();
-        const unsigned bz = (unsigned)((int64_t)N * (Lv.kxp / Tile<N>::L));
-        ProfScope prof(ctx, P_FFT_Z_GREEN, Lv.index);
+        const unsigned bz = (unsigned)((int64_t)Lv.batch * N * (Lv.kxp / Tile<N>::L));
+        ProfScope prof(ctx, Lv.active ? -1 : P_FFT_Z_GREEN, Lv.index);
         if (green)
-            fft_z<N, 2><<<bz, Tile<N>::T, Tile<N>::SMEMY, ctx->stream>>>(Lv.spec, Lv.green, Lv.kxp, Lv.tw);
+            fft_z<N, 2><<<bz, Tile<N>::T, Tile<N>::SMEMY, ctx->stream>>>(Lv.spec, Lv.green, Lv.kxp, Lv.tw, Lv.active);
         else
-            fft_z<N, 0><<<bz, Tile<N>::T, Tile<N>::SMEMY, ctx->stream>>>(Lv.spec, nullptr, Lv.kxp, Lv.tw);
+            fft_z<N, 0><<<bz, Tile<N>::T, Tile<N>::SMEMY, ctx->stream>>>(Lv.spec, nullptr, Lv.kxp, Lv.tw, Lv.active);
         ctx->launches += 1;
         return cudaGetLastError();
     }
     static cudaError_t inverse(cube2_ctx *ctx, Level &Lv) {
         setup();
-        const unsigned by = (unsigned)((int64_t)N * (Lv.kxp / Tile<N>::L));
+        const unsigned by = (unsigned)((int64_t)Lv.batch * N * (Lv.kxp / Tile<N>::L));
+        const int cls = Lv.active ? -1 : 0;
         {
-            ProfScope prof(ctx, P_FFT_Y_INV, Lv.index);
-            fft_y<N, true><<<by, Tile<N>::T, Tile<N>::SMEMY, ctx->stream>>>(Lv.spec, Lv.kxp, Lv.tw);
+            ProfScope prof(ctx, cls < 0 ? -1 : P_FFT_Y_INV, Lv.index);
+            fft_y<N, true><<<by, Tile<N>::T, Tile<N>::SMEMY, ctx->stream>>>(Lv.spec, Lv.kxp, Lv.tw, Lv.active);
         }
-        const int64_t nrows = (int64_t)N * N;
+        const int64_t nrows = (int64_t)Lv.batch * N * N;
         const unsigned bx = (unsigned)((nrows + 2 * Tile<N>::L - 1) / (2 * Tile<N>::L));
         {
-            ProfScope prof(ctx, P_FFT_X_INV, Lv.index);
-            fft_x_c2r<N><<<bx, Tile<N>::T, Tile<N>::SMEM, ctx->stream>>>(Lv.spec, Lv.real, nrows, Lv.kxp, Lv.tw);
+            ProfScope prof(ctx, cls < 0 ? -1 : P_FFT_X_INV, Lv.index);
+            fft_x_c2r<N><<<bx, Tile<N>::T, Tile<N>::SMEM, ctx->stream>>>(Lv.spec, Lv.real, nrows, Lv.kxp, Lv.tw,
+                                                                         Lv.active);
         }
         ctx->launches += 2;
         return cudaGetLastError();
@@ -413,6 +426,13 @@ cudaError_t launch_fft_z_green(cube2_ctx *ctx, Level &L) { return dispatch(ctx, 
 cudaError_t launch_fft_z_forward(cube2_ctx *ctx, Level &L) { return dispatch(ctx, L, Op::ZForward); }
 cudaError_t launch_fft_inverse(cube2_ctx *ctx, Level &L) { return dispatch(ctx, L, Op::Inverse); }
 
+cudaError_t launch_fft_batched_solve(cube2_ctx *ctx, Level &L) {
+    cudaError_t e = dispatch(ctx, L, Op::Forward);
+    if (e == cudaSuccess) e = dispatch(ctx, L, Op::ZGreen);
+    if (e == cudaSuccess) e = dispatch(ctx, L, Op::Inverse);
+    return e;
+}
+
 }  // namespace cube2
 
 // ---------------------------------------------------------------------------
@@ -461,11 +481,11 @@ cudaError_t noalloc_passes(const float *rho, float2 *spec, const float *gpad, fl
     const int64_t nrows = (int64_t)N * N;
     const unsigned bx = (unsigned)((nrows + 2 * L - 1) / (2 * L));
     const unsigned by = (unsigned)((int64_t)N * (kxp / L));
-    fft_x_r2c<N><<<bx, Tile<N>::T, Tile<N>::SMEM, st>>>(rho, spec, nrows, kxp, tw);
-    fft_y<N, false><<<by, Tile<N>::T, Tile<N>::SMEMY, st>>>(spec, kxp, tw);
-    fft_z<N, 1><<<by, Tile<N>::T, Tile<N>::SMEMY, st>>>(spec, gpad, kxp, tw);
-    fft_y<N, true><<<by, Tile<N>::T, Tile<N>::SMEMY, st>>>(spec, kxp, tw);
-    fft_x_c2r<N><<<bx, Tile<N>::T, Tile<N>::SMEM, st>>>(spec, phi, nrows, kxp, tw);
+    fft_x_r2c<N><<<bx, Tile<N>::T, Tile<N>::SMEM, st>>>(rho, spec, nrows, kxp, tw, nullptr);
+    fft_y<N, false><<<by, Tile<N>::T, Tile<N>::SMEMY, st>>>(spec, kxp, tw, nullptr);
+    fft_z<N, 1><<<by, Tile<N>::T, Tile<N>::SMEMY, st>>>(spec, gpad, kxp, tw, nullptr);
+    fft_y<N, true><<<by, Tile<N>::T, Tile<N>::SMEMY, st>>>(spec, kxp, tw, nullptr);
+    fft_x_c2r<N><<<bx, Tile<N>::T, Tile<N>::SMEM, st>>>(spec, phi, nrows, kxp, tw, nullptr);
     return cudaGetLastError();
 }
 

@@ -46,6 +46,11 @@ struct PPParams {
     float coef;                       // V_p / (4 pi s_ios^2)
     float kick;                       // 0: no kick; else v += kick * acc after the sum
     int *status;
+    // adaptive third level: targets in a refined subtile (pm3_slot >= 0) use
+    // the range b_3 (bcut2_3, inv_bcut_3) instead of b_cut; null when off
+    const int32_t *pm3_slot;
+    int pm3_T, pm3_ns;
+    float bcut2_3, inv_bcut_3;
 };
 
 // R(r, b) of Eq. (refforce) times b^2, as a function of u = r / b < 1.
@@ -366,7 +371,7 @@ __device__ int build_segments(const PPParams &P, WarpSegs &W, int c0, int xa, in
 }
 
 __device__ void union_path(const PPParams &P, const WarpSegs &W, float4 *S, int64_t i, bool has, int c0, int xa,
-                           float4 me, Sum3 &a, unsigned &pairs, unsigned &cands) {
+                           float4 me, float bcut2, float ibc, Sum3 &a, unsigned &pairs, unsigned &cands) {
     const int lane = threadIdx.x & 31;
     const int n = P.n_ios;
     const int total = W.cum[PP_SEGS];
@@ -374,7 +379,7 @@ __device__ void union_path(const PPParams &P, const WarpSegs &W, float4 *S, int6
     const int pself = has ? W.cum[8] + (int)(i - W.beg[8]) : -1000;
     const int cx = (has ? __float_as_int(me.w) : c0) % n;
     const float mx = (float)(cx - xa) + me.x, my = me.y + 1.0f, mz = me.z + 1.0f;
-    const float bcut2 = P.bcut2, bpp2 = P.bpp2, ibc = P.inv_bcut, ibp = P.inv_bpp;
+    const float bpp2 = P.bpp2, ibp = P.inv_bpp;
     int sa = 0, sb = 0;
     for (int b0 = 0; b0 < total; b0 += 64) {
         S[lane] = stage_source(P, W, b0 + lane, sa);
@@ -439,12 +444,12 @@ __device__ void union_path(const PPParams &P, const WarpSegs &W, float4 *S, int6
 // Warps whose targets span several rows or a wide x range (sparse regions):
 // each lane walks its own 27 cells as 9 row ranges and evaluates the pairs in
 // range as it meets them.  Plain nested loops keep the loads pipelined.
-__device__ void lane_path(const PPParams &P, bool has, int c, float4 me, Sum3 &a,
+__device__ void lane_path(const PPParams &P, bool has, int c, float4 me, float bcut2, float ibc, Sum3 &a,
                                     unsigned &pairs, unsigned &cands) {
     if (!has) return;
     const int n = P.n_ios;
     const int cx = c % n, cy = (c / n) % n, cz = c / (n * n);
-    const float bcut2 = P.bcut2, bpp2 = P.bpp2, ibc = P.inv_bcut, ibp = P.inv_bpp;
+    const float bpp2 = P.bpp2, ibp = P.inv_bpp;
     for (int dz = -1; dz <= 1; ++dz)
         for (int dy = -1; dy <= 1; ++dy) {
             const int64_t r = ((int64_t)wrap(cz + dz, n) * n + wrap(cy + dy, n)) * n;
@@ -663,6 +668,7 @@ __global__ void __launch_bounds__(PP_CTA, PPV_MINB) pp_vjp_kernel(PPParams P, Vj
 #ifndef PP_MINB
 #define PP_MINB 16
 #endif
+template <bool PM3>
 __global__ void __launch_bounds__(PP_CTA, PP_MINB) pp_kernel(PPParams P) {
     __shared__ PPShared sh;
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -680,12 +686,22 @@ __global__ void __launch_bounds__(PP_CTA, PP_MINB) pp_kernel(PPParams P) {
     // warps inside one row, at most PP_WMAX + 1 cells wide, share a source stream
     const bool one_row = (c0 / n) == (c31 / n) && xb - xa <= PP_WMAX && xb - xa + 3 <= n;
     if (one_row) build_segments(P, sh.w[wib].u.seg, c0, xa, xb);
+    // PP range of this target: b_3 inside a refined subtile of the third level
+    float bcut2 = P.bcut2, ibc = P.inv_bcut;
+    if (PM3 && has) {
+        const int T = P.pm3_T;
+        const int s = ((c / (n * n)) / T * P.pm3_ns + ((c / n) % n) / T) * P.pm3_ns + (c % n) / T;
+        if (__ldg(&P.pm3_slot[s]) >= 0) {
+            bcut2 = P.bcut2_3;
+            ibc = P.inv_bcut_3;
+        }
+    }
     Sum3 a;
     unsigned pairs = 0, cands = 0;
     if (one_row)
-        union_path(P, sh.w[wib].u.seg, sh.w[wib].u.buf, i, has, c0, xa, me, a, pairs, cands);
+        union_path(P, sh.w[wib].u.seg, sh.w[wib].u.buf, i, has, c0, xa, me, bcut2, ibc, a, pairs, cands);
     else
-        lane_path(P, has, c, me, a, pairs, cands);
+        lane_path(P, has, c, me, bcut2, ibc, a, pairs, cands);
     if (has) finish(P, P.perm[i], a.x - a.cx, a.y - a.cy, a.z - a.cz);
     add_stats(P.stats, pairs, cands);
 }
@@ -730,6 +746,13 @@ static PPParams pp_params(cube2_ctx *ctx, const cube2_particles *p, int accumula
     P.coef = (float)(vp / (4.0 * 3.14159265358979323846) / (s * s));
     P.kick = kick;
     P.status = ctx->dev_status;
+    if (ctx->pm3.on) {
+        P.pm3_slot = ctx->pm3.slot;
+        P.pm3_T = ctx->pm3.T;
+        P.pm3_ns = ctx->pm3.ns;
+        P.bcut2_3 = (float)((ctx->pm3.b3 / s) * (ctx->pm3.b3 / s));
+        P.inv_bcut_3 = (float)(s / ctx->pm3.b3);
+    }
     return P;
 }
 
@@ -752,7 +775,10 @@ cudaError_t launch_pp(cube2_ctx *ctx, const cube2_particles *p, int accumulate, 
     }
     {
         ProfScope prof(ctx, P_PP, 0);
-        pp_kernel<<<(unsigned)nblocks, PP_CTA, 0, ctx->stream>>>(P);
+        if (P.pm3_slot)
+            pp_kernel<true><<<(unsigned)nblocks, PP_CTA, 0, ctx->stream>>>(P);
+        else
+            pp_kernel<false><<<(unsigned)nblocks, PP_CTA, 0, ctx->stream>>>(P);
     }
     ctx->launches += 4;
     return cudaGetLastError();

@@ -28,7 +28,8 @@ ERR_UNSUPPORTED_SIZE = -6
 ERR_STATE = -7
 ERR_DISPLACEMENT = -8
 MAX_LEVELS = 2
-PROFILE_CLASSES = 23
+PROFILE_CLASSES = 27
+LEVEL_PM3 = 2
 
 
 class Cube2Error(RuntimeError):
@@ -51,6 +52,11 @@ class Config(ctypes.Structure):
         ("alias_max", ctypes.c_int32),
         ("assign_order", ctypes.c_int32),
         ("iso_length", ctypes.c_double),
+        ("pm3_tile", ctypes.c_int32),
+        ("pm3_refine", ctypes.c_int32),
+        ("pm3_beta", ctypes.c_double),
+        ("pm3_rho_min", ctypes.c_int32),
+        ("pm3_max_tiles", ctypes.c_int32),
     ]
 
 
@@ -96,6 +102,9 @@ def _load():
         "cube2_pp_stats": (I, [P, ctypes.POINTER(ctypes.c_int64)]),
         "cube2_solve_pm_noalloc": (I, [P, P, P, ctypes.c_int32, P]),
         "cube2_fma_probe": (I, [P, I, I, I, P]),
+        "cube2_pm3_info": (I, [P, ctypes.POINTER(D)]),
+        "cube2_pm3_stats": (I, [P, ctypes.POINTER(ctypes.c_int64)]),
+        "cube2_pm3_map": (I, [P, P]),
         "cube2_adjoint_init": (I, [P]),
         "cube2_force_vjp": (I, [P, ctypes.POINTER(Particles), P, P]),
         "cube2_kdk_permutation": (I, [P, P]),
@@ -140,6 +149,10 @@ def make_config(w, n_particles=None, alias_max=2) -> Config:
     c.alias_max = alias_max
     c.assign_order = getattr(w, "assign_order", 2)
     c.iso_length = getattr(w, "iso_length", 0.0)
+    pm3 = getattr(w, "pm3", None)
+    if pm3 is not None:
+        c.pm3_tile, c.pm3_refine, c.pm3_beta = pm3.tile, pm3.refine, pm3.beta
+        c.pm3_rho_min, c.pm3_max_tiles = pm3.rho_min, pm3.max_tiles
     return c
 
 
@@ -341,7 +354,7 @@ class Context:
         return self._grid(_lib.cube2_get_potential, level, (n, n, n), torch.float32, device)
 
     def get_green(self, level, device="cuda"):
-        n = self.cfg.n_mesh[level]
+        n = self.pm3_info()["m"] if level == LEVEL_PM3 else self.cfg.n_mesh[level]
         return self._grid(_lib.cube2_get_green, level, (n, n, n // 2 + 1), torch.float32, device)
 
     def debug_forward_fft(self, level, device="cuda"):
@@ -351,6 +364,26 @@ class Context:
 
     def check(self):
         self._chk(_lib.cube2_check(self.ptr))
+
+    def pm3_info(self):
+        """Geometry of the adaptive third level: dict(tile, ns, refine, B, m, H3, b3, max_tiles)."""
+        out = (ctypes.c_double * 8)()
+        self._chk(_lib.cube2_pm3_info(self.ptr, out))
+        keys = ("tile", "ns", "refine", "B", "m", "H3", "b3", "max_tiles")
+        return {k: (out[i] if k in ("H3", "b3") else int(out[i])) for i, k in enumerate(keys)}
+
+    def pm3_stats(self):
+        """(local meshes in use, subtiles that asked for refinement) of the last force/PP call."""
+        out = (ctypes.c_int64 * 2)()
+        self._chk(_lib.cube2_pm3_stats(self.ptr, out))
+        return int(out[0]), int(out[1])
+
+    def pm3_map(self):
+        """Local mesh index of every subtile (device int32, -1 = unrefined) of the last force/PP call."""
+        ns = self.pm3_info()["ns"]
+        out = torch.empty(ns ** 3, dtype=torch.int32, device="cuda")
+        self._chk(_lib.cube2_pm3_map(self.ptr, out.data_ptr()))
+        return out
 
     def launch_count(self):
         return int(_lib.cube2_launch_count(self.ptr))

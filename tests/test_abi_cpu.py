@@ -96,3 +96,23 @@ def test_kdk_factors_match_oracle(binding):
         assert k1 == pytest.approx(okdk.kick_integral(a[i], ah, 0.3, 0.7), rel=1e-13)
         assert dr == pytest.approx(okdk.drift_integral(a[i], a[i + 1], 0.3, 0.7), rel=1e-13)
         assert k2 == pytest.approx(okdk.kick_integral(ah, a[i + 1], 0.3, 0.7), rel=1e-13)
+
+
+def test_third_level_config_is_validated_on_host(binding):
+    from inputs import C2_SMALL
+    from inputs.workloads import Level, PM3Spec, Workload
+    lib = binding.library()
+    small = Workload(name="pm3-8c-8x32mesh", n_p=10, box=32.0, n_ios=8, levels=(Level(8, 3.5), Level(32, 3.5)),
+                     b_pp=0.3)
+    # refinement not a power of two, tile not dividing n_ios, b_3 beyond the PP range, no capacity
+    for field, value in (("pm3_refine", 3), ("pm3_tile", 3), ("pm3_beta", 28.0), ("pm3_max_tiles", 0)):
+        cfg = binding.make_config(small.with_(pm3=PM3Spec(2, 2, 3.5, 2, 8)), n_particles=1000)
+        setattr(cfg, field, value)
+        ptr = ctypes.c_void_p()
+        assert lib.cube2_init_mesh(ctypes.byref(ptr), ctypes.byref(cfg), None) == -1, field
+    # a local mesh the FFT passes do not take: 16^3 IOS-cell subtiles need 64 + 2 x 8 cells -> 81 = 3^4
+    cfg = binding.make_config(C2_SMALL.with_(pm3=PM3Spec(16, 2, 2.0, 2, 8)))
+    assert lib.cube2_init_mesh(ctypes.byref(ctypes.c_void_p()), ctypes.byref(cfg), None) == -6
+    # TSC with the third level
+    cfg = binding.make_config(small.with_(pm3=PM3Spec(2, 2, 3.5, 2, 8), assign_order=3), n_particles=1000)
+    assert lib.cube2_init_mesh(ctypes.byref(ctypes.c_void_p()), ctypes.byref(cfg), None) == -1
