@@ -109,6 +109,12 @@ typedef struct {
     double  pm3_beta;
     int32_t pm3_rho_min;
     int32_t pm3_max_tiles;
+    /* 1: the particle sets this context steps store their velocities as FP16
+     * with a per-IOS-cell FP32 scale (cube2_particles.vel16 / vscale, the
+     * compressed velocity storage of Sec. 2.3); the context then holds one
+     * FP32 working copy of them (12 bytes per particle) for the step.  0: FP32
+     * velocities (cube2_particles.vel).                                       */
+    int32_t vel_fp16;
 } cube2_config;
 
 /* Level index of the adaptive third level in cube2_set_green / cube2_get_green. */
@@ -122,6 +128,14 @@ typedef struct {
     int32_t  *start;      /* [n_ios^3] exclusive prefix sum of count               */
     float    *vel[3];     /* [3][n] canonical momenta (FP32)                       */
     float    *acc[3];     /* [3][n] force F = -grad u (FP32, output of force calls) */
+    /* FP16 velocity storage (contexts with cfg.vel_fp16 = 1; NULL otherwise,
+     * and vel is then unused): the momentum of particle p is
+     * v_d = half(vel16[d][p]) * vscale[c], c its IOS cell, with
+     * vscale[c] = max over the cell's particles and d of |v_d| (FP32) and
+     * vel16 = RN_half(RN32(v_d / vscale[c])) (0 where vscale[c] = 0).
+     * vel16: [3][n] IEEE binary16 bit patterns; vscale: [n_ios^3] FP32.     */
+    uint16_t *vel16[3];
+    float    *vscale;
 } cube2_particles;
 
 /* Validate cfg, allocate the context and all device buffers, and build the
@@ -283,6 +297,18 @@ int cube2_solve_pm_noalloc(const float *rho, const float *green, float *phi, int
  * float, never written in practice (it keeps the chains from being removed).
  * Returns CUBE2_ERR_BAD_ARG for bad sizes, CUBE2_ERR_CUDA if the launch fails. */
 int cube2_fma_probe(float *out, int blocks, int threads, int iters, void *stream);
+
+/* FP16 velocity codec (contexts with cfg.vel_fp16 = 1).  cube2_vel_encode:
+ * p->vel16 and p->vscale from FP32 momenta v[3] (device [N] each, in p's
+ * particle order; counts and starts of p give the cells).
+ * cube2_vel_decode: v[3] (device FP32 [N] each) = half(vel16) * vscale.
+ * In a step the kick decodes, the re-bin gathers FP32 momenta into the
+ * context's working copy, the second kick updates it and the step ends by
+ * encoding it into p->vel16 / p->vscale.  cube2_kdk_step_host,
+ * cube2_ios_from_positions and the adjoint take FP32 velocities only
+ * (CUBE2_ERR_BAD_ARG / CUBE2_ERR_STATE for a vel_fp16 context). */
+int cube2_vel_encode(cube2_ctx *ctx, const cube2_particles *p, const float *const v[3]);
+int cube2_vel_decode(cube2_ctx *ctx, const cube2_particles *p, float *const v[3]);
 
 /* Host helper: out = {K(a0,ah), Dr(a0,a1), K(ah,a1)} for cfg's cosmology. */
 int cube2_kdk_factors(const cube2_config *cfg, double a0, double a1, double out[3]);

@@ -58,6 +58,7 @@ class Workload:
     assign_order: int = 2        # mass assignment: 2 = CIC (the workload's), 3 = TSC (the paper's)
     iso_length: float = 0.0      # > 0: isolated boundary conditions, force truncated at this r [Mpc/h]
     pm3: PM3Spec | None = None   # adaptive third PM level (None: the global levels only)
+    vel_fp16: bool = False       # velocities stored as FP16 with a per-IOS-cell FP32 scale
 
     @property
     def n_particles(self) -> int:

@@ -11,8 +11,9 @@ as tie-break).  The Gaussian field comes from ``torch.randn`` with a seeded
 drawn here is a different realisation from the host generator's, and both the
 CUDA path and the oracle's sampled checks read the IOS arrays returned here.
 The transforms run through torch (cuFFT) in FP32; the displacement is rounded
-to the IOS grid in FP64.  Velocities are not produced (single force
-evaluations do not read them).
+to the IOS grid in FP64.  With ``momenta=True`` the canonical momenta
+p = a^2 E f D psi (the host recipe's, at the displacement's scale factor) are
+returned as well, in FP32 and in the IOS order.
 """
 from __future__ import annotations
 
@@ -20,7 +21,7 @@ import math
 
 import torch
 
-from .zeldovich import FIX, growth_d, spectrum_amplitude
+from .zeldovich import FIX, growth_d, growth_f, hubble_e, spectrum_amplitude
 
 
 def _fftfreq_k(n, kf, device):
@@ -28,10 +29,10 @@ def _fftfreq_k(n, kf, device):
     return f * kf
 
 
-def zeldovich_ios_torch(w, device="cuda"):
+def zeldovich_ios_torch(w, device="cuda", momenta=False):
     """IOS arrays for workload ``w`` (n_ios must equal n_p): dict(off=(3,N)
-    int16 storage of the uint16 offsets, count, start=(n_ios^3,) int32), all
-    on ``device``."""
+    int16 storage of the uint16 offsets, count, start=(n_ios^3,) int32, and
+    with ``momenta`` vel=(3,N) float32), all on ``device``."""
     n, box = w.n_p, w.box
     if w.n_ios != n:
         raise ValueError("the device generator places one particle per IOS cell before displacement")
@@ -62,12 +63,16 @@ def zeldovich_ios_torch(w, device="cuda"):
     del k2
     s_ios = box / w.n_ios
     cell = None
-    offs = []
+    offs, moms = [], []
+    mom_fac = a_disp ** 2 * float(hubble_e(a_disp, w.omega_m, w.omega_l)) * growth_f(a_disp, w.omega_m, w.omega_l) \
+        * d_growth
     idx = torch.arange(n, device=device, dtype=torch.int64)
     for d, kd in enumerate((kx, ky, kz)):
         psi = torch.fft.irfftn(1j * kd * inv_k2 * dk, s=(n, n, n))
         # X = (i_d + 1/2 + D psi / s) 2^16 on the lattice point of axis d, wrapped
         disp = torch.round(psi.double() * (d_growth / s_ios * FIX)).to(torch.int64)
+        if momenta:
+            moms.append((psi * mom_fac).view(-1))
         del psi
         lattice = (idx.view(1, 1, n) if d == 0 else (idx.view(1, n, 1) if d == 1 else idx.view(n, 1, 1)))
         fixed = torch.remainder(lattice * FIX + FIX // 2 + disp, n * FIX).view(-1)
@@ -80,8 +85,12 @@ def zeldovich_ios_torch(w, device="cuda"):
     order = torch.sort(cell, stable=True).indices
     cell_sorted = cell[order]
     off = torch.stack([o[order] for o in offs])
-    del offs, order
+    vel = torch.stack([m[order] for m in moms]) if momenta else None
+    del offs, moms, order
     count = torch.bincount(cell_sorted, minlength=w.n_ios ** 3).to(torch.int32)
     del cell, cell_sorted
     start = (torch.cumsum(count, 0, dtype=torch.int64) - count).to(torch.int32)
-    return dict(off=off, count=count, start=start)
+    out = dict(off=off, count=count, start=start)
+    if momenta:
+        out["vel"] = vel
+    return out

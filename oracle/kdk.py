@@ -98,3 +98,36 @@ def kdk_step(state, w, a0, a1, greens=None):
     acc = total_force(off, count, start, w, greens)
     vel = vel + 1.5 * om * kick_integral(ah, a1, om, ol) * acc
     return dict(off=off, count=count, start=start, vel=vel, acc=acc)
+
+
+# ------------------------------------------------- compressed velocities
+# Sec. 2.3 stores velocities compactly next to the IOS positions (the paper
+# points to its predecessor for the formula, which is not in the text).  The
+# reading used here, the large workload's: each velocity component as an IEEE
+# binary16 code times an FP32 scale per IOS cell, the largest |v_d| of the
+# cell's particles, so that every code lies in [-1, 1].
+def velocity_scales(vel, count):
+    """FP32 per-cell scale: max over the cell's particles and components of |v_d|."""
+    v = np.abs(np.asarray(vel, dtype=np.float32)).max(axis=0)
+    cell = np.repeat(np.arange(count.size, dtype=np.int64), count.astype(np.int64))
+    scale = np.zeros(count.size, dtype=np.float32)
+    np.maximum.at(scale, cell, v)
+    return scale
+
+
+def encode_velocities(vel, count):
+    """(codes float16 (3, N), scale float32 (n_cells,)): code = RN_half(RN32(v / scale)),
+    0 in cells whose scale is 0."""
+    v = np.asarray(vel, dtype=np.float32)
+    scale = velocity_scales(v, count)
+    cell = np.repeat(np.arange(count.size, dtype=np.int64), count.astype(np.int64))
+    s = scale[cell]
+    safe = np.where(s > 0, s, np.float32(1.0))
+    codes = np.where(s > 0, v / safe, np.float32(0.0)).astype(np.float16)
+    return codes, scale
+
+
+def decode_velocities(codes, scale, count):
+    """FP32 velocities RN32(float(code) * scale) of each particle's cell."""
+    cell = np.repeat(np.arange(count.size, dtype=np.int64), count.astype(np.int64))
+    return np.asarray(codes, dtype=np.float16).astype(np.float32) * scale[cell]

@@ -134,4 +134,46 @@ def pp_force_at(off, count, start, n_ios, box, b_pp, b_cut, targets, n_particles
     return out
 
 
-__all__ = ["pp_force", "pp_force_at", "pp_force_brute", "cell_coords"]
+def pp_force_at_many(off, count, start, n_ios, box, b_pp, b_cut, targets, n_particles=None):
+    """``pp_force_at`` for many targets at once, (3, K): for each of the 27
+    cell offsets, every (target, source) pair of the target's neighbour cell
+    is formed in one array and the pair terms are summed per target."""
+    n_part = int(count.sum()) if n_particles is None else n_particles
+    s_ios = box / n_ios
+    vp = box ** 3 / n_part
+    targets = np.asarray(targets, dtype=np.int64)
+    starts = start.astype(np.int64)
+    cnt = count.astype(np.int64)
+    c = np.searchsorted(starts + cnt, targets, side="right")
+    cc = np.stack([c % n_ios, (c // n_ios) % n_ios, c // (n_ios * n_ios)])
+    oi = off[:, targets].astype(np.int64)
+    out = np.zeros((3, len(targets)))
+    k_all = np.arange(len(targets), dtype=np.int64)
+    for oz in (-1, 0, 1):
+        for oy in (-1, 0, 1):
+            for ox in (-1, 0, 1):
+                nb = ((((cc[2] + oz) % n_ios) * n_ios + (cc[1] + oy) % n_ios) * n_ios + (cc[0] + ox) % n_ios)
+                m = cnt[nb]
+                tot = int(m.sum())
+                if tot == 0:
+                    continue
+                k = np.repeat(k_all, m)
+                first = np.repeat(np.cumsum(m) - m, m)
+                j = np.repeat(starts[nb], m) + (np.arange(tot, dtype=np.int64) - first)
+                keep = j != targets[k]
+                k, j = k[keep], j[keep]
+                d = np.empty((3, j.size))
+                for ax, o in enumerate((ox, oy, oz)):
+                    d[ax] = (o * FIX + off[ax, j].astype(np.int64) - oi[ax, k]) * (s_ios / FIX)
+                r = np.sqrt((d * d).sum(axis=0))
+                sel = (r > 0) & (r < b_cut)
+                if not sel.any():
+                    continue
+                k, d, r = k[sel], d[:, sel], r[sel]
+                mag = vp * pp_reference(r, b_pp, b_cut) / (4.0 * math.pi * r)
+                for ax in range(3):
+                    out[ax] += np.bincount(k, weights=mag * d[ax], minlength=len(targets))
+    return out
+
+
+__all__ = ["pp_force", "pp_force_at", "pp_force_at_many", "pp_force_brute", "cell_coords"]

@@ -145,6 +145,7 @@ void free_ctx(cube2_ctx *c) {
     cudaFree(c->pm3.slot);
     cudaFree(c->pm3.list);
     cudaFree(c->pm3.count);
+    cudaFree(c->vel32);
     cudaFree(c->dev_status);
     cudaFreeHost(c->host_status);
     if (c->aux_event) cudaEventDestroy(c->aux_event);
@@ -158,9 +159,11 @@ bool particles_ok(cube2_ctx *ctx, const cube2_particles *p, bool need_vel, bool 
     if (ctx->N == 0) return p->count && p->start;
     for (int d = 0; d < 3; ++d) {
         if (!p->off[d]) return false;
-        if (need_vel && !p->vel[d]) return false;
+        // a vel_fp16 context steps FP16 velocities with their per-cell scale
+        if (need_vel && (ctx->vel32 ? !p->vel16[d] : !p->vel[d])) return false;
         if (need_acc && !p->acc[d]) return false;
     }
+    if (need_vel && ctx->vel32 && !p->vscale) return false;
     return p->count && p->start;
 }
 
@@ -328,6 +331,7 @@ int cube2_init_mesh(cube2_ctx **out, const cube2_config *cfg, void *stream) {
     alloc((void **)&c->pp_perm, N * 4);
     alloc((void **)&c->pp_stats, 2 * sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaMemsetAsync(c->pp_stats, 0, 2 * sizeof(unsigned long long), c->stream);
+    if (cfg->vel_fp16) alloc((void **)&c->vel32, N * 3 * 4);
     if (c->pm3.on) {
         PM3 &M = c->pm3;
         Level &L = M.lev;
@@ -563,7 +567,12 @@ static int kdk_step_core(cube2_ctx *ctx, cube2_particles *p, double a0, double a
     if (e == cudaSuccess) e = launch_rebin(ctx, p);
     if (e == cudaSuccess && after_rebin) e = cudaEventRecord(after_rebin, ctx->stream);
     if (e != cudaSuccess) return cuda_error(ctx, e, "kick/drift/rebin");
-    return force_core(ctx, p, (float)(c * f[2]));
+    const int r = force_core(ctx, p, (float)(c * f[2]));
+    if (r != CUBE2_OK || !ctx->vel32) return r;
+    // FP16 storage: encode the working momenta of the new order
+    const float *const w[3] = {ctx->vel32, ctx->vel32 + ctx->N, ctx->vel32 + 2 * ctx->N};
+    e = launch_vel_encode(ctx, p, w);
+    return e == cudaSuccess ? CUBE2_OK : cuda_error(ctx, e, "velocity encode");
 }
 
 int cube2_kdk_step(cube2_ctx *ctx, cube2_particles *p, double a0, double a1) {
@@ -573,6 +582,7 @@ int cube2_kdk_step(cube2_ctx *ctx, cube2_particles *p, double a0, double a1) {
 int cube2_ios_from_positions(cube2_ctx *ctx, const double *const pos[3], const float *const mom[3],
                              cube2_particles *p, int32_t *perm) {
     if (!ctx) return CUBE2_ERR_BAD_ARG;
+    if (ctx->vel32) return set_error(ctx, CUBE2_ERR_BAD_ARG, "placement writes FP32 velocities (vel_fp16 context)");
     if (!particles_ok(ctx, p, true, false)) return set_error(ctx, CUBE2_ERR_BAD_ARG, "bad particle arrays");
     if (ctx->N > 0 && (!pos || !pos[0] || !pos[1] || !pos[2]))
         return set_error(ctx, CUBE2_ERR_BAD_ARG, "null position arrays");
@@ -588,6 +598,7 @@ int cube2_ios_from_positions(cube2_ctx *ctx, const double *const pos[3], const f
 
 int cube2_adjoint_init(cube2_ctx *ctx) {
     if (!ctx) return CUBE2_ERR_BAD_ARG;
+    if (ctx->vel32) return set_error(ctx, CUBE2_ERR_STATE, "the adjoint takes FP32 velocities (vel_fp16 context)");
     if (ctx->pm3.on) return set_error(ctx, CUBE2_ERR_STATE, "the adjoint does not cover the adaptive third level");
     if (ctx->vjp_mu) return CUBE2_OK;
     int64_t m = 0;
@@ -766,6 +777,7 @@ int cube2_kdk_adjoint(cube2_ctx *ctx, const cube2_particles *const *states, cons
 
 int cube2_kdk_step_host(cube2_ctx *ctx, cube2_particles *dev, cube2_particles *host, double a0, double a1) {
     if (!ctx || !host) return CUBE2_ERR_BAD_ARG;
+    if (ctx->vel32) return set_error(ctx, CUBE2_ERR_BAD_ARG, "the host-buffer step takes FP32 velocities");
     if (!particles_ok(ctx, dev, true, true) || !particles_ok(ctx, host, true, true))
         return set_error(ctx, CUBE2_ERR_BAD_ARG, "bad particle arrays");
     const size_t N = (size_t)ctx->N, C = (size_t)ctx->n_cells;
@@ -932,6 +944,26 @@ int cube2_pp_stats(cube2_ctx *ctx, int64_t out[2]) {
     out[0] = (int64_t)h[0];
     out[1] = (int64_t)h[1];
     return CUBE2_OK;
+}
+
+int cube2_vel_encode(cube2_ctx *ctx, const cube2_particles *p, const float *const v[3]) {
+    if (!ctx || !v) return CUBE2_ERR_BAD_ARG;
+    if (!ctx->vel32) return set_error(ctx, CUBE2_ERR_STATE, "the context was not made with vel_fp16");
+    if (!particles_ok(ctx, p, true, false) || (ctx->N > 0 && (!v[0] || !v[1] || !v[2])))
+        return set_error(ctx, CUBE2_ERR_BAD_ARG, "bad particle or velocity arrays");
+    cudaError_t e = launch_cellid(ctx, p);
+    if (e == cudaSuccess) e = launch_vel_encode(ctx, p, v);
+    return e == cudaSuccess ? CUBE2_OK : cuda_error(ctx, e, "velocity encode");
+}
+
+int cube2_vel_decode(cube2_ctx *ctx, const cube2_particles *p, float *const v[3]) {
+    if (!ctx || !v) return CUBE2_ERR_BAD_ARG;
+    if (!ctx->vel32) return set_error(ctx, CUBE2_ERR_STATE, "the context was not made with vel_fp16");
+    if (!particles_ok(ctx, p, true, false) || (ctx->N > 0 && (!v[0] || !v[1] || !v[2])))
+        return set_error(ctx, CUBE2_ERR_BAD_ARG, "bad particle or velocity arrays");
+    cudaError_t e = launch_cellid(ctx, p);
+    if (e == cudaSuccess) e = launch_vel_decode(ctx, p, v);
+    return e == cudaSuccess ? CUBE2_OK : cuda_error(ctx, e, "velocity decode");
 }
 
 int cube2_pm3_info(cube2_ctx *ctx, double out[8]) {

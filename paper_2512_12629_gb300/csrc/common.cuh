@@ -131,6 +131,7 @@ struct cube2_ctx {
     float *vjp_u = nullptr;        // [12][N] reverse-step scratch
     double *vjp_sq = nullptr;      // [1] loss accumulator
     cube2::PM3 pm3;                // adaptive third level (cfg.pm3_tile > 0)
+    float *vel32 = nullptr;        // [3][N] FP32 working momenta of a step (cfg.vel_fp16 = 1 only)
 };
 
 namespace cube2 {
@@ -183,6 +184,8 @@ cudaError_t launch_pp(cube2_ctx *ctx, const cube2_particles *p, int accumulate, 
 cudaError_t launch_fft_batched_solve(cube2_ctx *ctx, Level &L);     // forward, z * G * z^-1, inverse
 cudaError_t launch_pm3(cube2_ctx *ctx, const cube2_particles *p);    // map, local deposit + solve, gather (acc +=)
 cudaError_t launch_pm3_map(cube2_ctx *ctx, const cube2_particles *p);  // refinement map only
+cudaError_t launch_vel_encode(cube2_ctx *ctx, const cube2_particles *p, const float *const v[3]);
+cudaError_t launch_vel_decode(cube2_ctx *ctx, const cube2_particles *p, float *const v[3]);
 cudaError_t launch_kick(cube2_ctx *ctx, const cube2_particles *p, float kick);
 cudaError_t launch_kick_drift(cube2_ctx *ctx, const cube2_particles *p, float kick, float drift_fix);
 cudaError_t launch_scan(cube2_ctx *ctx, const int32_t *in, int32_t *out, int64_t n);

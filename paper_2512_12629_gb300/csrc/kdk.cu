@@ -18,6 +18,8 @@
 //   6. ncount/nstart copied into the caller's count/start
 #include "common.cuh"
 
+#include <cuda_fp16.h>
+
 namespace cube2 {
 namespace {
 
@@ -39,6 +41,8 @@ __global__ void kick_kernel(float *v0, float *v1, float *v2, const float *a0, co
 struct DriftParams {
     const uint16_t *off0, *off1, *off2;
     const float *vel0, *vel1, *vel2;
+    const uint16_t *v16_0, *v16_1, *v16_2;   // FP16 storage (null: FP32 vel)
+    const float *vscale;                     // its per-cell scale
     const float *acc0, *acc1, *acc2;
     const int32_t *cellid;
     int32_t *count;           // zeroed before the launch, receives the new histogram
@@ -58,8 +62,18 @@ __global__ void __launch_bounds__(256) kick_drift_kernel(DriftParams P) {
     const int c = P.cellid[i];
     const int cc[3] = {c % n, (c / n) % n, c / (n * n)};
     const uint16_t off[3] = {P.off0[i], P.off1[i], P.off2[i]};
-    const float v[3] = {P.vel0[i] + P.kick * P.acc0[i], P.vel1[i] + P.kick * P.acc1[i],
-                        P.vel2[i] + P.kick * P.acc2[i]};
+    float v0[3];
+    if (P.v16_0) {
+        const float sc = P.vscale[c];
+        v0[0] = __half2float(__ushort_as_half(P.v16_0[i])) * sc;
+        v0[1] = __half2float(__ushort_as_half(P.v16_1[i])) * sc;
+        v0[2] = __half2float(__ushort_as_half(P.v16_2[i])) * sc;
+    } else {
+        v0[0] = P.vel0[i];
+        v0[1] = P.vel1[i];
+        v0[2] = P.vel2[i];
+    }
+    const float v[3] = {v0[0] + P.kick * P.acc0[i], v0[1] + P.kick * P.acc1[i], v0[2] + P.kick * P.acc2[i]};
     const int period = n * FIX;
     int nc[3];
     uint16_t no[3];
@@ -328,7 +342,69 @@ __global__ void gather_kernel(GatherParams P) {
     P.cellid[i] = P.tcell[j];
 }
 
+// FP16 velocity codec: per IOS cell the FP32 scale max_p,d |v_d| (an atomic
+// max on the bit patterns, which order like the values for v >= 0, so the
+// result does not depend on order), then code = RN_half(RN32(v / scale)).
+__global__ void vel_scale_kernel(const float *__restrict__ v0, const float *__restrict__ v1,
+                                 const float *__restrict__ v2, const int32_t *__restrict__ cellid,
+                                 float *__restrict__ vscale, int64_t N) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const float m = fmaxf(fabsf(v0[i]), fmaxf(fabsf(v1[i]), fabsf(v2[i])));
+    atomicMax(reinterpret_cast<int *>(&vscale[cellid[i]]), __float_as_int(m));
+}
+
+__global__ void vel_encode_kernel(const float *__restrict__ v0, const float *__restrict__ v1,
+                                  const float *__restrict__ v2, const int32_t *__restrict__ cellid,
+                                  const float *__restrict__ vscale, uint16_t *__restrict__ c0,
+                                  uint16_t *__restrict__ c1, uint16_t *__restrict__ c2, int64_t N) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const float s = vscale[cellid[i]];
+    if (s > 0.0f) {
+        c0[i] = __half_as_ushort(__float2half_rn(__fdiv_rn(v0[i], s)));
+        c1[i] = __half_as_ushort(__float2half_rn(__fdiv_rn(v1[i], s)));
+        c2[i] = __half_as_ushort(__float2half_rn(__fdiv_rn(v2[i], s)));
+    } else {
+        c0[i] = c1[i] = c2[i] = 0;
+    }
+}
+
+__global__ void vel_decode_kernel(const uint16_t *__restrict__ c0, const uint16_t *__restrict__ c1,
+                                  const uint16_t *__restrict__ c2, const int32_t *__restrict__ cellid,
+                                  const float *__restrict__ vscale, float *__restrict__ v0, float *__restrict__ v1,
+                                  float *__restrict__ v2, int64_t N) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const float s = vscale[cellid[i]];
+    v0[i] = __half2float(__ushort_as_half(c0[i])) * s;
+    v1[i] = __half2float(__ushort_as_half(c1[i])) * s;
+    v2[i] = __half2float(__ushort_as_half(c2[i])) * s;
+}
+
 }  // namespace
+
+// p->vel16 / p->vscale from FP32 momenta v (ctx->cellid must hold p's cells).
+cudaError_t launch_vel_encode(cube2_ctx *ctx, const cube2_particles *p, const float *const v[3]) {
+    cudaError_t e = cudaMemsetAsync(p->vscale, 0, sizeof(float) * ctx->n_cells, ctx->stream);
+    const int64_t blocks = (ctx->N + 255) / 256;
+    if (e != cudaSuccess || blocks == 0) return e;
+    ProfScope prof(ctx, P_KICK, 0);
+    vel_scale_kernel<<<(unsigned)blocks, 256, 0, ctx->stream>>>(v[0], v[1], v[2], ctx->cellid, p->vscale, ctx->N);
+    vel_encode_kernel<<<(unsigned)blocks, 256, 0, ctx->stream>>>(v[0], v[1], v[2], ctx->cellid, p->vscale, p->vel16[0],
+                                                                p->vel16[1], p->vel16[2], ctx->N);
+    ctx->launches += 2;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_vel_decode(cube2_ctx *ctx, const cube2_particles *p, float *const v[3]) {
+    const int64_t blocks = (ctx->N + 255) / 256;
+    if (blocks == 0) return cudaSuccess;
+    vel_decode_kernel<<<(unsigned)blocks, 256, 0, ctx->stream>>>(p->vel16[0], p->vel16[1], p->vel16[2], ctx->cellid,
+                                                                p->vscale, v[0], v[1], v[2], ctx->N);
+    ctx->launches++;
+    return cudaGetLastError();
+}
 
 int64_t scan_scratch_len(int64_t n) {
     int64_t total = 0;
@@ -375,6 +451,10 @@ cudaError_t launch_kick_drift(cube2_ctx *ctx, const cube2_particles *p, float ki
     DriftParams P{};
     P.off0 = p->off[0]; P.off1 = p->off[1]; P.off2 = p->off[2];
     P.vel0 = p->vel[0]; P.vel1 = p->vel[1]; P.vel2 = p->vel[2];
+    if (ctx->vel32) {
+        P.v16_0 = p->vel16[0]; P.v16_1 = p->vel16[1]; P.v16_2 = p->vel16[2];
+        P.vscale = p->vscale;
+    }
     P.acc0 = p->acc[0]; P.acc1 = p->acc[1]; P.acc2 = p->acc[2];
     P.cellid = ctx->cellid;
     P.count = ctx->ncount;
@@ -451,7 +531,11 @@ cudaError_t launch_rebin(cube2_ctx *ctx, const cube2_particles *p) {
         G.toff = ctx->toff;
         G.tvel = ctx->tvel;
         G.off0 = p->off[0]; G.off1 = p->off[1]; G.off2 = p->off[2];
-        G.vel0 = p->vel[0]; G.vel1 = p->vel[1]; G.vel2 = p->vel[2];
+        if (ctx->vel32) {   // FP16 storage: the step's FP32 working copy
+            G.vel0 = ctx->vel32; G.vel1 = ctx->vel32 + ctx->N; G.vel2 = ctx->vel32 + 2 * ctx->N;
+        } else {
+            G.vel0 = p->vel[0]; G.vel1 = p->vel[1]; G.vel2 = p->vel[2];
+        }
         G.cellid = ctx->cellid;
         G.N = ctx->N;
         {

@@ -732,7 +732,11 @@ static PPParams pp_params(cube2_ctx *ctx, const cube2_particles *p, int accumula
     P.perm = ctx->pp_perm;
     P.count = p->count; P.start = p->start;
     P.acc0 = p->acc[0]; P.acc1 = p->acc[1]; P.acc2 = p->acc[2];
-    P.vel0 = p->vel[0]; P.vel1 = p->vel[1]; P.vel2 = p->vel[2];
+    if (ctx->vel32) {   // FP16 storage: the second kick updates the step's FP32 working copy
+        P.vel0 = ctx->vel32; P.vel1 = ctx->vel32 + ctx->N; P.vel2 = ctx->vel32 + 2 * ctx->N;
+    } else {
+        P.vel0 = p->vel[0]; P.vel1 = p->vel[1]; P.vel2 = p->vel[2];
+    }
     P.stats = ctx->pp_stats;
     P.N = ctx->N;
     P.n_ios = ctx->n_ios;

@@ -57,6 +57,7 @@ class Config(ctypes.Structure):
         ("pm3_beta", ctypes.c_double),
         ("pm3_rho_min", ctypes.c_int32),
         ("pm3_max_tiles", ctypes.c_int32),
+        ("vel_fp16", ctypes.c_int32),
     ]
 
 
@@ -68,6 +69,8 @@ class Particles(ctypes.Structure):
         ("start", ctypes.c_void_p),
         ("vel", ctypes.c_void_p * 3),
         ("acc", ctypes.c_void_p * 3),
+        ("vel16", ctypes.c_void_p * 3),
+        ("vscale", ctypes.c_void_p),
     ]
 
 
@@ -105,6 +108,8 @@ def _load():
         "cube2_pm3_info": (I, [P, ctypes.POINTER(D)]),
         "cube2_pm3_stats": (I, [P, ctypes.POINTER(ctypes.c_int64)]),
         "cube2_pm3_map": (I, [P, P]),
+        "cube2_vel_encode": (I, [P, ctypes.POINTER(Particles), P]),
+        "cube2_vel_decode": (I, [P, ctypes.POINTER(Particles), P]),
         "cube2_adjoint_init": (I, [P]),
         "cube2_force_vjp": (I, [P, ctypes.POINTER(Particles), P, P]),
         "cube2_kdk_permutation": (I, [P, P]),
@@ -149,6 +154,7 @@ def make_config(w, n_particles=None, alias_max=2) -> Config:
     c.alias_max = alias_max
     c.assign_order = getattr(w, "assign_order", 2)
     c.iso_length = getattr(w, "iso_length", 0.0)
+    c.vel_fp16 = 1 if getattr(w, "vel_fp16", False) else 0
     pm3 = getattr(w, "pm3", None)
     if pm3 is not None:
         c.pm3_tile, c.pm3_refine, c.pm3_beta = pm3.tile, pm3.refine, pm3.beta
@@ -158,12 +164,17 @@ def make_config(w, n_particles=None, alias_max=2) -> Config:
 
 @dataclass
 class IOSState:
-    """Particle set in IOS form as torch tensors (device or pinned host)."""
+    """Particle set in IOS form as torch tensors (device or pinned host).
+
+    vel16 / vscale (optional): FP16 velocity storage for contexts made with
+    vel_fp16 (then ``vel`` is unused and may be a placeholder)."""
     off: torch.Tensor     # (3, N) int16 storage of the uint16 offsets
     count: torch.Tensor   # (n_ios^3,) int32
     start: torch.Tensor   # (n_ios^3,) int32
     vel: torch.Tensor     # (3, N) float32
     acc: torch.Tensor     # (3, N) float32
+    vel16: torch.Tensor = None   # (3, N) int16 storage of IEEE binary16 codes
+    vscale: torch.Tensor = None  # (n_ios^3,) float32 per-cell scale
 
     @property
     def n(self):
@@ -191,7 +202,8 @@ class IOSState:
                     start=self.start.cpu().numpy(), vel=self.vel.cpu().numpy(), acc=self.acc.cpu().numpy())
 
     def clone(self):
-        return IOSState(*(x.clone() for x in (self.off, self.count, self.start, self.vel, self.acc)))
+        extra = (None, None) if self.vel16 is None else (self.vel16.clone(), self.vscale.clone())
+        return IOSState(*(x.clone() for x in (self.off, self.count, self.start, self.vel, self.acc)), *extra)
 
     def struct(self) -> Particles:
         p = Particles()
@@ -202,6 +214,10 @@ class IOSState:
             p.acc[d] = self.acc[d].data_ptr()
         p.count = self.count.data_ptr()
         p.start = self.start.data_ptr()
+        if self.vel16 is not None:
+            for d in range(3):
+                p.vel16[d] = self.vel16[d].data_ptr()
+            p.vscale = self.vscale.data_ptr()
         return p
 
 
@@ -364,6 +380,23 @@ class Context:
 
     def check(self):
         self._chk(_lib.cube2_check(self.ptr))
+
+    def vel_encode(self, p: IOSState, v: torch.Tensor):
+        """Fill p.vel16 / p.vscale (allocated here if absent) from FP32 momenta v (3, N)."""
+        if p.vel16 is None:
+            p.vel16 = torch.empty(p.off.shape, dtype=torch.int16, device=p.off.device)
+            p.vscale = torch.empty(p.count.shape, dtype=torch.float32, device=p.off.device)
+        vp = (ctypes.c_void_p * 3)(*[v[d].data_ptr() for d in range(3)])
+        self._chk(_lib.cube2_vel_encode(self.ptr, ctypes.byref(p.struct()), vp))
+        return p
+
+    def vel_decode(self, p: IOSState, out: torch.Tensor = None):
+        """FP32 momenta (3, N) = half(p.vel16) * p.vscale of each particle's cell."""
+        if out is None:
+            out = torch.empty(p.off.shape, dtype=torch.float32, device=p.off.device)
+        vp = (ctypes.c_void_p * 3)(*[out[d].data_ptr() for d in range(3)])
+        self._chk(_lib.cube2_vel_decode(self.ptr, ctypes.byref(p.struct()), vp))
+        return out
 
     def pm3_info(self):
         """Geometry of the adaptive third level: dict(tile, ns, refine, B, m, H3, b3, max_tiles)."""

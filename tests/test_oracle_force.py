@@ -63,6 +63,10 @@ def test_pp_cell_list_matches_brute_force_and_is_antisymmetric():
     assert np.array_equal(sub, f[:, [3, 77, 500]])
     at = P.pp_force_at(st["off"], st["count"], st["start"], w.n_ios, w.box, b_pp, b_cut, [0, 3, 77, 500, 599])
     assert np.allclose(at, f[:, [0, 3, 77, 500, 599]], rtol=1e-12, atol=1e-12 * np.abs(f).max())
+    # the vectorised point evaluator, on every particle (repeats included)
+    t = np.concatenate([np.arange(600), [3, 3, 599]])
+    many = P.pp_force_at_many(st["off"], st["count"], st["start"], w.n_ios, w.box, b_pp, b_cut, t)
+    assert np.allclose(many, f[:, t], rtol=1e-12, atol=1e-12 * np.abs(f).max())
 
 
 def _ewald_errors(w, n, seed):

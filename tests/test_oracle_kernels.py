@@ -141,3 +141,34 @@ def test_green_by_symmetry_equals_full_table(n, order, iso):
     g = K.green(n, 2.0, 7.0, order=order, iso=iso)
     gs = K.green_by_symmetry(n, 2.0, 7.0, order=order, iso=iso, chunk=37)
     assert np.abs(gs - g).max() <= 1e-13 * np.abs(g).max()
+
+
+def test_velocity_codec_follows_the_binary16_format():
+    # pins of the compressed velocity storage from the binary16 format itself:
+    # 11 significant bits, so the round trip errs by half an ulp of the code
+    # plus the FP32 roundings of the division and the decode: within one ulp
+    # (2^-11 of the scale for codes in [1/2, 1), 2^-12 below 1/2); the
+    # largest component of each cell is +-1 x scale exactly; empty and
+    # all-zero cells give zero codes; powers of two times the scale are exact
+    from oracle import kdk as KD
+    rng = np.random.default_rng(7)
+    count = np.array([0, 5, 1, 0, 7, 3], dtype=np.int32)
+    n = int(count.sum())
+    vel = (rng.normal(size=(3, n)) * rng.lognormal(0.0, 2.0, size=n)).astype(np.float32)
+    vel[:, 5] = 0.0                                # the one-particle cell: all zero
+    vel[1, 6] = 0.25 * np.abs(vel[:, 6:13]).max()  # a power of two times its cell's scale
+    codes, scale = KD.encode_velocities(vel, count)
+    assert codes.dtype == np.float16 and scale.dtype == np.float32
+    assert scale[0] == 0 and scale[3] == 0 and scale[2] == 0
+    back = KD.decode_velocities(codes, scale, count).astype(np.float64)
+    cell = np.repeat(np.arange(count.size), count)
+    s = scale[cell].astype(np.float64)
+    ratio = np.abs(vel / np.where(s > 0, s, 1.0))
+    ulp = np.where(ratio >= 0.5, 2.0 ** -11, 2.0 ** -12)
+    assert np.all(np.abs(back - vel) <= ulp * s * (1 + 1e-6) + 1e-30)
+    assert np.all(np.abs(codes.astype(np.float32)).max(axis=0)[count[cell] > 0] <= 1.0)
+    for c in np.nonzero(scale > 0)[0]:
+        sel = cell == c
+        assert np.abs(codes[:, sel].astype(np.float32)).max() == 1.0
+    assert back[1, 6] == vel[1, 6]
+    assert not codes[:, 5].any()
