@@ -387,6 +387,15 @@ int cube2_kdk_permutation(cube2_ctx *ctx, int32_t *out);
 int cube2_density_mse_vjp(cube2_ctx *ctx, int level, const cube2_particles *p, const float *target,
                           float *const w[3], double *loss);
 
+/* Position gradient of <g, delta> for a cotangent g on the density of level
+ * `level` (device FP32 [n][n][n], the layout of cube2_get_density): w[d]
+ * (device FP32 [N], overwritten) = d<g, delta>/dx_i = (n^3/(N H)) sum_c
+ * g(c) grad_u W(u_i, c), with delta the CIC overdensity cube2_deposit
+ * computes (Sec. 2.1.2 assignment; IOS quantisation taken as the identity).
+ * The entry of a backward pass through the final density: the cotangent
+ * arrives as it is, with no loss of its own.  Overwrites the level's grid. */
+int cube2_density_vjp(cube2_ctx *ctx, int level, const cube2_particles *p, const float *g, float *const w[3]);
+
 /* Reverse of one cube2_kdk_step(a0, a1) (Sec. 2.2: kick K(a0, ah), drift
  * Dr(a0, a1), force, kick K(ah, a1); drift rounding taken as the identity).
  * pre / post: the particle states before and after the step (positions,
@@ -439,6 +448,60 @@ typedef struct cube2_ensemble cube2_ensemble;
  * failure nothing is kept and *out is NULL. */
 int cube2_ensemble_create(cube2_ensemble **out, cube2_ctx *const *ctxs, cube2_particles *const *parts,
                           int n_boxes, const double *a, int n_steps, int n_streams);
+
+/* Options of an ensemble recording.
+ *   n_streams       concurrent graph branches (1..64); boxes are placed on them
+ *                   by cube2_lpt_partition of cube2_config_cost
+ *   persistent_pp   0: every box's steps are its own launches on its branch
+ *                   (one join at the end).  1: step by step, each box's step
+ *                   up to its PP inputs on its branch, then ONE persistent PP
+ *                   kernel (with the second kick) over every box: its CTAs take
+ *                   (box, block of 128 targets) items from a device queue,
+ *                   ordered each step by a cost estimate (the particles in the
+ *                   targets' IOS cells; largest first, the load balancing of
+ *                   Sec. 2.2.3).  The host publishes each step's queue by a
+ *                   stream-ordered write of the step's epoch from pinned
+ *                   memory; the kernel waits for it at most timeout_ms
+ *                   (%globaltimer) and otherwise records CUBE2_ERR_TIMEOUT
+ *                   (cube2_ensemble_check) and returns.  Boxes with the third
+ *                   level or FP16 velocities are refused (CUBE2_ERR_STATE).
+ *   pp_ctas_per_sm  persistent grid: CTAs per SM (1..16)
+ *   pp_wmax         PP shared-stream width for every box (0: each context's own, 16)
+ *   timeout_ms      bound of the persistent kernel's wait (> 0)                  */
+typedef struct {
+    int32_t n_streams;
+    int32_t persistent_pp;
+    int32_t pp_ctas_per_sm;
+    int32_t pp_wmax;
+    double  timeout_ms;
+} cube2_ensemble_opts;
+
+/* cube2_ensemble_create with options (cube2_ensemble_create is this with
+ * persistent_pp = 0, pp_wmax = 0). */
+int cube2_ensemble_create_ex(cube2_ensemble **out, cube2_ctx *const *ctxs, cube2_particles *const *parts,
+                             int n_boxes, const double *a, int n_steps, const cube2_ensemble_opts *opts);
+
+/* Synchronise `stream` and return CUBE2_ERR_TIMEOUT (clearing it) if a
+ * persistent PP kernel of the last launches gave up waiting for its queue;
+ * the boxes' states are then unspecified.  CUBE2_OK otherwise. */
+int cube2_ensemble_check(cube2_ensemble *ens, void *stream);
+
+/* Host control of the persistent kernel's queue publication: on = 0 makes the
+ * later launches write no valid epoch (the host withholds the work counts), so
+ * that each persistent kernel's bounded wait runs out; on = 1 restores it.
+ * This is how a lost host publication is detected without any GPU fault. */
+int cube2_ensemble_publish(cube2_ensemble *ens, int on);
+
+/* Autotuner of the runtime knobs: starting from *best (persistent_pp and
+ * timeout_ms kept), a coordinate search over pp_ctas_per_sm in {4, 8, 16}
+ * (persistent only), pp_wmax in {8, 16, 24} and n_streams in {8, 16, 32}; each
+ * candidate is recorded and timed with CUDA events on `stream` (the fastest of
+ * `trials` launches after one warm-up launch), every launch starting from the
+ * boxes' states at the call (snapshotted in scratch that this call allocates
+ * and frees; states restored at the end).  Writes the fastest options to *best
+ * and their milliseconds per launch to *best_ms. */
+int cube2_ensemble_autotune(cube2_ctx *const *ctxs, cube2_particles *const *parts, int n_boxes, const double *a,
+                            int n_steps, int trials, void *stream, cube2_ensemble_opts *best, double *best_ms);
 
 /* Run the recorded steps once on `stream` (a cudaStream_t; NULL = default
  * stream).  Each launch advances every box by its n_steps from whatever state

@@ -106,9 +106,58 @@ def _pairs(x, box, b_cut):
     return i, j, d[:, i, j], r[i, j]
 
 
+def _pairs_cells(x, box, b_cut):
+    """The pairs of ``_pairs`` found through a cell list: cells of side
+    box / nc >= b_cut (nc >= 3), every particle against the particles of its
+    27 neighbouring cells (minimum image)."""
+    nc = int(box // b_cut)
+    if nc < 3:
+        return _pairs(x, box, b_cut)
+    side = box / nc
+    c3 = np.floor(x / side).astype(np.int64) % nc
+    cid = (c3[2] * nc + c3[1]) * nc + c3[0]
+    order = np.argsort(cid, kind="stable")
+    cnt = np.bincount(cid, minlength=nc ** 3)
+    beg = np.cumsum(cnt) - cnt
+    cells = np.arange(nc ** 3, dtype=np.int64)
+    cx, cy, cz = cells % nc, (cells // nc) % nc, cells // (nc * nc)
+    out_i, out_j = [], []
+    for oz in (-1, 0, 1):
+        for oy in (-1, 0, 1):
+            for ox in (-1, 0, 1):
+                nb = (((cz + oz) % nc) * nc + (cy + oy) % nc) * nc + (cx + ox) % nc
+                npair = cnt * cnt[nb]
+                keep = npair > 0
+                if not keep.any():
+                    continue
+                ck, nbk, ci, cj, np_k = cells[keep], nb[keep], cnt[keep], cnt[nb][keep], npair[keep]
+                tot = int(np_k.sum())
+                first = np.repeat(np.cumsum(np_k) - np_k, np_k)
+                local = np.arange(tot, dtype=np.int64) - first
+                rep_cj = np.repeat(cj, np_k)
+                a = np.repeat(beg[ck], np_k) + local // rep_cj
+                b = np.repeat(beg[nbk], np_k) + local % rep_cj
+                out_i.append(order[a])
+                out_j.append(order[b])
+    if not out_i:
+        z = np.zeros(0, dtype=np.int64)
+        return z, z, np.zeros((3, 0)), np.zeros(0)
+    i, j = np.concatenate(out_i), np.concatenate(out_j)
+    d = x[:, j] - x[:, i]
+    d -= box * np.rint(d / box)
+    r = np.sqrt((d * d).sum(axis=0))
+    m = (r > 0) & (r < b_cut) & (i != j)
+    return i[m], j[m], d[:, m], r[m]
+
+
+def _pair_search(x, box, b_cut):
+    """All-pairs for small sets, the cell list beyond 4096 particles."""
+    return _pairs(x, box, b_cut) if x.shape[1] <= 4096 else _pairs_cells(x, box, b_cut)
+
+
 def pp_force(x, box, n_particles, b_pp, b_cut):
-    """PP force (3, N) at continuous positions, all pairs."""
-    i, j, d, r = _pairs(x, box, b_cut)
+    """PP force (3, N) at continuous positions (every pair closer than b_cut)."""
+    i, j, d, r = _pair_search(x, box, b_cut)
     g = box ** 3 / n_particles * pp_reference(r, b_pp, b_cut) / (4 * math.pi * r)
     f = np.zeros_like(x)
     for ax in range(3):
@@ -117,8 +166,8 @@ def pp_force(x, box, n_particles, b_pp, b_cut):
 
 
 def pp_vjp(x, v, box, n_particles, b_pp, b_cut):
-    """d<v, F_PP(x)>/dx (3, N), all pairs."""
-    i, j, d, r = _pairs(x, box, b_cut)
+    """d<v, F_PP(x)>/dx (3, N) (every pair closer than b_cut)."""
+    i, j, d, r = _pair_search(x, box, b_cut)
     vp = box ** 3 / n_particles / (4 * math.pi)
     rpp = pp_reference(r, b_pp, b_cut)
     drpp = reference_force_derivative(r, b_pp) - reference_force_derivative(r, b_cut)

@@ -707,6 +707,27 @@ int cube2_density_mse_vjp(cube2_ctx *ctx, int level, const cube2_particles *p, c
     return CUBE2_OK;
 }
 
+int cube2_density_vjp(cube2_ctx *ctx, int level, const cube2_particles *p, const float *g, float *const w[3]) {
+    if (!ctx) return CUBE2_ERR_BAD_ARG;
+    int r = level_ok(ctx, level, false);
+    if (r) return r;
+    if (!particles_ok(ctx, p, false, false) || !g || !w)
+        return set_error(ctx, CUBE2_ERR_BAD_ARG, "bad particle, cotangent or output arrays");
+    for (int d = 0; d < 3; ++d)
+        if (ctx->N > 0 && !w[d]) return set_error(ctx, CUBE2_ERR_BAD_ARG, "null output array");
+    if (ctx->cfg.assign_order == 3)
+        return set_error(ctx, CUBE2_ERR_UNSUPPORTED_SIZE, "the adjoint is built for the CIC assignment");
+    Level &L = ctx->lev[level];
+    cudaError_t e = launch_cellid(ctx, p);
+    for (int d = 0; d < 3 && e == cudaSuccess; ++d)
+        if (ctx->N > 0) e = cudaMemsetAsync(w[d], 0, sizeof(float) * (size_t)ctx->N, ctx->stream);
+    if (e == cudaSuccess) e = launch_density_vjp(ctx, L, p, g, w);
+    if (e != cudaSuccess) return cuda_error(ctx, e, "density_vjp");
+    L.has_density = false;
+    L.has_potential = false;
+    return CUBE2_OK;
+}
+
 int cube2_kdk_adjoint_step(cube2_ctx *ctx, const cube2_particles *pre, const cube2_particles *post,
                            const int32_t *perm, float *const xbar[3], float *const pbar[3], double a0, double a1) {
     if (!ctx) return CUBE2_ERR_BAD_ARG;

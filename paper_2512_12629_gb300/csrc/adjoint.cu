@@ -236,6 +236,19 @@ cudaError_t launch_density_mse_vjp(cube2_ctx *ctx, Level &L, const cube2_particl
     return cudaGetLastError();
 }
 
+cudaError_t launch_density_vjp(cube2_ctx *ctx, Level &L, const cube2_particles *p, const float *g,
+                               float *const w[3]) {
+    const int64_t n3 = (int64_t)L.n * L.n * L.n;
+    cudaError_t e = cudaMemcpyAsync(L.real, g, sizeof(float) * n3, cudaMemcpyDeviceToDevice, ctx->stream);
+    if (e != cudaSuccess || ctx->N == 0) return e;
+    const float *const nv[3] = {nullptr, nullptr, nullptr};
+    VjpParams P = make_params(ctx, L, p, nv, w, L.real);
+    P.scale = (float)((double)n3 / ((double)ctx->N * L.H));
+    vjp_gather_kernel<false><<<(unsigned)((ctx->N + 255) / 256), 256, 0, ctx->stream>>>(P);
+    ctx->launches++;
+    return cudaGetLastError();
+}
+
 cudaError_t launch_kdk_adjoint_scatter(cube2_ctx *ctx, const int32_t *perm, float *const xbar[3],
                                        float *const pbar[3], const float *t, float k2) {
     // xbar/pbar are three separate arrays: gather them through the scratch rows

@@ -132,6 +132,12 @@ struct cube2_ctx {
     double *vjp_sq = nullptr;      // [1] loss accumulator
     cube2::PM3 pm3;                // adaptive third level (cfg.pm3_tile > 0)
     float *vel32 = nullptr;        // [3][N] FP32 working momenta of a step (cfg.vel_fp16 = 1 only)
+    // shared-stream width of the PP kernel (warps spanning at most pp_wmax + 1 cells)
+    int pp_wmax = 16;
+    // ensemble recording: launch_pp prepares the PP inputs and leaves the PP
+    // kernel to the ensemble's persistent kernel, saving its parameters here
+    bool defer_pp = false;
+    alignas(16) unsigned char pp_deferred[320];
 };
 
 namespace cube2 {
@@ -185,6 +191,11 @@ cudaError_t launch_fft_batched_solve(cube2_ctx *ctx, Level &L);     // forward, 
 cudaError_t launch_pm3(cube2_ctx *ctx, const cube2_particles *p);    // map, local deposit + solve, gather (acc +=)
 cudaError_t launch_pm3_map(cube2_ctx *ctx, const cube2_particles *p);  // refinement map only
 cudaError_t launch_vel_encode(cube2_ctx *ctx, const cube2_particles *p, const float *const v[3]);
+size_t pp_params_bytes();
+size_t pp_queue_bytes();
+cudaError_t launch_pp_persistent_step(cudaStream_t st, const void *boxes, const int32_t *item_box,
+                                      const int32_t *base, int n_items, unsigned *cost, int32_t *order, void *queue,
+                                      const int *publish_host, int epoch, unsigned long long timeout_ns, int grid);
 cudaError_t launch_vel_decode(cube2_ctx *ctx, const cube2_particles *p, float *const v[3]);
 cudaError_t launch_kick(cube2_ctx *ctx, const cube2_particles *p, float kick);
 cudaError_t launch_kick_drift(cube2_ctx *ctx, const cube2_particles *p, float kick, float drift_fix);
@@ -201,6 +212,7 @@ cudaError_t launch_vjp_source(cube2_ctx *ctx, Level &L, const cube2_particles *p
 cudaError_t launch_pp_vjp(cube2_ctx *ctx, const cube2_particles *p, const float *const v[3], float *const w[3]);
 cudaError_t launch_density_mse_vjp(cube2_ctx *ctx, Level &L, const cube2_particles *p, const float *target,
                                    float *const w[3], double *sq);
+cudaError_t launch_density_vjp(cube2_ctx *ctx, Level &L, const cube2_particles *p, const float *g, float *const w[3]);
 cudaError_t launch_kdk_adjoint_scatter(cube2_ctx *ctx, const int32_t *perm, float *const xbar[3],
                                        float *const pbar[3], const float *t, float k2);
 cudaError_t launch_kdk_adjoint_drift(cube2_ctx *ctx, float *const xbar[3], float *const pbar[3], float drift);

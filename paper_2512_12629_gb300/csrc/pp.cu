@@ -15,7 +15,7 @@
 // dense cells (64 or more) reordered by a 4x4x4 sub-cell key inside their
 // cell (PP's own position array and slot -> particle map; results are written
 // back to the particle's index).  A warp whose 32 targets
-// lie in one row of cells, narrow enough (every dense region; see PP_WMAX),
+// lie in one row of cells, narrow enough (every dense region; see wmax),
 // shares one source stream: the particles of cells xa-1 .. xb+1 in the 9 rows
 // around it.  It stages 64 sources at a time in shared memory; each lane tests
 // all 64 (sign of r^2 - b_cut^2 shifted into two 32-bit masks, 8 instructions
@@ -29,6 +29,8 @@
 // on the cell layout and every sum has a fixed order, so results are bitwise
 // reproducible.
 #include "common.cuh"
+
+#include <string.h>
 
 namespace cube2 {
 namespace {
@@ -51,6 +53,7 @@ struct PPParams {
     const int32_t *pm3_slot;
     int pm3_T, pm3_ns;
     float bcut2_3, inv_bcut_3;
+    int wmax;                         // widest warp (cells beyond the first) on the shared stream
 };
 
 // R(r, b) of Eq. (refforce) times b^2, as a function of u = r / b < 1.
@@ -285,13 +288,12 @@ struct WarpSegs {
     int cum[PP_SEGS + 2];
 };
 
-// Widest warp (cells beyond the first) that takes the shared-stream path: its
-// lanes test (w + 3) / 3 times their own candidates, still cheaper than the
-// per-lane walk up to about w = 16 over the 256^3 run (at full occupancy
-// w = 8, 12, 16 and 24 lie within 2 % of each other).
-#ifndef PP_WMAX
-#define PP_WMAX 16
-#endif
+// The widest warp (cells beyond the first) that takes the shared-stream path
+// is a runtime parameter (PPParams.wmax, the context's pp_wmax, 16 unless an
+// ensemble's autotuner chose another): its lanes test (w + 3) / 3 times their
+// own candidates, still cheaper than the per-lane walk up to about w = 16 over
+// the 256^3 run (at full occupancy w = 8, 12, 16 and 24 lie within 2 % of each
+// other).
 
 struct PPWarpShared {
     struct {
@@ -624,6 +626,9 @@ __device__ void union_vjp(const PPParams &P, const VjpIO &V, const WarpSegs &W, 
     }
 }
 
+// the adjoint's product keeps the force's default shared-stream width
+constexpr int PP_WMAX_VJP = 16;
+
 struct PPVjpWarpShared {
     float4 buf[64];   // staged source positions
     float4 vbuf[64];  // and their v_j
@@ -645,7 +650,7 @@ __global__ void __launch_bounds__(PP_CTA, PPV_MINB) pp_vjp_kernel(PPParams P, Vj
     if (!has) c = c0;
     const int c31 = __reduce_max_sync(0xffffffffu, c);
     const int xa = c0 % n, xb = c31 % n;
-    const bool one_row = (c0 / n) == (c31 / n) && xb - xa <= PP_WMAX && xb - xa + 3 <= n;
+    const bool one_row = (c0 / n) == (c31 / n) && xb - xa <= PP_WMAX_VJP && xb - xa + 3 <= n;
     const float vix = has ? V.v0[i] : 0.f, viy = has ? V.v1[i] : 0.f, viz = has ? V.v2[i] : 0.f;
     Sum3 a;
     if (one_row) {
@@ -668,10 +673,10 @@ __global__ void __launch_bounds__(PP_CTA, PPV_MINB) pp_vjp_kernel(PPParams P, Vj
 #ifndef PP_MINB
 #define PP_MINB 16
 #endif
+// The targets of one block of PP_CTA slots: [block * PP_CTA, block * PP_CTA + PP_CTA).
 template <bool PM3>
-__global__ void __launch_bounds__(PP_CTA, PP_MINB) pp_kernel(PPParams P) {
-    __shared__ PPShared sh;
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void pp_block(const PPParams &P, int64_t block, PPShared &sh) {
+    const int64_t i = block * PP_CTA + threadIdx.x;
     const int wib = threadIdx.x >> 5;
     const bool has = i < P.N;
     const int n = P.n_ios;
@@ -683,8 +688,8 @@ __global__ void __launch_bounds__(PP_CTA, PP_MINB) pp_kernel(PPParams P) {
     // lane 0 and the largest cell bound its extent
     const int c31 = __reduce_max_sync(0xffffffffu, c);
     const int xa = c0 % n, xb = c31 % n;
-    // warps inside one row, at most PP_WMAX + 1 cells wide, share a source stream
-    const bool one_row = (c0 / n) == (c31 / n) && xb - xa <= PP_WMAX && xb - xa + 3 <= n;
+    // warps inside one row, at most wmax + 1 cells wide, share a source stream
+    const bool one_row = (c0 / n) == (c31 / n) && xb - xa <= P.wmax && xb - xa + 3 <= n;
     if (one_row) build_segments(P, sh.w[wib].u.seg, c0, xa, xb);
     // PP range of this target: b_3 inside a refined subtile of the third level
     float bcut2 = P.bcut2, ibc = P.inv_bcut;
@@ -704,6 +709,108 @@ __global__ void __launch_bounds__(PP_CTA, PP_MINB) pp_kernel(PPParams P) {
         lane_path(P, has, c, me, bcut2, ibc, a, pairs, cands);
     if (has) finish(P, P.perm[i], a.x - a.cx, a.y - a.cy, a.z - a.cz);
     add_stats(P.stats, pairs, cands);
+}
+
+template <bool PM3>
+__global__ void __launch_bounds__(PP_CTA, PP_MINB) pp_kernel(PPParams P) {
+    __shared__ PPShared sh;
+    pp_block<PM3>(P, blockIdx.x, sh);
+}
+
+// ------------------------------------------------- ensemble: one persistent PP
+// kernel over many boxes.  Work items are (box, block) pairs; a per-step cost
+// estimate orders them largest first (the load balancing of Sec. 2.2.3: work
+// sorted by its density, taken in that order by whoever is free), and
+// persistent CTAs take the next item from a device counter.  The host
+// publishes each step's queue with a stream-ordered write of the step's epoch;
+// the kernel waits for that epoch for at most timeout_ns (%globaltimer), then
+// records CUBE2_ERR_TIMEOUT in the queue's status word and returns.
+struct PPQueueDev {
+    int head;        // next item to take
+    int count;       // items of this step
+    int ready;       // epoch published by the host
+    int status;      // sticky ST_TIMEOUT
+};
+
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// cost[k] of item k (box b = item_box[k], block j = k - base[b]): the number of
+// particles in the IOS cells of its targets, a proxy of the block's pair count
+__global__ void __launch_bounds__(256) pp_item_cost_kernel(const PPParams *__restrict__ boxes,
+                                                            const int32_t *__restrict__ item_box,
+                                                            const int32_t *__restrict__ base, int n_items,
+                                                            unsigned *__restrict__ cost) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n_items) return;
+    const int b = item_box[k];
+    const PPParams &P = boxes[b];
+    const int64_t i0 = (int64_t)(k - base[b]) * PP_CTA;
+    const int64_t i1 = min(i0 + PP_CTA, P.N);
+    unsigned s = 0;
+    for (int64_t i = i0; i < i1; ++i) s += (unsigned)__ldg(&P.count[__float_as_int(__ldg(&P.pos[i]).w)]);
+    cost[k] = s;
+}
+
+// One CTA: items bucketed by floor(log2(cost + 1)), largest bucket first,
+// written to order[]; the queue's counters are reset for the step.
+__global__ void __launch_bounds__(1024) pp_item_order_kernel(const unsigned *__restrict__ cost, int n_items,
+                                                             int32_t *__restrict__ order, PPQueueDev *q) {
+    __shared__ int hist[33], offs[33];
+    if (threadIdx.x < 33) hist[threadIdx.x] = 0;
+    __syncthreads();
+    for (int k = threadIdx.x; k < n_items; k += blockDim.x) atomicAdd(&hist[32 - __clz(cost[k] + 1u)], 1);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int run = 0;
+        for (int b = 32; b >= 0; --b) {
+            offs[b] = run;
+            run += hist[b];
+        }
+        q->head = 0;
+        q->count = n_items;
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < n_items; k += blockDim.x) order[atomicAdd(&offs[32 - __clz(cost[k] + 1u)], 1)] = k;
+}
+
+__global__ void __launch_bounds__(PP_CTA, PP_MINB) pp_persistent_kernel(const PPParams *__restrict__ boxes,
+                                                                       const int32_t *__restrict__ item_box,
+                                                                       const int32_t *__restrict__ base,
+                                                                       const int32_t *__restrict__ order,
+                                                                       PPQueueDev *q, int epoch,
+                                                                       unsigned long long timeout_ns) {
+    __shared__ PPShared sh;
+    __shared__ int s_item, s_ok;
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        const unsigned long long t0 = global_ns();
+        while (atomicAdd(&q->ready, 0) != epoch) {
+            if (atomicAdd(&q->status, 0) != 0 || global_ns() - t0 > timeout_ns) {
+                atomicOr(&q->status, ST_TIMEOUT);
+                ok = 0;
+                break;
+            }
+            __nanosleep(2000);
+        }
+        s_ok = ok;
+    }
+    __syncthreads();
+    if (!s_ok) return;
+    const int count = *((volatile int *)&q->count);
+    for (;;) {
+        if (threadIdx.x == 0) s_item = atomicAdd(&q->head, 1);
+        __syncthreads();
+        const int item = s_item;
+        __syncthreads();
+        if (item >= count) break;
+        const int k = order[item];
+        const int b = item_box[k];
+        pp_block<false>(boxes[b], (int64_t)(k - base[b]), sh);
+    }
 }
 
 }  // namespace
@@ -750,6 +857,7 @@ static PPParams pp_params(cube2_ctx *ctx, const cube2_particles *p, int accumula
     P.coef = (float)(vp / (4.0 * 3.14159265358979323846) / (s * s));
     P.kick = kick;
     P.status = ctx->dev_status;
+    P.wmax = ctx->pp_wmax;
     if (ctx->pm3.on) {
         P.pm3_slot = ctx->pm3.slot;
         P.pm3_T = ctx->pm3.T;
@@ -777,6 +885,12 @@ cudaError_t launch_pp(cube2_ctx *ctx, const cube2_particles *p, int accumulate, 
         pp_dense_sort_kernel<<<(unsigned)(ctx->num_sms * 8), 256, 0, ctx->stream>>>(
             p->off[0], p->off[1], p->off[2], p->count, p->start, ctx->big, ctx->big_n, ctx->pos4, ctx->pp_perm);
     }
+    if (ctx->defer_pp) {   // an ensemble's persistent kernel runs this box's PP later
+        static_assert(sizeof(PPParams) <= sizeof(ctx->pp_deferred), "deferred PP parameters");
+        memcpy(ctx->pp_deferred, &P, sizeof P);
+        ctx->launches += 3;
+        return cudaGetLastError();
+    }
     {
         ProfScope prof(ctx, P_PP, 0);
         if (P.pm3_slot)
@@ -787,5 +901,23 @@ cudaError_t launch_pp(cube2_ctx *ctx, const cube2_particles *p, int accumulate, 
     ctx->launches += 4;
     return cudaGetLastError();
 }
+
+size_t pp_params_bytes() { return sizeof(PPParams); }
+
+cudaError_t launch_pp_persistent_step(cudaStream_t st, const void *boxes, const int32_t *item_box,
+                                      const int32_t *base, int n_items, unsigned *cost, int32_t *order, void *queue,
+                                      const int *publish_host, int epoch, unsigned long long timeout_ns, int grid) {
+    const PPParams *B = static_cast<const PPParams *>(boxes);
+    PPQueueDev *q = static_cast<PPQueueDev *>(queue);
+    pp_item_cost_kernel<<<(unsigned)((n_items + 255) / 256), 256, 0, st>>>(B, item_box, base, n_items, cost);
+    pp_item_order_kernel<<<1, 1024, 0, st>>>(cost, n_items, order, q);
+    // the host's publication of this step's work count
+    cudaError_t e = cudaMemcpyAsync(&q->ready, publish_host, sizeof(int), cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return e;
+    pp_persistent_kernel<<<(unsigned)grid, PP_CTA, 0, st>>>(B, item_box, base, order, q, epoch, timeout_ns);
+    return cudaGetLastError();
+}
+
+size_t pp_queue_bytes() { return sizeof(PPQueueDev); }
 
 }  // namespace cube2

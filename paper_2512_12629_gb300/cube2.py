@@ -61,6 +61,20 @@ class Config(ctypes.Structure):
     ]
 
 
+class EnsembleOpts(ctypes.Structure):
+    _fields_ = [
+        ("n_streams", ctypes.c_int32),
+        ("persistent_pp", ctypes.c_int32),
+        ("pp_ctas_per_sm", ctypes.c_int32),
+        ("pp_wmax", ctypes.c_int32),
+        ("timeout_ms", ctypes.c_double),
+    ]
+
+
+def ensemble_opts(n_streams=16, persistent_pp=False, pp_ctas_per_sm=16, pp_wmax=0, timeout_ms=1000.0):
+    return EnsembleOpts(int(n_streams), int(bool(persistent_pp)), int(pp_ctas_per_sm), int(pp_wmax), float(timeout_ms))
+
+
 class Particles(ctypes.Structure):
     _fields_ = [
         ("n", ctypes.c_int64),
@@ -114,12 +128,18 @@ def _load():
         "cube2_force_vjp": (I, [P, ctypes.POINTER(Particles), P, P]),
         "cube2_kdk_permutation": (I, [P, P]),
         "cube2_density_mse_vjp": (I, [P, I, ctypes.POINTER(Particles), P, P, ctypes.POINTER(D)]),
+        "cube2_density_vjp": (I, [P, I, ctypes.POINTER(Particles), P, P]),
         "cube2_kdk_adjoint_step": (I, [P, ctypes.POINTER(Particles), ctypes.POINTER(Particles), P, P, P, D, D]),
         "cube2_kdk_adjoint": (I, [P, P, P, I, ctypes.POINTER(D), P, P]),
         "cube2_lpt_partition": (I, [ctypes.POINTER(D), I, I, ctypes.POINTER(I)]),
         "cube2_config_cost": (I, [ctypes.POINTER(Config), ctypes.POINTER(D)]),
         "cube2_ensemble_create": (I, [ctypes.POINTER(P), P, P, I, ctypes.POINTER(D), I, I]),
         "cube2_ensemble_launch": (I, [P, P]),
+        "cube2_ensemble_create_ex": (I, [ctypes.POINTER(P), P, P, I, ctypes.POINTER(D), I, ctypes.POINTER(EnsembleOpts)]),
+        "cube2_ensemble_check": (I, [P, P]),
+        "cube2_ensemble_publish": (I, [P, I]),
+        "cube2_ensemble_autotune": (I, [P, P, I, ctypes.POINTER(D), I, I, P, ctypes.POINTER(EnsembleOpts),
+                                        ctypes.POINTER(D)]),
         "cube2_ensemble_info": (I, [P, ctypes.POINTER(ctypes.c_int64)]),
         "cube2_ensemble_destroy": (None, [P]),
         "cube2_destroy": (None, [P]),
@@ -303,6 +323,15 @@ class Context:
         self._chk(_lib.cube2_density_mse_vjp(self.ptr, int(level), ctypes.byref(p.struct()), target.data_ptr(), wp,
                                              ctypes.byref(loss)))
         return loss.value, out
+
+    def density_vjp(self, level, p: IOSState, g: torch.Tensor, out: torch.Tensor = None):
+        """d<g, delta>/dx (3, N) FP32 for a cotangent g ([n][n][n] FP32, device) on the level's overdensity."""
+        if out is None:
+            out = torch.empty((3, p.n), dtype=torch.float32, device=p.off.device)
+        g = g.contiguous()
+        wp = (ctypes.c_void_p * 3)(*[out[d].data_ptr() for d in range(3)])
+        self._chk(_lib.cube2_density_vjp(self.ptr, int(level), ctypes.byref(p.struct()), g.data_ptr(), wp))
+        return out
 
     def kdk_adjoint_step(self, pre: IOSState, post: IOSState, perm: torch.Tensor, xbar: torch.Tensor,
                          pbar: torch.Tensor, a0, a1):
@@ -502,25 +531,35 @@ def lpt_partition(costs, bins):
     return out
 
 
+def _ensemble_arrays(ctxs, states, a):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    nb = a.shape[0]
+    if nb != len(ctxs) or nb != len(states):
+        raise ValueError("one context, state and schedule per box")
+    structs = [st.struct() for st in states]
+    cp = (ctypes.c_void_p * nb)(*[c.ptr.value for c in ctxs])
+    pp = (ctypes.c_void_p * nb)(*[ctypes.addressof(x) for x in structs])
+    return a, structs, cp, pp
+
+
 class Ensemble:
     """n_steps KDK steps of many boxes recorded as one CUDA graph (cube2_ensemble_*).
 
     ctxs / states: one Context and IOSState per box, forces current.  a: array
-    (n_boxes, n_steps + 1) of scale factors.  The states' tensors are used in
-    place by every launch and must stay alive (this object keeps them)."""
+    (n_boxes, n_steps + 1) of scale factors.  opts: an EnsembleOpts
+    (``ensemble_opts``); without it, n_streams branches of per-box launches.
+    The states' tensors are used in place by every launch and must stay alive
+    (this object keeps them)."""
 
-    def __init__(self, ctxs, states, a, n_streams=8):
-        a = np.ascontiguousarray(a, dtype=np.float64)
-        nb, ns = a.shape[0], a.shape[1] - 1
-        if nb != len(ctxs) or nb != len(states):
-            raise ValueError("one context, state and schedule per box")
+    def __init__(self, ctxs, states, a, n_streams=8, opts=None):
         self.ctxs, self.states = list(ctxs), list(states)
-        self._structs = [st.struct() for st in self.states]
-        cp = (ctypes.c_void_p * nb)(*[c.ptr.value for c in self.ctxs])
-        pp = (ctypes.c_void_p * nb)(*[ctypes.addressof(x) for x in self._structs])
+        a, self._structs, cp, pp = _ensemble_arrays(self.ctxs, self.states, a)
+        nb, ns = a.shape[0], a.shape[1] - 1
+        self.opts = opts if opts is not None else ensemble_opts(n_streams=n_streams)
         ptr = ctypes.c_void_p()
-        code = _lib.cube2_ensemble_create(ctypes.byref(ptr), cp, pp, nb,
-                                          a.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), ns, int(n_streams))
+        code = _lib.cube2_ensemble_create_ex(ctypes.byref(ptr), cp, pp, nb,
+                                             a.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), ns,
+                                             ctypes.byref(self.opts))
         if code != OK:
             msgs = [_lib.cube2_last_error(c.ptr).decode() for c in self.ctxs]
             raise Cube2Error(code, "; ".join(m for m in msgs if m) or "ensemble_create")
@@ -531,6 +570,19 @@ class Ensemble:
         code = _lib.cube2_ensemble_launch(self.ptr, ctypes.c_void_p(st.cuda_stream))
         if code != OK:
             raise Cube2Error(code, "ensemble_launch")
+
+    def check(self, stream=None):
+        """Synchronise; raise Cube2Error(ERR_TIMEOUT) if a persistent kernel gave up waiting."""
+        st = torch.cuda.current_stream() if stream is None else stream
+        code = _lib.cube2_ensemble_check(self.ptr, ctypes.c_void_p(st.cuda_stream))
+        if code != OK:
+            raise Cube2Error(code, "ensemble_check")
+
+    def publish(self, on=True):
+        """Host control of the persistent queue's publication (False withholds it)."""
+        code = _lib.cube2_ensemble_publish(self.ptr, int(bool(on)))
+        if code != OK:
+            raise Cube2Error(code, "ensemble_publish")
 
     def info(self):
         """(kernel nodes in the graph, particle-steps per launch)."""
@@ -550,6 +602,22 @@ class Ensemble:
             self.close()
         except Exception:
             pass
+
+
+def ensemble_autotune(ctxs, states, a, start=None, trials=2, stream=None):
+    """cube2_ensemble_autotune: (fastest EnsembleOpts, its ms per launch); the
+    boxes' states are left as they were."""
+    a, _structs, cp, pp = _ensemble_arrays(list(ctxs), list(states), a)
+    best = start if start is not None else ensemble_opts()
+    best = EnsembleOpts(best.n_streams, best.persistent_pp, best.pp_ctas_per_sm, best.pp_wmax, best.timeout_ms)
+    ms = ctypes.c_double()
+    st = torch.cuda.current_stream() if stream is None else stream
+    code = _lib.cube2_ensemble_autotune(cp, pp, a.shape[0], a.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                        a.shape[1] - 1, int(trials), ctypes.c_void_p(st.cuda_stream),
+                                        ctypes.byref(best), ctypes.byref(ms))
+    if code != OK:
+        raise Cube2Error(code, "ensemble_autotune")
+    return best, ms.value
 
 
 def kdk_factors(cfg: Config, a0, a1):
@@ -633,10 +701,9 @@ class FinalDensity(torch.autograd.Function):
 
     Forward: cube2_ios_from_positions, the force, the steps (a checkpoint and
     re-bin map kept per step), cube2_deposit of the final state.  Backward, for
-    a cotangent g on the density: cube2_density_mse_vjp with the target
-    delta - g n^3 / 2 (its cotangent 2 (delta - target) / n^3 is then g), the
-    reverse sweep cube2_kdk_adjoint, and the gradients put back into the input
-    order through the placement's permutation.  The IOS quantisation of x0 and
+    a cotangent g on the density: cube2_density_vjp (the position gradient of
+    <g, delta>), the reverse sweep cube2_kdk_adjoint, and the gradients put
+    back into the input order through the placement's permutation.  The IOS quantisation of x0 and
     the drift's rounding are taken as the identity (the gradient of the
     continuous map at the stored positions)."""
 
@@ -660,9 +727,7 @@ class FinalDensity(torch.autograd.Function):
     @staticmethod
     def backward(fctx, g):
         ctx, a, level, states, perms, perm, delta = fctx.sim
-        n3 = delta.numel()
-        target = (delta - g.to(delta.dtype) * (n3 / 2.0)).contiguous()
-        _, xbar = ctx.density_mse_vjp(level, states[-1], target)
+        xbar = ctx.density_vjp(level, states[-1], g.to(delta.dtype))
         pbar = torch.zeros_like(xbar)
         ctx.kdk_adjoint(states, perms, a, xbar, pbar)
         idx = perm.long()

@@ -130,3 +130,16 @@ def test_loss_gradient_matches_finite_differences():
         assert abs(gx[d, i] - fd) <= 1e-6 * np.abs(gx).max(), (i, d, gx[d, i], fd)
         fdp = (lossf(x0, p0 + e) - lossf(x0, p0 - e)) / (2 * eps)
         assert abs(gp[d, i] - fdp) <= 1e-6 * np.abs(gp).max(), (i, d, gp[d, i], fdp)
+
+
+def test_cell_list_pairs_equal_all_pairs():
+    # the cell list the continuous-position PP uses beyond 4096 particles
+    # finds exactly the pairs of the all-pairs search
+    rng = np.random.default_rng(12)
+    box, b_cut = 20.0, 1.3
+    x = np.concatenate([rng.uniform(0, box, (3, 1500)), (7.0 + rng.normal(0, 0.8, (3, 500))) % box], axis=1)
+    i0, j0, d0, r0 = A._pairs(x, box, b_cut)
+    i1, j1, d1, r1 = A._pairs_cells(x, box, b_cut)
+    k0, k1 = np.lexsort((j0, i0)), np.lexsort((j1, i1))
+    assert np.array_equal(i0[k0], i1[k1]) and np.array_equal(j0[k0], j1[k1])
+    assert np.array_equal(d0[:, k0], d1[:, k1]) and np.array_equal(r0[k0], r1[k1])
