@@ -299,6 +299,7 @@ struct PPWarpShared {
     struct {
         float4 buf[64];   // staged sources of the union path
         WarpSegs seg;
+        float box[8];     // the warp's target bounding box (lo x, y, z, hi x, y, z) and largest squared range
     } u;
 };
 
@@ -372,75 +373,111 @@ __device__ int build_segments(const PPParams &P, WarpSegs &W, int c0, int xa, in
     return W.cum[PP_SEGS];
 }
 
-__device__ void union_path(const PPParams &P, const WarpSegs &W, float4 *S, int64_t i, bool has, int c0, int xa,
-                           float4 me, float bcut2, float ibc, Sum3 &a, unsigned &pairs, unsigned &cands) {
-    const int lane = threadIdx.x & 31;
-    const int n = P.n_ios;
-    const int total = W.cum[PP_SEGS];
-    // own particle's stream position (row (0, 0) main segment is s = 8)
-    const int pself = has ? W.cum[8] + (int)(i - W.beg[8]) : -1000;
-    const int cx = (has ? __float_as_int(me.w) : c0) % n;
-    const float mx = (float)(cx - xa) + me.x, my = me.y + 1.0f, mz = me.z + 1.0f;
-    const float bpp2 = P.bpp2, ibp = P.inv_bpp;
-    int sa = 0, sb = 0;
-    for (int b0 = 0; b0 < total; b0 += 64) {
-        S[lane] = stage_source(P, W, b0 + lane, sa);
-        S[32 + lane] = stage_source(P, W, b0 + 32 + lane, sb);
-        if (has) cands += (unsigned)min(64, total - b0);
-        __syncwarp();
-        unsigned mh = test32(S, mx, my, mz, bcut2), ml = test32(S + 32, mx, my, mz, bcut2);
-        const int ts = pself - b0;
-        if (ts >= 0 && ts < 32) mh &= ~(0x80000000u >> ts);
-        if (ts >= 32 && ts < 64) ml &= ~(0x80000000u >> (ts - 32));
-        if (!has) mh = ml = 0u;
-        pairs += __popc(mh) + __popc(ml);
-        float px = 0.f, py = 0.f, pz = 0.f;
-        unsigned ch = 0u, cl = 0u;   // pairs closer than b_pp
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            unsigned m = h ? ml : mh;
-            const float4 *SB = S + 32 * h;
-            unsigned cm = 0u;
-            while (m) {
-                const int k = __clz(m);
-                const unsigned bit = 0x80000000u >> k;
-                m ^= bit;
-                const float4 q = SB[k];
-                const float rx = q.x - mx, ry = q.y - my, rz = q.z - mz;
-                const float r2 = rx * rx + ry * ry + rz * rz;
-                const float g = far_pair(r2, ibc, bpp2);
-                if (r2 < bpp2) cm |= bit;
+// Test of 32 staged sources by every lane and evaluation of the set bits (the
+// pairs in range), far pairs first, the rare pairs closer than b_pp after.
+__device__ __forceinline__ void eval32(const float4 *S, float mx, float my, float mz, float bcut2, float ibc,
+                                       float bpp2, float ibp, float coef, bool has, Sum3 &a, unsigned &pairs) {
+    unsigned m = has ? test32(S, mx, my, mz, bcut2) : 0u;
+    pairs += __popc(m);
+    float px = 0.f, py = 0.f, pz = 0.f;
+    unsigned cm = 0u;   // pairs closer than b_pp
+    while (m) {
+        const int k = __clz(m);
+        const unsigned bit = 0x80000000u >> k;
+        m ^= bit;
+        const float4 q = S[k];
+        const float rx = q.x - mx, ry = q.y - my, rz = q.z - mz;
+        const float r2 = rx * rx + ry * ry + rz * rz;
+        const float g = far_pair(r2, ibc, bpp2);
+        if (r2 < bpp2) cm |= bit;
+        px = fmaf(g, rx, px);
+        py = fmaf(g, ry, py);
+        pz = fmaf(g, rz, pz);
+    }
+    if (__any_sync(0xffffffffu, cm != 0u)) {
+        while (cm) {
+            const int k = __clz(cm);
+            cm ^= 0x80000000u >> k;
+            const float4 q = S[k];
+            const float rx = q.x - mx, ry = q.y - my, rz = q.z - mz;
+            const float r2 = rx * rx + ry * ry + rz * rz;
+            if (r2 > 0.0f) {
+                const float g = close_pair(r2, ibp, ibc);
                 px = fmaf(g, rx, px);
                 py = fmaf(g, ry, py);
                 pz = fmaf(g, rz, pz);
-            }
-            if (h) cl = cm; else ch = cm;
-        }
-        if (__any_sync(0xffffffffu, (ch | cl) != 0u)) {
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                unsigned cm = h ? cl : ch;
-                const float4 *SB = S + 32 * h;
-                while (cm) {
-                    const int k = __clz(cm);
-                    cm ^= 0x80000000u >> k;
-                    const float4 q = SB[k];
-                    const float rx = q.x - mx, ry = q.y - my, rz = q.z - mz;
-                    const float r2 = rx * rx + ry * ry + rz * rz;
-                    if (r2 > 0.0f) {
-                        const float g = close_pair(r2, ibp, ibc);
-                        px = fmaf(g, rx, px);
-                        py = fmaf(g, ry, py);
-                        pz = fmaf(g, rz, pz);
-                    } else {
-                        --pairs;   // coincident particles: no pair force
-                    }
-                }
+            } else {
+                --pairs;   // the target itself, or a coincident particle: no pair force
             }
         }
-        a.add_block(P.coef * px, P.coef * py, P.coef * pz);
-        __syncwarp();
     }
+    a.add_block(coef * px, coef * py, coef * pz);
+}
+
+// Warps inside one row of cells share one source stream (the cells xa-1 ..
+// xb+1 of the 9 rows around it).  Each source is staged once by one lane and
+// kept only if it lies within the warp's largest PP range of the bounding box
+// of the warp's targets (no pair of it can be in range otherwise); the kept
+// sources are packed in shared memory and every lane tests and evaluates them
+// 32 at a time.  The target itself is in the stream and drops out at r = 0.
+__device__ void union_path(const PPParams &P, const WarpSegs &W, float4 *S, float *box, int64_t i, bool has, int c0,
+                           int xa, float4 me, float bcut2, float ibc, Sum3 &a, unsigned &pairs, unsigned &cands) {
+    (void)i;
+    const int lane = threadIdx.x & 31;
+    const int n = P.n_ios;
+    const int total = W.cum[PP_SEGS];
+    const int cx = (has ? __float_as_int(me.w) : c0) % n;
+    const float mx = (float)(cx - xa) + me.x, my = me.y + 1.0f, mz = me.z + 1.0f;
+    const float bpp2 = P.bpp2, ibp = P.inv_bpp;
+    // bounding box of the warp's targets and the largest squared range
+    float lx = has ? mx : 1e30f, ly = has ? my : 1e30f, lz = has ? mz : 1e30f;
+    float hx = has ? mx : -1e30f, hy = has ? my : -1e30f, hz = has ? mz : -1e30f;
+    float reach2 = has ? bcut2 : 0.0f;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        lx = fminf(lx, __shfl_xor_sync(0xffffffffu, lx, o));
+        ly = fminf(ly, __shfl_xor_sync(0xffffffffu, ly, o));
+        lz = fminf(lz, __shfl_xor_sync(0xffffffffu, lz, o));
+        hx = fmaxf(hx, __shfl_xor_sync(0xffffffffu, hx, o));
+        hy = fmaxf(hy, __shfl_xor_sync(0xffffffffu, hy, o));
+        hz = fmaxf(hz, __shfl_xor_sync(0xffffffffu, hz, o));
+        reach2 = fmaxf(reach2, __shfl_xor_sync(0xffffffffu, reach2, o));
+    }
+    // kept in the warp's shared memory: fewer live registers in the loop
+    if (lane == 0) {
+        box[0] = lx; box[1] = ly; box[2] = lz;
+        box[3] = hx; box[4] = hy; box[5] = hz;
+        box[6] = reach2;
+    }
+    __syncwarp();
+    int fill = 0, sa = 0;
+    for (int b0 = 0; b0 < total; b0 += 32) {
+        const float4 q = stage_source(P, W, b0 + lane, sa);
+        const float dx = fmaxf(fmaxf(box[0] - q.x, q.x - box[3]), 0.0f);
+        const float dy = fmaxf(fmaxf(box[1] - q.y, q.y - box[4]), 0.0f);
+        const float dz = fmaxf(fmaxf(box[2] - q.z, q.z - box[5]), 0.0f);
+        const bool keep = dx * dx + dy * dy + dz * dz < box[6];
+        const unsigned km = __ballot_sync(0xffffffffu, keep);
+        if (keep) S[fill + __popc(km & ((1u << lane) - 1u))] = q;
+        fill += __popc(km);
+        __syncwarp();
+        if (fill >= 32) {
+            if (has) cands += 32u;
+            eval32(S, mx, my, mz, bcut2, ibc, bpp2, ibp, P.coef, has, a, pairs);
+            __syncwarp();
+            const float4 t = S[32 + lane];
+            if (32 + lane < fill) S[lane] = t;
+            fill -= 32;
+            __syncwarp();
+        }
+    }
+    if (fill > 0) {
+        if (lane >= fill) S[lane] = make_float4(1.0e18f, 1.0e18f, 1.0e18f, 0.0f);
+        __syncwarp();
+        if (has) cands += (unsigned)fill;
+        eval32(S, mx, my, mz, bcut2, ibc, bpp2, ibp, P.coef, has, a, pairs);
+    }
+    __syncwarp();
 }
 
 // Warps whose targets span several rows or a wide x range (sparse regions):
@@ -704,7 +741,8 @@ __device__ __forceinline__ void pp_block(const PPParams &P, int64_t block, PPSha
     Sum3 a;
     unsigned pairs = 0, cands = 0;
     if (one_row)
-        union_path(P, sh.w[wib].u.seg, sh.w[wib].u.buf, i, has, c0, xa, me, bcut2, ibc, a, pairs, cands);
+        union_path(P, sh.w[wib].u.seg, sh.w[wib].u.buf, sh.w[wib].u.box, i, has, c0, xa, me, bcut2, ibc, a, pairs,
+                   cands);
     else
         lane_path(P, has, c, me, bcut2, ibc, a, pairs, cands);
     if (has) finish(P, P.perm[i], a.x - a.cx, a.y - a.cy, a.z - a.cz);
