@@ -150,3 +150,56 @@ def test_fused_reverse_sweep_equals_step_by_step():
     ctx.check()
     for u, v in ((xb1, xb2), (pb1, pb2)):
         assert torch.allclose(u, v, rtol=1e-4, atol=1e-4 * v.abs().max().item())
+
+
+def test_gradient_on_the_differentiation_schedule_matches_oracle():
+    """The differentiation workload's layout and schedule (1 Mpc/h per
+    particle, a mesh of 2 cells per particle with a 2-cell softening, 10
+    constant-Delta-a KDK steps z = 9 -> 0, density MSE loss against the final
+    density of the seed-4 realisation) at 32^3 particles: the GPU gradient
+    with respect to the initial positions and momenta against the FP64
+    oracle's reverse sweep over its continuous trajectory (the oracle's
+    gradient equals central differences of its loss to 1e-6,
+    test_oracle_adjoint).  Bar: 64 random components (32 of dL/dx0, 32 of
+    dL/dp0) within 1e-3 of their own size or of 1e-3 of the rms gradient,
+    the spec bar; the whole arrays' median and 99th percentile are
+    printed."""
+    from inputs.workloads import WORKLOADS
+    from oracle import mesh as M
+    c3 = WORKLOADS["pm1-128c-256mesh"]
+    w = c3.with_(n_p=32, box=32.0, n_ios=32, levels=(Level(64, 2.0),))
+    st = zeldovich_ios(w)
+    n_part = int(st["count"].sum())
+    a = w.scale_factors()
+    assert len(a) == 11 and abs(1.0 / a[0] - 10.0) < 1e-12 and a[-1] == 1.0
+    ctx = cube2.init_mesh(cube2.make_config(w, n_particles=n_part))
+    ctx.set_green(0)
+    ctx.adjoint_init()
+    # target: the final overdensity of the seed-4 realisation, from the oracle's trajectory
+    tgt = zeldovich_ios(w.with_(seed=4))
+    xt = M.positions(tgt["off"], tgt["count"], w.n_ios, w.box)
+    vt = np.asarray(tgt["vel"], dtype=np.float32).astype(np.float64)
+    greens = M.green_tables(w)
+    xf = A.kdk_trajectory(xt, vt, w, greens, a)[-1][0]
+    n = 64
+    h = w.box / n
+    target = A._deposit(A.cic_corners(xf / h, n), np.ones(xf.shape[1]), n) * (n ** 3 / xf.shape[1]) - 1.0
+    p0 = cube2.IOSState.from_numpy(st)
+    ctx.force(p0)
+    loss, gx, gp = cube2.loss_gradient(ctx, p0, torch.from_numpy(target.astype(np.float32)).cuda(), a)
+    ctx.check()
+    x0 = M.positions(st["off"], st["count"], w.n_ios, w.box)
+    v0 = np.asarray(st["vel"], dtype=np.float32).astype(np.float64)
+    lo, ox, op = A.loss_gradient(x0, v0, w, greens, a, target)
+    print(f"differentiation schedule at 32^3: loss GPU {loss:.6e} oracle {lo:.6e}")
+    assert abs(loss - lo) <= 1e-3 * lo
+    rng = np.random.default_rng(64)
+    for name, got, ref in (("dL/dx0", gx.cpu().numpy().astype(np.float64), ox),
+                           ("dL/dp0", gp.cpu().numpy().astype(np.float64), op)):
+        floor = 1e-3 * np.sqrt(np.mean(ref ** 2))
+        rel = np.abs(got - ref) / np.maximum(np.abs(ref), floor)
+        comp = rng.choice(ref.size, 32, replace=False)
+        rs = rel.ravel()[comp]
+        print(f"{name}: all components median {np.median(rel):.2e}, p99 {np.quantile(rel, 0.99):.2e}; "
+              f"32 random components max {rs.max():.2e}")
+        assert rs.max() <= 1e-3, (name, rs.max())
