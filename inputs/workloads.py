@@ -163,8 +163,10 @@ def c4_ensemble(n_boxes=64, seed=100, n_steps=20, sizes=(32, 48, 64, 96)):
 # 0.25 Mpc/h cells (48^3 with its buffer) and softening 2 local cells, which
 # halves their PP range.  The threshold balances a local mesh (about 2 us of
 # deposit and FFT) against the PP pairs it removes (about 2.4 ps each) at the
-# densities this run reaches (a few hundred subtiles by z = 0).
+# densities this run reaches (a few hundred subtiles by z = 0: 392 at the
+# last step).  The capacity bounds the batched FFT grids (blocks of unused
+# meshes return at once, but are still scheduled), so it is sized to the run.
 C2_PM3 = C2.with_(name="pm2-256c-128x512mesh-pm3", pm3=PM3Spec(tile=8, refine=2, beta=2.0, rho_min=512,
-                                                                max_tiles=2048))
+                                                                max_tiles=512))
 
 WORKLOADS = {w.name: w for w in (C1, C2, C2_SMALL, C2_MID, C3, C5, C2_SMALL_TSC, C2_TSC, ISO_PAIRS, C2_PM3)}

@@ -234,10 +234,20 @@ def force_vjp(x, v, wl, greens):
 
 
 # --------------------------------------------------- trajectory and loss
-def kdk_trajectory(x0, p0, wl, greens, a):
+def quantise_drift(x, dx, wl):
+    """x + dx with the displacement rounded to the IOS grid (2^-16 IOS cell,
+    round half to even) and wrapped: the fixed-point drift of Sec. 2.3 on
+    positions that lie on that grid (X + rint(d) = rint(X + d) for integer X)."""
+    q = wl.box / wl.n_ios / FIX
+    return (x + np.rint(dx / q) * q) % wl.box
+
+
+def kdk_trajectory(x0, p0, wl, greens, a, ios=False):
     """KDK steps a[0] -> a[-1] (Sec. 2.2; kick K(a0, ah), drift Dr(a0, a1),
-    kick K(ah, a1), dp/da = 1.5 Omega_m F / (a^2 E)) at continuous positions.
-    Returns the states [(x_k, p_k)] before the first and after every step."""
+    kick K(ah, a1), dp/da = 1.5 Omega_m F / (a^2 E)) at continuous positions,
+    or with ``ios`` on the IOS grid (every drift rounded as ``quantise_drift``;
+    x0 must lie on the grid).  Returns the states [(x_k, p_k)] before the first
+    and after every step."""
     from .kdk import drift_integral, kick_integral
     c = 1.5 * wl.omega_m
     x, p = x0.copy(), p0.copy()
@@ -246,7 +256,8 @@ def kdk_trajectory(x0, p0, wl, greens, a):
     for a0, a1 in zip(a[:-1], a[1:]):
         ah = 0.5 * (a0 + a1)
         pm = p + c * kick_integral(a0, ah, wl.omega_m, wl.omega_l) * f
-        x = (x + drift_integral(a0, a1, wl.omega_m, wl.omega_l) * pm) % wl.box
+        dx = drift_integral(a0, a1, wl.omega_m, wl.omega_l) * pm
+        x = quantise_drift(x, dx, wl) if ios else (x + dx) % wl.box
         f = force(x, wl, greens)
         p = pm + c * kick_integral(ah, a1, wl.omega_m, wl.omega_l) * f
         out.append((x, p))
@@ -276,12 +287,15 @@ def density_loss_grad(x, wl, target):
     return float(np.mean(r ** 2)), w * (n ** 3 / (npart * h))
 
 
-def loss_gradient(x0, p0, wl, greens, a, target):
+def loss_gradient(x0, p0, wl, greens, a, target, ios=False):
     """(L, dL/dx0, dL/dp0) through the KDK steps of ``kdk_trajectory``:
-    reverse mode, step by step, with the force products above."""
+    reverse mode, step by step, with the force products above.  With ``ios``
+    the forward steps round their drifts to the IOS grid and the reverse sweep
+    takes that rounding as the identity (the products are evaluated at the
+    grid positions the trajectory visits)."""
     from .kdk import drift_integral, kick_integral
     c = 1.5 * wl.omega_m
-    traj = kdk_trajectory(x0, p0, wl, greens, a)
+    traj = kdk_trajectory(x0, p0, wl, greens, a, ios=ios)
     loss, xbar = density_loss_grad(traj[-1][0], wl, target)
     pbar = np.zeros_like(xbar)
     for k in range(len(a) - 2, -1, -1):

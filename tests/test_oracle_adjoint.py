@@ -143,3 +143,26 @@ def test_cell_list_pairs_equal_all_pairs():
     k0, k1 = np.lexsort((j0, i0)), np.lexsort((j1, i1))
     assert np.array_equal(i0[k0], i1[k1]) and np.array_equal(j0[k0], j1[k1])
     assert np.array_equal(d0[:, k0], d1[:, k1]) and np.array_equal(r0[k0], r1[k1])
+
+
+def test_ios_trajectory_equals_the_fixed_point_kdk_step():
+    # the adjoint oracle's IOS mode (drifts rounded to the 2^-16 grid) visits
+    # the same positions and momenta as the IOS KDK step of oracle/kdk.py
+    from inputs import C1
+    from inputs.zeldovich import zeldovich_ios
+    from oracle import kdk as KD
+    w = C1.with_(n_p=16, box=32.0, n_ios=16, levels=(Level(32, 2.0),), b_pp=0.2)
+    st = zeldovich_ios(w)
+    greens = M.green_tables(w)
+    a0 = 1.0 / (1.0 + w.z_init)
+    a = [a0 + k * (1.0 - a0) / 50 for k in range(4)]
+    x0 = M.positions(st["off"], st["count"], w.n_ios, w.box)
+    v0 = np.asarray(st["vel"], dtype=np.float32).astype(np.float64)
+    xf, pf = A.kdk_trajectory(x0, v0, w, greens, a, ios=True)[-1]
+    state = dict(off=st["off"], count=st["count"], start=st["start"], vel=v0, acc=None)
+    for k in range(3):
+        state = KD.kdk_step(state, w, a[k], a[k + 1], greens)
+    xk = M.positions(state["off"], state["count"], w.n_ios, w.box)
+    i1, i2 = np.lexsort(xf[::-1]), np.lexsort(xk[::-1])
+    assert np.array_equal(xf[:, i1], xk[:, i2])
+    assert np.allclose(pf[:, i1], state["vel"][:, i2], rtol=1e-10, atol=1e-12 * np.abs(pf).max())
