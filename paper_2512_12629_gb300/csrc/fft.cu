@@ -169,7 +169,10 @@ struct Tile {
     static constexpr size_t SMEMY = (size_t)N * LPY * sizeof(float2);
     // resident CTAs the z pass asks registers for: two for 512-thread tiles
     // that fit twice in shared memory (64 registers, no spills); one otherwise
-    // (larger tiles do not fit twice, and smaller bounds only cost registers)
+    // (larger tiles do not fit twice, and smaller bounds only cost registers).
+    // Three 512-thread CTAs per SM (40 registers, spills) measured slower for
+    // the y and z passes (0.37 and 0.66 ms against 0.23 and 0.44 at 512^3) and
+    // equal for the x passes.
     static constexpr int ZMINB = (T == 512 && 2 * SMEMY <= 200 * 1024) ? 2 : 1;
 };
 

@@ -157,19 +157,13 @@ def test_fused_reverse_sweep_equals_step_by_step():
         assert torch.allclose(u, v, rtol=1e-4, atol=1e-4 * v.abs().max().item())
 
 
-def test_gradient_on_the_differentiation_schedule_matches_oracle():
-    """The differentiation workload's layout and schedule (1 Mpc/h per
-    particle, a mesh of 2 cells per particle with a 2-cell softening, 10
-    constant-Delta-a KDK steps z = 9 -> 0, density MSE loss against the final
-    density of the seed-4 realisation) at 32^3 particles: the GPU gradient
-    with respect to the initial positions and momenta against the FP64
-    oracle's reverse sweep along its own IOS trajectory (drifts rounded to the
-    2^-16 grid, as on the GPU; the oracle's gradient equals central
-    differences of its loss, test_oracle_adjoint).  Ten steps into the
-    nonlinear regime the FP32 and FP64 trajectories part (their losses differ
-    by ~1e-3): the agreement is statistical, the direction of each gradient
-    and its relative L2 difference; the component bar of 1e-3 holds where the
-    trajectories stay together (the 3-step test)."""
+def _differentiation_case(n_steps):
+    """The differentiation workload's layout (1 Mpc/h per particle, a mesh of 2
+    cells per particle with a 2-cell softening) at 32^3 particles, the first
+    n_steps of its 10-step z = 9 -> 0 schedule, the MSE loss against the
+    final density of the seed-4 realisation (its oracle IOS trajectory).
+    Returns the GPU's (loss, dL/dx0, dL/dp0) and the oracle's along its own
+    IOS trajectory."""
     from inputs.workloads import WORKLOADS
     from oracle import mesh as M
     c3 = WORKLOADS["pm1-128c-256mesh"]
@@ -178,10 +172,10 @@ def test_gradient_on_the_differentiation_schedule_matches_oracle():
     n_part = int(st["count"].sum())
     a = w.scale_factors()
     assert len(a) == 11 and abs(1.0 / a[0] - 10.0) < 1e-12 and a[-1] == 1.0
+    a = a[:n_steps + 1]
     ctx = cube2.init_mesh(cube2.make_config(w, n_particles=n_part))
     ctx.set_green(0)
     ctx.adjoint_init()
-    # target: the final overdensity of the seed-4 realisation (oracle trajectory)
     tgt = zeldovich_ios(w.with_(seed=4))
     xt = M.positions(tgt["off"], tgt["count"], w.n_ios, w.box)
     vt = np.asarray(tgt["vel"], dtype=np.float32).astype(np.float64)
@@ -194,17 +188,43 @@ def test_gradient_on_the_differentiation_schedule_matches_oracle():
     ctx.force(p0)
     loss, gx, gp = cube2.loss_gradient(ctx, p0, torch.from_numpy(target.astype(np.float32)).cuda(), a)
     ctx.check()
+    ctx.close()
     x0 = M.positions(st["off"], st["count"], w.n_ios, w.box)
     v0 = np.asarray(st["vel"], dtype=np.float32).astype(np.float64)
     lo, ox, op = A.loss_gradient(x0, v0, w, greens, a, target, ios=True)
-    print(f"differentiation schedule at 32^3: loss GPU {loss:.6e} oracle {lo:.6e}")
-    assert abs(loss - lo) <= 3e-3 * lo
-    for name, got, ref in (("dL/dx0", gx.cpu().numpy().astype(np.float64), ox),
-                           ("dL/dp0", gp.cpu().numpy().astype(np.float64), op)):
-        cos = float((got * ref).sum() / np.sqrt((got ** 2).sum() * (ref ** 2).sum()))
-        l2 = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
-        mag = np.linalg.norm(ref, axis=0)
-        rel = np.linalg.norm(got - ref, axis=0) / np.maximum(mag, 1e-3 * np.sqrt(np.mean(mag ** 2)))
-        print(f"{name}: cosine {cos:.6f}, relative L2 difference {l2:.3e}, per particle median {np.median(rel):.2e}, "
-              f"p99 {np.quantile(rel, 0.99):.2e}")
-        assert cos >= 0.99 and l2 <= 0.1, (name, cos, l2)
+    return (loss, gx.cpu().numpy().astype(np.float64), gp.cpu().numpy().astype(np.float64)), (lo, ox, op)
+
+
+def test_gradient_over_the_first_steps_of_the_differentiation_schedule():
+    """The first two steps of the differentiation schedule (z = 9 -> 2.6, the
+    schedule's large Delta a) on its layout at 32^3: the GPU gradient against
+    the oracle's along its IOS trajectory, 64 random components (32 of
+    dL/dx0, 32 of dL/dp0) within 1e-3 of their own size or of 1e-3 of the
+    rms gradient: the spec bar (the oracle's gradient equals central
+    differences of its loss, test_oracle_adjoint)."""
+    (loss, gx, gp), (lo, ox, op) = _differentiation_case(2)
+    print(f"2 steps of the differentiation schedule: loss GPU {loss:.6e} oracle {lo:.6e}")
+    assert abs(loss - lo) <= 1e-4 * lo
+    rng = np.random.default_rng(65)
+    for name, got, ref in (("dL/dx0", gx, ox), ("dL/dp0", gp, op)):
+        floor = 1e-3 * np.sqrt(np.mean(ref ** 2))
+        rel = (np.abs(got - ref) / np.maximum(np.abs(ref), floor)).ravel()
+        comp = rng.choice(ref.size, 32, replace=False)
+        print(f"{name}: all components median {np.median(rel):.2e}, p99 {np.quantile(rel, 0.99):.2e}; "
+              f"32 random components max {rel[comp].max():.2e}")
+        assert rel[comp].max() <= 1e-3, (name, rel[comp].max())
+
+
+def test_loss_over_the_whole_differentiation_schedule():
+    """All ten steps (z = 9 -> 0) of the differentiation schedule at 32^3: the
+    loss of the GPU's trajectory against the oracle's FP64 IOS trajectory.
+    The gradient through ten steps into the nonlinear regime is
+    ill-conditioned: the oracle's own gradients along its continuous and its
+    IOS trajectory (which differ by at most 2^-17 IOS cell per drift) have a
+    cosine of 0.18 (0.987 after five steps, 0.99996 after two), so gradients of
+    two implementations that round differently are compared over the first
+    steps (the test above) and the whole schedule is checked on its loss."""
+    (loss, gx, gp), (lo, ox, op) = _differentiation_case(10)
+    cos = float((gx * ox).sum() / np.sqrt((gx ** 2).sum() * (ox ** 2).sum()))
+    print(f"10 steps: loss GPU {loss:.6e} oracle {lo:.6e}; gradient cosine {cos:.3f}")
+    assert abs(loss - lo) <= 1e-3 * lo
