@@ -98,12 +98,13 @@ typedef struct {
      * gets a local periodic mesh of spacing H_3 = H_finest / pm3_refine over
      * the subtile plus a buffer of B = ceil(b_finest / H_3) + 4 cells on each
      * side (m = the smallest 2^a 3^b >= pm3_tile s_ios / H_3 + 2 B cells, which
-     * must be a supported mesh size), softening b_3 = pm3_beta H_3 and the
+     * must be a supported mesh size of at most 256), softening b_3 = pm3_beta H_3 and the
      * kernel R(r, b_3) - R(r, b_finest); its own particles get that force and
      * a PP range of b_3 instead of b_finest.  pm3_refine: a power of two with
      * H_3 <= s_ios; b_pp < b_3 < b_finest.  At most pm3_max_tiles subtiles are
      * refined per force evaluation (the first in subtile order, x fastest);
-     * the rest keep the two-level method.                                    */
+     * the rest keep the two-level method.  The capacity actually allocated is
+     * min(pm3_max_tiles, subtiles, 65535) (cube2_pm3_info reports it).        */
     int32_t pm3_tile;
     int32_t pm3_refine;
     double  pm3_beta;
@@ -175,7 +176,7 @@ int cube2_set_green(cube2_ctx *ctx, int level, const char *cache_path);
  * context with the third level (CUBE2_ERR_STATE).
  *
  * cube2_pm3_info: out = {pm3_tile, subtiles per dimension, refinement r,
- * buffer B, mesh m, H_3 [Mpc/h], b_3 [Mpc/h], pm3_max_tiles} (host only;
+ * buffer B, mesh m, H_3 [Mpc/h], b_3 [Mpc/h], local mesh capacity} (host only;
  * CUBE2_ERR_STATE when the third level is off).
  * cube2_pm3_stats: synchronises; out = {local meshes in use, subtiles that
  * asked for refinement} of the last force or PP call.

@@ -140,7 +140,6 @@ void free_ctx(cube2_ctx *c) {
     cudaFree(c->pm3.lev.spec);
     cudaFree(c->pm3.lev.green);
     cudaFree(c->pm3.lev.tw);
-    cudaFree(c->pm3.acc);
     cudaFree(c->pm3.rho_max);
     cudaFree(c->pm3.slot);
     cudaFree(c->pm3.list);
@@ -196,7 +195,8 @@ std::string pm3_geometry(cube2_ctx *c) {
     M.r = r;
     M.q_shift = q_shift;
     M.rho_min = cfg->pm3_rho_min;
-    M.max_tiles = cfg->pm3_max_tiles;
+    // more slots than subtiles would never be filled; the slot is a grid dimension
+    M.max_tiles = (int)std::min<int64_t>(std::min<int64_t>(cfg->pm3_max_tiles, M.n_sub), 65535);
     M.H = F.H / r;
     M.b3 = cfg->pm3_beta * M.H;
     if (!(M.b3 < c->b_range) || !(M.b3 > cfg->b_pp)) return "Bthe third level's softening must lie between b_pp and the PP range";
@@ -206,7 +206,8 @@ std::string pm3_geometry(cube2_ctx *c) {
     for (int64_t a = 1; a <= (int64_t)1 << 20; a *= 2)
         for (int64_t v = a; v <= (int64_t)1 << 22; v *= 3)
             if (v >= need && (best < 0 || v < best)) best = v;
-    if (best < 0 || !fft_size_supported((int)best)) return "Uthe third level's local mesh size is not supported";
+    if (best < 0 || best > 256 || !fft_size_supported((int)best))
+        return "Uthe third level's local mesh size is not supported (batched local meshes go up to 256)";
     M.m = (int)best;
     if (M.m * M.H > cfg->box * (1.0 + 1e-12)) return "Bthe third level's local box exceeds the simulation box";
     const int64_t m3 = (int64_t)M.m * M.m * M.m;
@@ -342,13 +343,11 @@ int cube2_init_mesh(cube2_ctx **out, const cube2_config *cfg, void *stream) {
         L.green_len = green_table_len(L.n);
         alloc((void **)&L.green, (size_t)L.green_len * sizeof(float));
         alloc((void **)&L.tw, (size_t)L.n * sizeof(float2));
-        alloc((void **)&M.acc, (size_t)M.max_tiles * m3 * sizeof(unsigned long long));
         alloc((void **)&M.rho_max, (size_t)M.n_sub * 4);
         alloc((void **)&M.slot, (size_t)M.n_sub * 4);
         alloc((void **)&M.list, (size_t)M.max_tiles * 4);
         alloc((void **)&M.count, 2 * sizeof(int));
         if (e == cudaSuccess) e = cudaMemsetAsync(L.spec, 0, (size_t)M.max_tiles * nh * sizeof(float2), c->stream);
-        if (e == cudaSuccess) e = cudaMemsetAsync(M.acc, 0, (size_t)M.max_tiles * m3 * 8, c->stream);
         if (e == cudaSuccess) e = cudaMemsetAsync(M.count, 0, 2 * sizeof(int), c->stream);
         if (e == cudaSuccess) e = cudaMemsetAsync(M.slot, 0xff, (size_t)M.n_sub * 4, c->stream);
         L.active = M.count;

@@ -75,7 +75,6 @@ struct PM3 {
     double b3 = 0;           // softening b_3 = beta_3 H_3 [Mpc/h]; PP range of refined subtiles
     float dens_scale = 0;    // RN32(V_p / H_3^3 2^-48)
     Level lev;               // batched meshes: real/spec [max_tiles] meshes, Green's table, twiddles
-    unsigned long long *acc = nullptr;   // [max_tiles][m^3] exact CIC accumulators (kept zero between uses)
     int32_t *rho_max = nullptr;          // [n_sub] densest IOS cell per subtile
     int32_t *slot = nullptr;             // [n_sub] local mesh of each subtile, -1 = not refined
     int32_t *list = nullptr;             // [max_tiles] subtile of each local mesh

@@ -23,6 +23,7 @@
 // exp(-2 pi i k/n) built from FP64 sincospi.
 #include "common.cuh"
 
+#include <algorithm>
 #include <string>
 
 namespace cube2 {
@@ -183,14 +184,15 @@ __device__ __forceinline__ void cp_async16(void *smem_dst, const void *gsrc) {
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
 // ---------------------------------------------------------------- X passes
+// Each pass is a per-block body with two entry kernels: one block per tile for
+// a single mesh (BATCH = false), or, for the batched meshes of the adaptive
+// third level (BATCH = true), a resident-sized grid whose blocks loop over the
+// tiles of the meshes in use (*active, on the device).
 template <int N>
-__global__ void __launch_bounds__(Tile<N>::T) fft_x_r2c(const float *__restrict__ in, float2 *__restrict__ out,
-                                                       int64_t nrows, int kxp, const float2 *__restrict__ tw,
-                                                       const int *__restrict__ active) {
+__device__ __forceinline__ void x_r2c_block(float2 *S, const float *__restrict__ in, float2 *__restrict__ out,
+                                            int64_t nrows, int kxp, const float2 *__restrict__ tw, int64_t vb) {
     constexpr int L = Tile<N>::L, LP = Tile<N>::LP, T = Tile<N>::T;
-    extern __shared__ float2 S[];
-    const int64_t row0 = (int64_t)blockIdx.x * 2 * L;
-    if (active && row0 / ((int64_t)N * N) >= *active) return;   // batched meshes not in use
+    const int64_t row0 = vb * 2 * L;
     for (int i = threadIdx.x; i < 2 * L * N; i += T) {
         const int r = i / N, x = i % N;
         const int64_t row = row0 + r;
@@ -212,14 +214,28 @@ __global__ void __launch_bounds__(Tile<N>::T) fft_x_r2c(const float *__restrict_
     }
 }
 
-template <int N>
-__global__ void __launch_bounds__(Tile<N>::T) fft_x_c2r(const float2 *__restrict__ in, float *__restrict__ out,
+template <int N, bool BATCH>
+__global__ void __launch_bounds__(Tile<N>::T) fft_x_r2c(const float *__restrict__ in, float2 *__restrict__ out,
                                                        int64_t nrows, int kxp, const float2 *__restrict__ tw,
                                                        const int *__restrict__ active) {
-    constexpr int L = Tile<N>::L, LP = Tile<N>::LP, T = Tile<N>::T;
     extern __shared__ float2 S[];
-    const int64_t row0 = (int64_t)blockIdx.x * 2 * L;
-    if (active && row0 / ((int64_t)N * N) >= *active) return;
+    if constexpr (BATCH) {
+        constexpr int L = Tile<N>::L;
+        const int64_t nvb = ((int64_t)*active * N * N + 2 * L - 1) / (2 * L);
+        for (int64_t vb = blockIdx.x; vb < nvb; vb += gridDim.x) {
+            x_r2c_block<N>(S, in, out, nrows, kxp, tw, vb);
+            __syncthreads();
+        }
+    } else {
+        x_r2c_block<N>(S, in, out, nrows, kxp, tw, blockIdx.x);
+    }
+}
+
+template <int N>
+__device__ __forceinline__ void x_c2r_block(float2 *S, const float2 *__restrict__ in, float *__restrict__ out,
+                                            int64_t nrows, int kxp, const float2 *__restrict__ tw, int64_t vb) {
+    constexpr int L = Tile<N>::L, LP = Tile<N>::LP, T = Tile<N>::T;
+    const int64_t row0 = vb * 2 * L;
     constexpr int NH = N / 2 + 1;
     for (int i = threadIdx.x; i < L * NH; i += T) {
         const int l = i / NH, k = i % NH;
@@ -239,16 +255,31 @@ __global__ void __launch_bounds__(Tile<N>::T) fft_x_c2r(const float2 *__restrict
     }
 }
 
+template <int N, bool BATCH>
+__global__ void __launch_bounds__(Tile<N>::T) fft_x_c2r(const float2 *__restrict__ in, float *__restrict__ out,
+                                                       int64_t nrows, int kxp, const float2 *__restrict__ tw,
+                                                       const int *__restrict__ active) {
+    extern __shared__ float2 S[];
+    if constexpr (BATCH) {
+        constexpr int L = Tile<N>::L;
+        const int64_t nvb = ((int64_t)*active * N * N + 2 * L - 1) / (2 * L);
+        for (int64_t vb = blockIdx.x; vb < nvb; vb += gridDim.x) {
+            x_c2r_block<N>(S, in, out, nrows, kxp, tw, vb);
+            __syncthreads();
+        }
+    } else {
+        x_c2r_block<N>(S, in, out, nrows, kxp, tw, blockIdx.x);
+    }
+}
+
 // ---------------------------------------------------------------- Y passes
 template <int N, bool INV>
-__global__ void __launch_bounds__(Tile<N>::T) fft_y(float2 *__restrict__ data, int kxp, const float2 *__restrict__ tw,
-                                                   const int *__restrict__ active) {
+__device__ __forceinline__ void y_block(float2 *S, float2 *__restrict__ data, int kxp, const float2 *__restrict__ tw,
+                                        int64_t vb) {
     constexpr int L = Tile<N>::L, LP = Tile<N>::LPY, T = Tile<N>::T;
-    extern __shared__ __align__(16) float2 S[];
     const int tiles_x = kxp / L;
-    const int tx = blockIdx.x % tiles_x;
-    const int64_t z = blockIdx.x / tiles_x;             // plane over all batched meshes
-    if (active && z / N >= *active) return;
+    const int tx = (int)(vb % tiles_x);
+    const int64_t z = vb / tiles_x;                    // plane over all batched meshes
     float2 *base = data + z * N * kxp + tx * L;
     for (int i = threadIdx.x; i < N * L / 2; i += T) {
         const int y = i / (L / 2), l2 = 2 * (i % (L / 2));
@@ -263,20 +294,33 @@ __global__ void __launch_bounds__(Tile<N>::T) fft_y(float2 *__restrict__ data, i
     }
 }
 
+template <int N, bool INV, bool BATCH>
+__global__ void __launch_bounds__(Tile<N>::T) fft_y(float2 *__restrict__ data, int kxp, const float2 *__restrict__ tw,
+                                                   const int *__restrict__ active) {
+    extern __shared__ __align__(16) float2 S[];
+    if constexpr (BATCH) {
+        const int64_t nvb = (int64_t)*active * N * (kxp / Tile<N>::L);
+        for (int64_t vb = blockIdx.x; vb < nvb; vb += gridDim.x) {
+            y_block<N, INV>(S, data, kxp, tw, vb);
+            __syncthreads();
+        }
+    } else {
+        y_block<N, INV>(S, data, kxp, tw, blockIdx.x);
+    }
+}
+
 // ------------------------------------------------------------ Z (+ Green)
 // GMODE 0: forward z FFT only; 1: G from a full [kz][ky][kxp] table; 2: G
 // from the symmetry-reduced table (green_index).
 template <int N, int GMODE>
-__global__ void __launch_bounds__(Tile<N>::T, Tile<N>::ZMINB) fft_z(float2 *__restrict__ data, const float *__restrict__ green,
-                                                   int kxp, const float2 *__restrict__ tw, const int *__restrict__ active) {
+__device__ __forceinline__ void z_block(float2 *S, float2 *__restrict__ data, const float *__restrict__ green,
+                                        int kxp, const float2 *__restrict__ tw, int64_t vb) {
     constexpr int L = Tile<N>::L, LP = Tile<N>::LPY, T = Tile<N>::T;
-    extern __shared__ __align__(16) float2 S[];
     const int tiles_x = kxp / L;
-    const int tx = blockIdx.x % tiles_x;
-    const int64_t row = blockIdx.x / tiles_x;             // (mesh, ky) over all batched meshes
+    const int tx = (int)(vb % tiles_x);
+    const int64_t row = vb / tiles_x;                     // (mesh, ky) over all batched meshes
     const int64_t mesh = row / N;
     const int64_t ky = row - mesh * N;
-    if (active && mesh >= *active) return;
     const int64_t zstride = (int64_t)N * kxp;
     float2 *base = data + mesh * N * zstride + ky * kxp + tx * L;
     for (int i = threadIdx.x; i < N * L / 2; i += T) {
@@ -314,66 +358,114 @@ __global__ void __launch_bounds__(Tile<N>::T, Tile<N>::ZMINB) fft_z(float2 *__re
     }
 }
 
+template <int N, int GMODE, bool BATCH>
+__global__ void __launch_bounds__(Tile<N>::T, Tile<N>::ZMINB) fft_z(float2 *__restrict__ data, const float *__restrict__ green,
+                                                   int kxp, const float2 *__restrict__ tw, const int *__restrict__ active) {
+    extern __shared__ __align__(16) float2 S[];
+    if constexpr (BATCH) {
+        const int64_t nvb = (int64_t)*active * N * (kxp / Tile<N>::L);
+        for (int64_t vb = blockIdx.x; vb < nvb; vb += gridDim.x) {
+            z_block<N, GMODE>(S, data, green, kxp, tw, vb);
+            __syncthreads();
+        }
+    } else {
+        z_block<N, GMODE>(S, data, green, kxp, tw, blockIdx.x);
+    }
+}
+
+// Grid of a pass: every block for a single mesh; for batched meshes a
+// resident-sized grid that loops over the blocks of the meshes in use.
+inline unsigned pass_grid(const cube2_ctx *ctx, const Level &Lv, int64_t blocks) {
+    return (unsigned)(Lv.active ? std::min<int64_t>(blocks, (int64_t)ctx->num_sms * 16) : blocks);
+}
+
+// the batched variants exist for the local meshes of the adaptive third level
+constexpr int BATCH_MAX_N = 256;
+
 template <int N>
 struct Launcher {
-    static cudaError_t forward(cube2_ctx *ctx, Level &Lv) {
-        setup();
+    template <bool B>
+    static cudaError_t forward_v(cube2_ctx *ctx, Level &Lv) {
         const int64_t nrows = (int64_t)Lv.batch * N * N;
-        const unsigned bx = (unsigned)((nrows + 2 * Tile<N>::L - 1) / (2 * Tile<N>::L));
-        const int cls = Lv.active ? -1 : 0;   // batched meshes are profiled as one group by the caller
+        const unsigned bx = pass_grid(ctx, Lv, (nrows + 2 * Tile<N>::L - 1) / (2 * Tile<N>::L));
         {
-            ProfScope prof(ctx, cls < 0 ? -1 : P_FFT_X_FWD, Lv.index);
-            fft_x_r2c<N><<<bx, Tile<N>::T, Tile<N>::SMEM, ctx->stream>>>(Lv.real, Lv.spec, nrows, Lv.kxp, Lv.tw,
-                                                                         Lv.active);
+            ProfScope prof(ctx, B ? -1 : P_FFT_X_FWD, Lv.index);   // batched meshes: profiled as one group by the caller
+            fft_x_r2c<N, B><<<bx, Tile<N>::T, Tile<N>::SMEM, ctx->stream>>>(Lv.real, Lv.spec, nrows, Lv.kxp, Lv.tw,
+                                                                            Lv.active);
         }
-        const unsigned by = (unsigned)((int64_t)Lv.batch * N * (Lv.kxp / Tile<N>::L));
+        const unsigned by = pass_grid(ctx, Lv, (int64_t)Lv.batch * N * (Lv.kxp / Tile<N>::L));
         {
-            ProfScope prof(ctx, cls < 0 ? -1 : P_FFT_Y_FWD, Lv.index);
-            fft_y<N, false><<<by, Tile<N>::T, Tile<N>::SMEMY, ctx->stream>>>(Lv.spec, Lv.kxp, Lv.tw, Lv.active);
+            ProfScope prof(ctx, B ? -1 : P_FFT_Y_FWD, Lv.index);
+            fft_y<N, false, B><<<by, Tile<N>::T, Tile<N>::SMEMY, ctx->stream>>>(Lv.spec, Lv.kxp, Lv.tw, Lv.active);
         }
         ctx->launches += 2;
         return cudaGetLastError();
     }
-    static cudaError_t z_pass(cube2_ctx *ctx, Level &Lv, bool green) {
-        setup();
-        const unsigned bz = (unsigned)((int64_t)Lv.batch * N * (Lv.kxp / Tile<N>::L));
-        ProfScope prof(ctx, Lv.active ? -1 : P_FFT_Z_GREEN, Lv.index);
+    template <bool B>
+    static cudaError_t z_pass_v(cube2_ctx *ctx, Level &Lv, bool green) {
+        const unsigned bz = pass_grid(ctx, Lv, (int64_t)Lv.batch * N * (Lv.kxp / Tile<N>::L));
+        ProfScope prof(ctx, B ? -1 : P_FFT_Z_GREEN, Lv.index);
         if (green)
-            fft_z<N, 2><<<bz, Tile<N>::T, Tile<N>::SMEMY, ctx->stream>>>(Lv.spec, Lv.green, Lv.kxp, Lv.tw, Lv.active);
+            fft_z<N, 2, B><<<bz, Tile<N>::T, Tile<N>::SMEMY, ctx->stream>>>(Lv.spec, Lv.green, Lv.kxp, Lv.tw, Lv.active);
         else
-            fft_z<N, 0><<<bz, Tile<N>::T, Tile<N>::SMEMY, ctx->stream>>>(Lv.spec, nullptr, Lv.kxp, Lv.tw, Lv.active);
+            fft_z<N, 0, B><<<bz, Tile<N>::T, Tile<N>::SMEMY, ctx->stream>>>(Lv.spec, nullptr, Lv.kxp, Lv.tw, Lv.active);
         ctx->launches += 1;
         return cudaGetLastError();
     }
-    static cudaError_t inverse(cube2_ctx *ctx, Level &Lv) {
-        setup();
-        const unsigned by = (unsigned)((int64_t)Lv.batch * N * (Lv.kxp / Tile<N>::L));
-        const int cls = Lv.active ? -1 : 0;
+    template <bool B>
+    static cudaError_t inverse_v(cube2_ctx *ctx, Level &Lv) {
+        const unsigned by = pass_grid(ctx, Lv, (int64_t)Lv.batch * N * (Lv.kxp / Tile<N>::L));
         {
-            ProfScope prof(ctx, cls < 0 ? -1 : P_FFT_Y_INV, Lv.index);
-            fft_y<N, true><<<by, Tile<N>::T, Tile<N>::SMEMY, ctx->stream>>>(Lv.spec, Lv.kxp, Lv.tw, Lv.active);
+            ProfScope prof(ctx, B ? -1 : P_FFT_Y_INV, Lv.index);
+            fft_y<N, true, B><<<by, Tile<N>::T, Tile<N>::SMEMY, ctx->stream>>>(Lv.spec, Lv.kxp, Lv.tw, Lv.active);
         }
         const int64_t nrows = (int64_t)Lv.batch * N * N;
-        const unsigned bx = (unsigned)((nrows + 2 * Tile<N>::L - 1) / (2 * Tile<N>::L));
+        const unsigned bx = pass_grid(ctx, Lv, (nrows + 2 * Tile<N>::L - 1) / (2 * Tile<N>::L));
         {
-            ProfScope prof(ctx, cls < 0 ? -1 : P_FFT_X_INV, Lv.index);
-            fft_x_c2r<N><<<bx, Tile<N>::T, Tile<N>::SMEM, ctx->stream>>>(Lv.spec, Lv.real, nrows, Lv.kxp, Lv.tw,
-                                                                         Lv.active);
+            ProfScope prof(ctx, B ? -1 : P_FFT_X_INV, Lv.index);
+            fft_x_c2r<N, B><<<bx, Tile<N>::T, Tile<N>::SMEM, ctx->stream>>>(Lv.spec, Lv.real, nrows, Lv.kxp, Lv.tw,
+                                                                            Lv.active);
         }
         ctx->launches += 2;
         return cudaGetLastError();
+    }
+    static cudaError_t forward(cube2_ctx *ctx, Level &Lv) {
+        setup();
+        if constexpr (N <= BATCH_MAX_N)
+            if (Lv.active) return forward_v<true>(ctx, Lv);
+        if (Lv.active) return cudaErrorInvalidValue;
+        return forward_v<false>(ctx, Lv);
+    }
+    static cudaError_t z_pass(cube2_ctx *ctx, Level &Lv, bool green) {
+        setup();
+        if constexpr (N <= BATCH_MAX_N)
+            if (Lv.active) return z_pass_v<true>(ctx, Lv, green);
+        if (Lv.active) return cudaErrorInvalidValue;
+        return z_pass_v<false>(ctx, Lv, green);
+    }
+    static cudaError_t inverse(cube2_ctx *ctx, Level &Lv) {
+        setup();
+        if constexpr (N <= BATCH_MAX_N)
+            if (Lv.active) return inverse_v<true>(ctx, Lv);
+        if (Lv.active) return cudaErrorInvalidValue;
+        return inverse_v<false>(ctx, Lv);
+    }
+    template <bool B>
+    static void setup_v() {
+        const int smem = (int)Tile<N>::SMEM;
+        cudaFuncSetAttribute(fft_x_r2c<N, B>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        cudaFuncSetAttribute(fft_x_c2r<N, B>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        cudaFuncSetAttribute(fft_y<N, false, B>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        cudaFuncSetAttribute(fft_y<N, true, B>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        cudaFuncSetAttribute(fft_z<N, 0, B>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        cudaFuncSetAttribute(fft_z<N, 2, B>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     }
     static void setup() {
         static bool done = false;
         if (done) return;
-        const int smem = (int)Tile<N>::SMEM;
-        cudaFuncSetAttribute(fft_x_r2c<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        cudaFuncSetAttribute(fft_x_c2r<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        cudaFuncSetAttribute(fft_y<N, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        cudaFuncSetAttribute(fft_y<N, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        cudaFuncSetAttribute(fft_z<N, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        cudaFuncSetAttribute(fft_z<N, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        cudaFuncSetAttribute(fft_z<N, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        setup_v<false>();
+        cudaFuncSetAttribute(fft_z<N, 1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Tile<N>::SMEM);
+        if constexpr (N <= BATCH_MAX_N) setup_v<true>();
         done = true;
     }
 };
@@ -484,11 +576,11 @@ cudaError_t noalloc_passes(const float *rho, float2 *spec, const float *gpad, fl
     const int64_t nrows = (int64_t)N * N;
     const unsigned bx = (unsigned)((nrows + 2 * L - 1) / (2 * L));
     const unsigned by = (unsigned)((int64_t)N * (kxp / L));
-    fft_x_r2c<N><<<bx, Tile<N>::T, Tile<N>::SMEM, st>>>(rho, spec, nrows, kxp, tw, nullptr);
-    fft_y<N, false><<<by, Tile<N>::T, Tile<N>::SMEMY, st>>>(spec, kxp, tw, nullptr);
-    fft_z<N, 1><<<by, Tile<N>::T, Tile<N>::SMEMY, st>>>(spec, gpad, kxp, tw, nullptr);
-    fft_y<N, true><<<by, Tile<N>::T, Tile<N>::SMEMY, st>>>(spec, kxp, tw, nullptr);
-    fft_x_c2r<N><<<bx, Tile<N>::T, Tile<N>::SMEM, st>>>(spec, phi, nrows, kxp, tw, nullptr);
+    fft_x_r2c<N, false><<<bx, Tile<N>::T, Tile<N>::SMEM, st>>>(rho, spec, nrows, kxp, tw, nullptr);
+    fft_y<N, false, false><<<by, Tile<N>::T, Tile<N>::SMEMY, st>>>(spec, kxp, tw, nullptr);
+    fft_z<N, 1, false><<<by, Tile<N>::T, Tile<N>::SMEMY, st>>>(spec, gpad, kxp, tw, nullptr);
+    fft_y<N, true, false><<<by, Tile<N>::T, Tile<N>::SMEMY, st>>>(spec, kxp, tw, nullptr);
+    fft_x_c2r<N, false><<<bx, Tile<N>::T, Tile<N>::SMEM, st>>>(spec, phi, nrows, kxp, tw, nullptr);
     return cudaGetLastError();
 }
 

@@ -16,16 +16,17 @@
 //            exclusive scan of the refinement flags, and the slot of each
 //            refined subtile (subtile order; slots beyond the capacity stay
 //            unrefined); the number of slots in use stays on the device.
-//   deposit  one CTA per slot: the IOS cells under the local box, one warp per
-//            cell, exact integer CIC at 2^-16 of a local cell into uint64
-//            accumulators (the local cell is a power-of-two fraction of the IOS
-//            cell, so positions are exact fixed point and the sum is order-free)
-//   convert  accumulator -> FP32 density V_p/H_3^3 sum_i W, and the
-//            accumulator back to zero for the next evaluation
+//   deposit  one CTA per (z-slab, slot): the IOS cells under the slab's band of
+//            the local box, one warp per cell, exact integer CIC at 2^-16 of a
+//            local cell into 64-bit shared-memory sums (the local cell is a
+//            power-of-two fraction of the IOS cell, so positions are exact
+//            fixed point and the sum is order-free), then the slab's planes
+//            written once as FP32 density V_p/H_3^3 sum_i W
 //   solve    the FFT passes of the global levels, batched over the slots
 //            (blocks of unused slots return at once)
-//   gather   one thread per particle of a refined subtile: the 4-point
-//            difference of Eq. (diff) at its 8 CIC cells, F += -H_3 E.
+//   gather   one CTA per slot, a warp per x-row of the subtile's IOS cells:
+//            the 4-point difference of Eq. (diff) at each particle's 8 CIC
+//            cells, F += -H_3 E.
 #include "common.cuh"
 
 #include <algorithm>
@@ -109,143 +110,191 @@ __global__ void __launch_bounds__(256) pm3_slot_kernel(const int32_t *__restrict
     }
 }
 
-constexpr int PM3_DEP_THREADS = 512;
-
-__global__ void __launch_bounds__(PM3_DEP_THREADS) pm3_deposit_kernel(
+// Owner-computes local deposit: CTA (slab, slot) owns `slab` consecutive
+// z-planes of the slot's local mesh, accumulates the exact integer CIC weights
+// that land in them in shared memory (64-bit sums as two 32-bit words, the
+// high word taking the low word's carry), and writes its planes once as FP32
+// density.  It visits the particles whose z-position lies within half a local
+// cell of its planes (and, for the first and last planes, the band that wraps
+// around the periodic local mesh): every particle is visited by at most three
+// CTAs, with no global atomics.
+__global__ void __launch_bounds__(256) pm3_slab_deposit_kernel(
     const uint16_t *__restrict__ off0, const uint16_t *__restrict__ off1, const uint16_t *__restrict__ off2,
     const int32_t *__restrict__ cnt, const int32_t *__restrict__ start, const int32_t *__restrict__ list,
-    const int *__restrict__ count, Pm3Geo g, unsigned long long *__restrict__ acc, int *status) {
-    const int slot = blockIdx.x;
+    const int *__restrict__ count, Pm3Geo g, int slab, float *__restrict__ real, float scale, int *status) {
+    const int slot = blockIdx.y;
     if (slot >= count[0]) return;
+    const int m = g.m, n = g.n_ios;
+    const int z0 = blockIdx.x * slab;
+    const int nz = min(slab, m - z0);
+    if (nz <= 0) return;
+    extern __shared__ unsigned int sw[];
+    const int plane = m * m;
+    unsigned int *lo = sw, *hi = sw + slab * plane;
+    for (int i = threadIdx.x; i < 2 * slab * plane; i += blockDim.x) sw[i] = 0u;
     const int sub = list[slot];
     const int sxyz[3] = {sub % g.ns, (sub / g.ns) % g.ns, sub / (g.ns * g.ns)};
+    const int64_t q = (int64_t)1 << (FIX_BITS - g.q_shift);   // one local cell, fixed point
+    const int64_t extent = (int64_t)m * q;
     int64_t org[3];
-    int c_lo[3], span[3];
-    const int64_t extent = (int64_t)g.m << (FIX_BITS - g.q_shift);   // local box side, fixed point
+    int c_lo[2], span[2];
 #pragma unroll
-    for (int d = 0; d < 3; ++d) {
-        org[d] = local_origin(g, sxyz[d]);
+    for (int d = 0; d < 3; ++d) org[d] = local_origin(g, sxyz[d]);
+#pragma unroll
+    for (int d = 0; d < 2; ++d) {
         c_lo[d] = (int)(org[d] >> FIX_BITS);
-        span[d] = (int)(((org[d] & (FIX - 1)) + extent + FIX - 1) >> FIX_BITS);
-        if (span[d] > g.n_ios) span[d] = g.n_ios;
+        span[d] = min((int)(((org[d] & (FIX - 1)) + extent + FIX - 1) >> FIX_BITS), n);
     }
-    unsigned long long *a = acc + (int64_t)slot * g.m3;
+    __syncthreads();
+    // z bands (fixed point, relative to the local origin): the planes +- one cell,
+    // and the wrapped band for the first or last plane of the mesh
+    int64_t ba[3], bb[3];
+    int nb = 0;
+    ba[nb] = max((int64_t)0, (int64_t)(z0 - 1) * q);
+    bb[nb] = min(extent, (int64_t)(z0 + nz + 1) * q);
+    ++nb;
+    // (a wrap band that meets the main band adds nothing: the main band holds it)
+    if (z0 == 0 && extent - q >= bb[0]) { ba[nb] = extent - q; bb[nb] = extent; ++nb; }
+    if (z0 + nz == m && q <= ba[0]) { ba[nb] = 0; bb[nb] = q; ++nb; }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    const int ncell = span[0] * span[1] * span[2];
-    const int n = g.n_ios, m = g.m;
-    for (int k = warp; k < ncell; k += nw) {
-        const int kx = k % span[0], ky = (k / span[0]) % span[1], kz = k / (span[0] * span[1]);
-        const int cx = wrap(c_lo[0] + kx, n), cy = wrap(c_lo[1] + ky, n), cz = wrap(c_lo[2] + kz, n);
-        const int64_t c = ((int64_t)cz * n + cy) * n + cx;
-        const int b = __ldg(&start[c]), e = b + __ldg(&cnt[c]);
-        const int cc[3] = {cx, cy, cz};
-        for (int j = b + lane; j < e; j += 32) {
-            const unsigned o[3] = {off0[j], off1[j], off2[j]};
-            int i0[3], w1[3];
-            bool inside = true;
+    for (int bi = 0; bi < nb; ++bi) {
+        if (bb[bi] <= ba[bi]) continue;
+        // IOS z-planes holding fixed-point z in [org + ba, org + bb)
+        const int64_t za = org[2] + ba[bi], zb = org[2] + bb[bi] - 1;
+        const int pz0 = (int)(za >> FIX_BITS), npz = (int)((zb >> FIX_BITS) - (za >> FIX_BITS)) + 1;
+        const int ncell = span[0] * span[1] * npz;
+        for (int k = warp; k < ncell; k += nw) {
+            const int kx = k % span[0], ky = (k / span[0]) % span[1], kz = k / (span[0] * span[1]);
+            const int cx = wrap(c_lo[0] + kx, n), cy = wrap(c_lo[1] + ky, n);
+            const int cz = (int)(((int64_t)pz0 + kz) % n);
+            const int64_t c = ((int64_t)cz * n + cy) * n + cx;
+            const int b = __ldg(&start[c]), e = b + __ldg(&cnt[c]);
+            const int cc[3] = {cx, cy, cz};
+            for (int j = b + lane; j < e; j += 32) {
+                const unsigned o[3] = {off0[j], off1[j], off2[j]};
+                int i0[3], w1[3];
+                bool inside = true;
+                int64_t relz = 0;
 #pragma unroll
-            for (int d = 0; d < 3; ++d) {
-                int64_t rel = (int64_t)cc[d] * FIX + o[d] - org[d];
-                if (rel < 0) rel += g.period;
-                inside = inside && rel < extent;
-                const int64_t t = (rel << g.q_shift) - (FIX >> 1);   // local cells, 16 fractional bits
-                const int64_t fl = t >> FIX_BITS;                    // floor, t may be negative
-                i0[d] = (int)fl;
-                w1[d] = (int)(t - (fl << FIX_BITS));
-            }
-            if (!inside) continue;
+                for (int d = 0; d < 3; ++d) {
+                    int64_t rel = (int64_t)cc[d] * FIX + o[d] - org[d];
+                    if (rel < 0) rel += g.period;
+                    inside = inside && rel < extent;
+                    if (d == 2) relz = rel;
+                    const int64_t t = (rel << g.q_shift) - (FIX >> 1);
+                    const int64_t fl = t >> FIX_BITS;
+                    i0[d] = (int)fl;
+                    w1[d] = (int)(t - (fl << FIX_BITS));
+                }
+                if (!inside || relz < ba[bi] || relz >= bb[bi]) continue;
 #pragma unroll
-            for (int dz = 0; dz < 2; ++dz) {
-                const int iz = wrap(i0[2] + dz, m);
-                const unsigned long long wz = dz ? w1[2] : FIX - w1[2];
+                for (int dz = 0; dz < 2; ++dz) {
+                    const int iz = wrap(i0[2] + dz, m) - z0;
+                    if (iz < 0 || iz >= nz) continue;
+                    const unsigned long long wz = dz ? w1[2] : FIX - w1[2];
 #pragma unroll
-                for (int dy = 0; dy < 2; ++dy) {
-                    const int iy = wrap(i0[1] + dy, m);
-                    const unsigned long long wyz = wz * (unsigned long long)(dy ? w1[1] : FIX - w1[1]);
+                    for (int dy = 0; dy < 2; ++dy) {
+                        const int iy = wrap(i0[1] + dy, m);
+                        const unsigned long long wyz = wz * (unsigned long long)(dy ? w1[1] : FIX - w1[1]);
 #pragma unroll
-                    for (int dx = 0; dx < 2; ++dx) {
-                        const int ix = wrap(i0[0] + dx, m);
-                        const unsigned long long w = wyz * (unsigned long long)(dx ? w1[0] : FIX - w1[0]);
-                        if (w) {
-                            const unsigned long long old = atomicAdd(&a[((int64_t)iz * m + iy) * m + ix], w);
-                            if (old + w < old) set_status(status, ST_CAPACITY);
+                        for (int dx = 0; dx < 2; ++dx) {
+                            const int ix = wrap(i0[0] + dx, m);
+                            const unsigned long long w = wyz * (unsigned long long)(dx ? w1[0] : FIX - w1[0]);
+                            if (!w) continue;
+                            const int cell = (iz * m + iy) * m + ix;
+                            const unsigned int wl = (unsigned int)w, wh = (unsigned int)(w >> 32);
+                            const unsigned int old = atomicAdd(&lo[cell], wl);
+                            const unsigned int add_hi = wh + ((old + wl < old) ? 1u : 0u);
+                            if (add_hi) {
+                                const unsigned int oldh = atomicAdd(&hi[cell], add_hi);
+                                if (oldh + add_hi < oldh) set_status(status, ST_CAPACITY);
+                            }
                         }
                     }
                 }
             }
         }
     }
+    __syncthreads();
+    float *out = real + (int64_t)slot * g.m3 + (int64_t)z0 * plane;
+    for (int i = threadIdx.x; i < nz * plane; i += blockDim.x) {
+        const unsigned long long v = ((unsigned long long)hi[i] << 32) | lo[i];
+        out[i] = (float)v * scale;
+    }
 }
 
-__global__ void __launch_bounds__(256) pm3_convert_kernel(unsigned long long *__restrict__ acc,
-                                                          float *__restrict__ real, const int *__restrict__ count,
-                                                          int64_t m3, float scale) {
+// -H_3 (D * phi) at the particles of one refined subtile per CTA: a warp per
+// x-row of the subtile's IOS cells (their particles are contiguous).
+__global__ void __launch_bounds__(256) pm3_slot_gather_kernel(
+    const uint16_t *__restrict__ off0, const uint16_t *__restrict__ off1, const uint16_t *__restrict__ off2,
+    const int32_t *__restrict__ cellid, const int32_t *__restrict__ cnt, const int32_t *__restrict__ start,
+    const int32_t *__restrict__ list, const int *__restrict__ count, const float *__restrict__ phi, Pm3Geo g,
+    float h3, float *__restrict__ acc0, float *__restrict__ acc1, float *__restrict__ acc2) {
+    // grid: (row chunks, slots); the subtile's T^2 rows of IOS cells are dealt
+    // to the warps of all its chunks so that a dense subtile spreads over SMs
     const int slot = blockIdx.y;
     if (slot >= count[0]) return;
-    const int64_t base = (int64_t)slot * m3;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m3; i += (int64_t)gridDim.x * blockDim.x) {
-        const unsigned long long v = acc[base + i];
-        real[base + i] = (float)v * scale;
-        acc[base + i] = 0ull;
-    }
-}
-
-__global__ void __launch_bounds__(256) pm3_gather_kernel(
-    const uint16_t *__restrict__ off0, const uint16_t *__restrict__ off1, const uint16_t *__restrict__ off2,
-    const int32_t *__restrict__ cellid, const int32_t *__restrict__ slot_of, const float *__restrict__ phi,
-    Pm3Geo g, float h3, float *__restrict__ acc0, float *__restrict__ acc1, float *__restrict__ acc2, int64_t N) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= N) return;
     const int n = g.n_ios, T = g.T, m = g.m;
-    const int c = cellid[i];
-    const int cc[3] = {c % n, (c / n) % n, c / (n * n)};
-    const int sxyz[3] = {cc[0] / T, cc[1] / T, cc[2] / T};
-    const int slot = slot_of[((int64_t)sxyz[2] * g.ns + sxyz[1]) * g.ns + sxyz[0]];
-    if (slot < 0) return;
-    const unsigned o[3] = {off0[i], off1[i], off2[i]};
-    int i0[3];
-    float w1[3];
+    const int sub = list[slot];
+    const int sxyz[3] = {sub % g.ns, (sub / g.ns) % g.ns, sub / (g.ns * g.ns)};
+    int64_t org[3];
 #pragma unroll
-    for (int d = 0; d < 3; ++d) {
-        int64_t rel = (int64_t)cc[d] * FIX + o[d] - local_origin(g, sxyz[d]);
-        if (rel < 0) rel += g.period;
-        const int64_t t = (rel << g.q_shift) - (FIX >> 1);
-        const int64_t fl = t >> FIX_BITS;
-        i0[d] = (int)fl;
-        w1[d] = (float)(t - (fl << FIX_BITS)) * (1.0f / FIX);
-    }
+    for (int d = 0; d < 3; ++d) org[d] = local_origin(g, sxyz[d]);
     const float *P = phi + (int64_t)slot * g.m3;
-    float e[3] = {0.f, 0.f, 0.f};
+    const int lane = threadIdx.x & 31, nw = (blockDim.x >> 5) * gridDim.x;
+    const int warp = (threadIdx.x >> 5) + (blockDim.x >> 5) * blockIdx.x;
+    for (int r = warp; r < T * T; r += nw) {
+        const int cy = sxyz[1] * T + r % T, cz = sxyz[2] * T + r / T;
+        const int64_t c0 = ((int64_t)cz * n + cy) * n + (int64_t)sxyz[0] * T;
+        const int b = __ldg(&start[c0]), e = __ldg(&start[c0 + T - 1]) + __ldg(&cnt[c0 + T - 1]);
+        for (int i = b + lane; i < e; i += 32) {
+            const int cx = cellid[i] % n;
+            const int cc[3] = {cx, cy, cz};
+            const unsigned o[3] = {off0[i], off1[i], off2[i]};
+            int i0[3];
+            float w1[3];
 #pragma unroll
-    for (int dz = 0; dz < 2; ++dz) {
-        const float wz = dz ? w1[2] : 1.0f - w1[2];
+            for (int d = 0; d < 3; ++d) {
+                int64_t rel = (int64_t)cc[d] * FIX + o[d] - org[d];
+                if (rel < 0) rel += g.period;
+                const int64_t t = (rel << g.q_shift) - (FIX >> 1);
+                const int64_t fl = t >> FIX_BITS;
+                i0[d] = (int)fl;
+                w1[d] = (float)(t - (fl << FIX_BITS)) * (1.0f / FIX);
+            }
+            float e3[3] = {0.f, 0.f, 0.f};
 #pragma unroll
-        for (int dy = 0; dy < 2; ++dy) {
-            const float wyz = wz * (dy ? w1[1] : 1.0f - w1[1]);
+            for (int dz = 0; dz < 2; ++dz) {
+                const float wz = dz ? w1[2] : 1.0f - w1[2];
 #pragma unroll
-            for (int dx = 0; dx < 2; ++dx) {
-                const float w = wyz * (dx ? w1[0] : 1.0f - w1[0]);
-                const int j[3] = {i0[0] + dx, i0[1] + dy, i0[2] + dz};
+                for (int dy = 0; dy < 2; ++dy) {
+                    const float wyz = wz * (dy ? w1[1] : 1.0f - w1[1]);
 #pragma unroll
-                for (int d = 0; d < 3; ++d) {
-                    float v[4];
+                    for (int dx = 0; dx < 2; ++dx) {
+                        const float w = wyz * (dx ? w1[0] : 1.0f - w1[0]);
+                        const int j[3] = {i0[0] + dx, i0[1] + dy, i0[2] + dz};
 #pragma unroll
-                    for (int k = 0; k < 4; ++k) {
-                        const int step = k < 2 ? k - 2 : k - 1;   // -2, -1, +1, +2
-                        int jj[3] = {j[0], j[1], j[2]};
-                        jj[d] += step;
+                        for (int d = 0; d < 3; ++d) {
+                            float v[4];
 #pragma unroll
-                        for (int a = 0; a < 3; ++a) jj[a] = mod_mesh(jj[a], m);
-                        v[k] = __ldg(&P[((int64_t)jj[2] * m + jj[1]) * m + jj[0]]);
+                            for (int k = 0; k < 4; ++k) {
+                                const int step = k < 2 ? k - 2 : k - 1;   // -2, -1, +1, +2
+                                int jj[3] = {j[0], j[1], j[2]};
+                                jj[d] += step;
+#pragma unroll
+                                for (int a = 0; a < 3; ++a) jj[a] = mod_mesh(jj[a], m);
+                                v[k] = __ldg(&P[((int64_t)jj[2] * m + jj[1]) * m + jj[0]]);
+                            }
+                            e3[d] += w * (2.0f / 3.0f * (v[2] - v[1]) - 1.0f / 12.0f * (v[3] - v[0]));
+                        }
                     }
-                    e[d] += w * (2.0f / 3.0f * (v[2] - v[1]) - 1.0f / 12.0f * (v[3] - v[0]));
                 }
             }
+            acc0[i] += -h3 * e3[0];
+            acc1[i] += -h3 * e3[1];
+            acc2[i] += -h3 * e3[2];
         }
     }
-    acc0[i] += -h3 * e[0];
-    acc1[i] += -h3 * e[1];
-    acc2[i] += -h3 * e[2];
 }
 
 }  // namespace
@@ -267,6 +316,10 @@ cudaError_t launch_pm3_map(cube2_ctx *ctx, const cube2_particles *p) {
     return cudaGetLastError();
 }
 
+// z-planes of a local mesh per deposit CTA: as many as fit in 96 KB of shared
+// 64-bit accumulators, at most 8
+int pm3_slab_planes(int m) { return std::max(1, std::min(8, (96 * 1024) / (8 * m * m))); }
+
 cudaError_t launch_pm3(cube2_ctx *ctx, const cube2_particles *p) {
     PM3 &M = ctx->pm3;
     const Pm3Geo g = pm3_geo(ctx);
@@ -274,12 +327,17 @@ cudaError_t launch_pm3(cube2_ctx *ctx, const cube2_particles *p) {
     if (e != cudaSuccess) return e;
     {
         ProfScope prof(ctx, P_PM3_DEPOSIT, 0);
-        pm3_deposit_kernel<<<(unsigned)M.max_tiles, PM3_DEP_THREADS, 0, ctx->stream>>>(
-            p->off[0], p->off[1], p->off[2], p->count, p->start, M.list, M.count, g, M.acc, ctx->dev_status);
-        const unsigned gx = (unsigned)std::min<int64_t>((g.m3 + 255) / 256, 64);
-        pm3_convert_kernel<<<dim3(gx, (unsigned)M.max_tiles), 256, 0, ctx->stream>>>(M.acc, M.lev.real, M.count, g.m3,
-                                                                                    M.dens_scale);
-        ctx->launches += 2;
+        const int slab = pm3_slab_planes(g.m);
+        const size_t smem = (size_t)2 * slab * g.m * g.m * sizeof(unsigned int);
+        static bool attr = false;
+        if (!attr) {
+            cudaFuncSetAttribute(pm3_slab_deposit_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
+            attr = true;
+        }
+        pm3_slab_deposit_kernel<<<dim3((unsigned)((g.m + slab - 1) / slab), (unsigned)M.max_tiles), 256, smem,
+                                  ctx->stream>>>(p->off[0], p->off[1], p->off[2], p->count, p->start, M.list, M.count,
+                                                 g, slab, M.lev.real, M.dens_scale, ctx->dev_status);
+        ctx->launches += 1;
         e = cudaGetLastError();
     }
     if (e != cudaSuccess) return e;
@@ -289,9 +347,10 @@ cudaError_t launch_pm3(cube2_ctx *ctx, const cube2_particles *p) {
     }
     if (e != cudaSuccess || ctx->N == 0) return e;
     ProfScope prof(ctx, P_PM3_GATHER, 0);
-    pm3_gather_kernel<<<(unsigned)((ctx->N + 255) / 256), 256, 0, ctx->stream>>>(
-        p->off[0], p->off[1], p->off[2], ctx->cellid, M.slot, M.lev.real, g, (float)M.H, p->acc[0], p->acc[1],
-        p->acc[2], ctx->N);
+    const unsigned chunks = (unsigned)std::max(1, std::min(8, (M.T * M.T + 7) / 8));   // a row per warp at most
+    pm3_slot_gather_kernel<<<dim3(chunks, (unsigned)M.max_tiles), 256, 0, ctx->stream>>>(
+        p->off[0], p->off[1], p->off[2], ctx->cellid, p->count, p->start, M.list, M.count, M.lev.real, g, (float)M.H,
+        p->acc[0], p->acc[1], p->acc[2]);
     ctx->launches++;
     return cudaGetLastError();
 }
