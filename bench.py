@@ -692,7 +692,6 @@ def run_large(args):
     stream = ctx.stream
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ctx.profile(capacity=64 * (args.steps + 2))
-    ctx.pp_stats()
     launches0 = ctx.launch_count()
     clocks = ClockSampler(bus_id_of(torch.cuda.current_device()))
     clocks.start()
@@ -707,8 +706,13 @@ def run_large(args):
     prof = ctx.profile_read()
     ctx.profile(0)
     ctx.check()
-    pairs, cands = ctx.pp_stats()
     launches = ctx.launch_count() - launches0
+    # PP work of the same evaluation, counted in an untimed pass (counting costs PP time)
+    ctx.pp_count(True)
+    ctx.pp_stats()
+    ctx.force(p)
+    pairs, cands = (v * args.steps for v in ctx.pp_stats())
+    ctx.pp_count(False)
     total_prof = sum(v[0] for v in prof.values())
     kernels = {f"{c}/{l}": {"share": v[0] / total_prof, "ms_per_launch": v[0] / v[1], "launches": v[1]}
                for (c, l), v in sorted(prof.items(), key=lambda kv: -kv[1][0])}
@@ -809,11 +813,10 @@ def main():
         ctx.kdk_step(p, a[i], a[i + 1])
     ctx.check()
     # the whole schedule from the initial conditions (untimed for the headline):
-    # per-step CUDA events and PP pair counts, and the states the timed steps start from
+    # per-step CUDA events and the states the timed steps start from
     load(p, p0)
     ckpt = {}
-    sched_ms, sched_pairs, sched_pm3 = [], [], []
-    ctx.pp_stats()
+    sched_ms, sched_pm3 = [], []
     for i in range(S):
         if i in idx:
             ckpt[i] = p.clone()
@@ -823,16 +826,27 @@ def main():
         e1.record(stream)
         e1.synchronize()
         sched_ms.append(e0.elapsed_time(e1))
-        sched_pairs.append(ctx.pp_stats()[0])
         if w.pm3 is not None:
             sched_pm3.append(ctx.pm3_stats()[0])
+    ctx.check()
+    # the same schedule again with the PP work counters on (they cost PP time,
+    # so no timed pass counts): pairs and candidates of every step
+    load(p, p0)
+    sched_pairs, sched_cands = [], []
+    ctx.pp_count(True)
+    ctx.pp_stats()
+    for i in range(S):
+        ctx.kdk_step(p, a[i], a[i + 1])
+        pc = ctx.pp_stats()
+        sched_pairs.append(pc[0])
+        sched_cands.append(pc[1])
+    ctx.pp_count(False)
     ctx.check()
     torch.cuda.synchronize()
 
     # timed region: K steps, each from its checkpoint (the restore is outside the event pair)
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in idx]
     ctx.profile(capacity=64 * (args.steps + 2))
-    ctx.pp_stats()
     launches = 0
     clocks = ClockSampler(bus_id_of(torch.cuda.current_device()))
     clocks.start()
@@ -852,7 +866,9 @@ def main():
     prof = ctx.profile_read()
     ctx.profile(0)
     ctx.check()
-    pp_pairs, pp_cands = ctx.pp_stats()
+    # the timed steps repeat schedule steps from their checkpoints (bitwise)
+    pp_pairs = sum(sched_pairs[i] for i in idx)
+    pp_cands = sum(sched_cands[i] for i in idx)
     ms_max = ranks.max(ms)
     units = ranks.sum(n_part * args.steps)
     value = job_throughput(units, ms_max / 1e3)

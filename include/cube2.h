@@ -337,12 +337,21 @@ int cube2_profile(cube2_ctx *ctx, int cap);
 int cube2_profile_read(cube2_ctx *ctx, double *ms, int64_t *counts);
 const char *cube2_profile_class_name(int cls);
 
-/* PP work counters accumulated since the last call: out[0] = ordered pairs
- * closer than the PP range that were evaluated, out[1] = candidate pairs
- * tested (per target: the shared source stream of its warp where the warp
- * has one, else the particles of its 27 cells).  Synchronises the stream and
- * resets the counters. */
+/* PP work counters.  cube2_pp_count(ctx, 1) switches counting on for the
+ * context's later PP evaluations (force, pp_force, steps; not the ensemble's
+ * persistent kernel), 0 off (the default: the counters cost PP time).
+ * cube2_pp_stats: the counts accumulated while counting was on, since the
+ * last call: out[0] = ordered pairs closer than the PP range that were
+ * evaluated, out[1] = candidate pairs tested (per target: the shared source
+ * stream of its warp where the warp has one, else the particles of its 27
+ * cells).  Synchronises the stream and resets the counters. */
+int cube2_pp_count(cube2_ctx *ctx, int on);
 int cube2_pp_stats(cube2_ctx *ctx, int64_t out[2]);
+
+/* The same counters split by path: out[0..1] = (pairs, candidates) of all
+ * targets as above, out[2..3] = those of the targets whose warp walked its
+ * own 27 cells per lane (no shared stream).  Synchronises and resets. */
+int cube2_pp_stats_paths(cube2_ctx *ctx, int64_t out[4]);
 
 /* Number of kernel launches this context has issued (for launch accounting). */
 int64_t cube2_launch_count(cube2_ctx *ctx);

@@ -330,8 +330,8 @@ int cube2_init_mesh(cube2_ctx **out, const cube2_config *cfg, void *stream) {
     alloc((void **)&c->big_n, sizeof(int));
     alloc((void **)&c->pos4, N * 16);
     alloc((void **)&c->pp_perm, N * 4);
-    alloc((void **)&c->pp_stats, 2 * sizeof(unsigned long long));
-    if (e == cudaSuccess) e = cudaMemsetAsync(c->pp_stats, 0, 2 * sizeof(unsigned long long), c->stream);
+    alloc((void **)&c->pp_stats, 4 * sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->pp_stats, 0, 4 * sizeof(unsigned long long), c->stream);
     if (cfg->vel_fp16) alloc((void **)&c->vel32, N * 3 * 4);
     if (c->pm3.on) {
         PM3 &M = c->pm3;
@@ -954,15 +954,30 @@ const char *cube2_profile_class_name(int cls) {
     return (cls >= 0 && cls < CUBE2_PROFILE_CLASSES) ? names[cls] : "";
 }
 
-int cube2_pp_stats(cube2_ctx *ctx, int64_t out[2]) {
+int cube2_pp_count(cube2_ctx *ctx, int on) {
+    if (!ctx) return CUBE2_ERR_BAD_ARG;
+    ctx->pp_count = on != 0;
+    return CUBE2_OK;
+}
+
+int cube2_pp_stats_paths(cube2_ctx *ctx, int64_t out[4]) {
     if (!ctx || !out) return CUBE2_ERR_BAD_ARG;
-    unsigned long long h[2] = {0, 0};
+    unsigned long long h[4] = {0, 0, 0, 0};
     cudaError_t e = cudaMemcpyAsync(h, ctx->pp_stats, sizeof h, cudaMemcpyDeviceToHost, ctx->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(ctx->pp_stats, 0, sizeof h, ctx->stream);
     if (e != cudaSuccess) return cuda_error(ctx, e, "pp stats");
-    out[0] = (int64_t)h[0];
-    out[1] = (int64_t)h[1];
+    for (int k = 0; k < 4; ++k) out[k] = (int64_t)h[k];
+    return CUBE2_OK;
+}
+
+int cube2_pp_stats(cube2_ctx *ctx, int64_t out[2]) {
+    if (!ctx || !out) return CUBE2_ERR_BAD_ARG;
+    int64_t all[4];
+    const int rc = cube2_pp_stats_paths(ctx, all);
+    if (rc != CUBE2_OK) return rc;
+    out[0] = all[0];
+    out[1] = all[1];
     return CUBE2_OK;
 }
 

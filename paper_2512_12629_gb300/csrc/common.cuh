@@ -133,6 +133,8 @@ struct cube2_ctx {
     float *vel32 = nullptr;        // [3][N] FP32 working momenta of a step (cfg.vel_fp16 = 1 only)
     // shared-stream width of the PP kernel (warps spanning at most pp_wmax + 1 cells)
     int pp_wmax = 16;
+    // PP work counters (cube2_pp_count): off unless asked for
+    bool pp_count = false;
     // ensemble recording: launch_pp prepares the PP inputs and leaves the PP
     // kernel to the ensemble's persistent kernel, saving its parameters here
     bool defer_pp = false;

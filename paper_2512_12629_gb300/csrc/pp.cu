@@ -482,9 +482,14 @@ __device__ void union_path(const PPParams &P, const WarpSegs &W, float4 *S, floa
 
 // Warps whose targets span several rows or a wide x range (sparse regions):
 // each lane walks its own 27 cells as 9 row ranges and evaluates the pairs in
-// range as it meets them.  Plain nested loops keep the loads pipelined.
+// range as it meets them.  Plain nested loops keep the loads pipelined.  (A
+// per-lane queue of the pairs in range, evaluated when full, measured 2x
+// slower over the 256^3 run: lanes of warps straddling two rows of a dense
+// region fill their queues at different steps and evaluate them one at a
+// time; skipping the rows and end cells beyond the range saved 6 % of the
+// candidates at z = 49 and cost more than that.)
 __device__ void lane_path(const PPParams &P, bool has, int c, float4 me, float bcut2, float ibc, Sum3 &a,
-                                    unsigned &pairs, unsigned &cands) {
+                          unsigned &pairs, unsigned &cands) {
     if (!has) return;
     const int n = P.n_ios;
     const int cx = c % n, cy = (c / n) % n, cz = c / (n * n);
@@ -711,7 +716,10 @@ __global__ void __launch_bounds__(PP_CTA, PPV_MINB) pp_vjp_kernel(PPParams P, Vj
 #define PP_MINB 16
 #endif
 // The targets of one block of PP_CTA slots: [block * PP_CTA, block * PP_CTA + PP_CTA).
-template <bool PM3>
+// COUNT: accumulate the work counters (off unless asked for: the two counters
+// live through the whole walk and, within the 32-register budget, cost up to
+// a fifth of the sparse-region time).
+template <bool PM3, bool COUNT>
 __device__ __forceinline__ void pp_block(const PPParams &P, int64_t block, PPShared &sh) {
     const int64_t i = block * PP_CTA + threadIdx.x;
     const int wib = threadIdx.x >> 5;
@@ -746,13 +754,16 @@ __device__ __forceinline__ void pp_block(const PPParams &P, int64_t block, PPSha
     else
         lane_path(P, has, c, me, bcut2, ibc, a, pairs, cands);
     if (has) finish(P, P.perm[i], a.x - a.cx, a.y - a.cy, a.z - a.cz);
-    add_stats(P.stats, pairs, cands);
+    if constexpr (COUNT) {
+        add_stats(P.stats, pairs, cands);
+        if (!one_row) add_stats(P.stats + 2, pairs, cands);   // warp-uniform
+    }
 }
 
-template <bool PM3>
+template <bool PM3, bool COUNT>
 __global__ void __launch_bounds__(PP_CTA, PP_MINB) pp_kernel(PPParams P) {
     __shared__ PPShared sh;
-    pp_block<PM3>(P, blockIdx.x, sh);
+    pp_block<PM3, COUNT>(P, blockIdx.x, sh);
 }
 
 // ------------------------------------------------- ensemble: one persistent PP
@@ -847,7 +858,7 @@ __global__ void __launch_bounds__(PP_CTA, PP_MINB) pp_persistent_kernel(const PP
         if (item >= count) break;
         const int k = order[item];
         const int b = item_box[k];
-        pp_block<false>(boxes[b], (int64_t)(k - base[b]), sh);
+        pp_block<false, false>(boxes[b], (int64_t)(k - base[b]), sh);
     }
 }
 
@@ -932,9 +943,11 @@ cudaError_t launch_pp(cube2_ctx *ctx, const cube2_particles *p, int accumulate, 
     {
         ProfScope prof(ctx, P_PP, 0);
         if (P.pm3_slot)
-            pp_kernel<true><<<(unsigned)nblocks, PP_CTA, 0, ctx->stream>>>(P);
+            (ctx->pp_count ? pp_kernel<true, true> : pp_kernel<true, false>)<<<(unsigned)nblocks, PP_CTA, 0,
+                                                                              ctx->stream>>>(P);
         else
-            pp_kernel<false><<<(unsigned)nblocks, PP_CTA, 0, ctx->stream>>>(P);
+            (ctx->pp_count ? pp_kernel<false, true> : pp_kernel<false, false>)<<<(unsigned)nblocks, PP_CTA, 0,
+                                                                                ctx->stream>>>(P);
     }
     ctx->launches += 4;
     return cudaGetLastError();

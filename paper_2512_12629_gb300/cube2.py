@@ -117,6 +117,8 @@ def _load():
         "cube2_profile_read": (I, [P, ctypes.POINTER(D), ctypes.POINTER(ctypes.c_int64)]),
         "cube2_profile_class_name": (ctypes.c_char_p, [I]),
         "cube2_pp_stats": (I, [P, ctypes.POINTER(ctypes.c_int64)]),
+        "cube2_pp_count": (I, [P, ctypes.c_int]),
+        "cube2_pp_stats_paths": (I, [P, ctypes.POINTER(ctypes.c_int64)]),
         "cube2_solve_pm_noalloc": (I, [P, P, P, ctypes.c_int32, P]),
         "cube2_fma_probe": (I, [P, I, I, I, P]),
         "cube2_pm3_info": (I, [P, ctypes.POINTER(D)]),
@@ -450,11 +452,21 @@ class Context:
     def launch_count(self):
         return int(_lib.cube2_launch_count(self.ptr))
 
+    def pp_count(self, on=True):
+        """Switch the PP work counters on (or off, the default) for later PP evaluations."""
+        self._chk(_lib.cube2_pp_count(self.ptr, int(bool(on))))
+
     def pp_stats(self):
-        """(in-range ordered pairs, candidate pairs) since the last call."""
+        """(in-range ordered pairs, candidate pairs) counted since the last call (see pp_count)."""
         out = (ctypes.c_int64 * 2)()
         self._chk(_lib.cube2_pp_stats(self.ptr, out))
         return int(out[0]), int(out[1])
+
+    def pp_stats_paths(self):
+        """(pairs, candidates) of all targets and of the per-lane path, since the last call."""
+        out = (ctypes.c_int64 * 4)()
+        self._chk(_lib.cube2_pp_stats_paths(self.ptr, out))
+        return tuple(int(v) for v in out)
 
     def profile(self, capacity):
         """Start (capacity > 0) or stop (0) per-kernel-class CUDA-event timing."""
