@@ -189,6 +189,28 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(rows)}
 
 
+def bind_local_numa(bus_id):
+    """Restrict this process to the CPUs of the NUMA node the GPU hangs off (as
+    sysfs reports it), so that pinned host buffers allocated afterwards are
+    local to that node; returns the node or None (nothing changed)."""
+    try:
+        dom, bus, devfn = bus_id.lower().split(":")
+        node = int(open(f"/sys/bus/pci/devices/{dom[-4:]}:{bus}:{devfn}/numa_node").read())
+        if node < 0:
+            return None
+        cpus = set()
+        for part in open(f"/sys/devices/system/node/node{node}/cpulist").read().strip().split(","):
+            if part:
+                lo, _, hi = part.partition("-")
+                cpus.update(range(int(lo), int(hi or lo) + 1))
+        if not cpus:
+            return None
+        os.sched_setaffinity(0, cpus)
+        return node
+    except (OSError, ValueError, AttributeError):
+        return None
+
+
 def bus_id_of(dev):
     try:
         import torch
@@ -918,9 +940,12 @@ def main():
     # end to end through the host-buffer entry point, on the same steps
     e2e = None
     if not args.no_e2e:
+        cpus_before = os.sched_getaffinity(0)
+        numa = bind_local_numa(bus_id_of(torch.cuda.current_device()))
         host = cube2.IOSState(*(x.cpu().pin_memory() for x in (p0.off, p0.count, p0.start, p0.vel, p0.acc)))
         pe = p0.clone()
-        bytes_step = sum(x.numel() * x.element_size() for x in (host.off, host.count, host.start, host.vel, host.acc))
+        bytes_down = sum(x.numel() * x.element_size() for x in (host.off, host.count, host.start, host.vel, host.acc))
+        bytes_up = bytes_down - host.start.numel() * host.start.element_size()   # start is formed on the device
         ctx.kdk_step_host(pe, host, a[0], a[1])                # warm
         el = 0.0
         ranks.barrier()
@@ -931,9 +956,11 @@ def main():
             ctx.kdk_step_host(pe, host, a[i], a[i + 1])
             el += time.perf_counter() - t0
         el = ranks.max(el)
+        os.sched_setaffinity(0, cpus_before)
         e2e = {"value": job_throughput(units, el), "unit": UNIT,
-               "h2d_bytes_per_step": bytes_step, "d2h_bytes_per_step": bytes_step,
-               "api": "cube2_kdk_step_host (pinned host state, H2D + step + D2H each step), the same steps"}
+               "h2d_bytes_per_step": bytes_up, "d2h_bytes_per_step": bytes_down,
+               "api": "cube2_kdk_step_host (pinned host state, H2D + step + D2H each step), the same steps",
+               "host_numa_node": numa}
     del ckpt
 
     # cuFFT (through torch.fft), timed only as a comparison with the library's own

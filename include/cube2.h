@@ -233,8 +233,10 @@ int cube2_force(cube2_ctx *ctx, const cube2_particles *p);
 int cube2_kdk_step(cube2_ctx *ctx, cube2_particles *p, double a0, double a1);
 
 /* The same step for a particle set held in HOST memory (pinned for speed):
- * copies host -> dev, runs cube2_kdk_step on dev, copies dev -> host (off,
- * count, start, vel, acc), then synchronises.  Offsets, counts and starts
+ * copies host -> dev (off, count, vel, acc; host->start is not read: the
+ * device forms it from count, of which it is the exclusive prefix sum in the
+ * IOS layout), runs cube2_kdk_step on dev, copies dev -> host (off, count,
+ * start, vel, acc), then synchronises.  Offsets, counts and starts
  * are final after the re-bin; their download runs on a second stream of the
  * context while the forces are computed. */
 int cube2_kdk_step_host(cube2_ctx *ctx, cube2_particles *dev, cube2_particles *host,

@@ -811,7 +811,9 @@ int cube2_kdk_step_host(cube2_ctx *ctx, cube2_particles *dev, cube2_particles *h
         cp(dev->acc[d], host->acc[d], N * 4, cudaMemcpyHostToDevice, ctx->stream);
     }
     cp(dev->count, host->count, C * 4, cudaMemcpyHostToDevice, ctx->stream);
-    cp(dev->start, host->start, C * 4, cudaMemcpyHostToDevice, ctx->stream);
+    // start is the exclusive prefix sum of count (the IOS layout): formed on
+    // the device instead of uploaded
+    if (e == cudaSuccess) e = launch_scan(ctx, dev->count, dev->start, (int64_t)C);
     if (e != cudaSuccess) return cuda_error(ctx, e, "upload");
     int r = kdk_step_core(ctx, dev, a0, a1, ctx->aux_event);
     if (r) return r;

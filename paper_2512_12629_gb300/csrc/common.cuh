@@ -110,7 +110,7 @@ struct cube2_ctx {
     int *big_n = nullptr;          // their number
     float4 *pos4 = nullptr;        // [N] in-cell offsets as floats (+ cell id bits), PP order
     int32_t *pp_perm = nullptr;    // [N] particle index of each PP slot (sub-cell order in dense cells)
-    unsigned long long *pp_stats = nullptr;  // [2] in-range ordered pairs, candidates
+    unsigned long long *pp_stats = nullptr;  // [4] in-range ordered pairs, candidates; the same of per-lane walks
     int num_sms = 152;
     int32_t *scan_tmp = nullptr;   // block sums of the multi-level scan
     int64_t scan_tmp_len = 0;

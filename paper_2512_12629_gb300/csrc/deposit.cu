@@ -168,6 +168,11 @@ __global__ void __launch_bounds__(DEP_THREADS) deposit_kernel(DepParams P) {
                 w0[a] = FIX - w1[a];
                 ext[a] = s >= 0 ? (e[a] >> s) : (e[a] << (-s));
             }
+            // a halo particle whose cloud misses the owned cells on some axis
+            // (most of them on the finer levels) has nothing to add here
+            if (i0[0] + 1 < 0 || i0[0] >= ext[0] || i0[1] + 1 < 0 || i0[1] >= ext[1] || i0[2] + 1 < 0 ||
+                i0[2] >= ext[2])
+                continue;
             unsigned int *tlo = lo + tile_off, *thi = hi + tile_off;
 #pragma unroll
             for (int cz = 0; cz < 2; ++cz) {

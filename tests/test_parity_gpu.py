@@ -358,12 +358,14 @@ def test_single_particle_and_empty_box():
 
 def test_host_buffer_step_equals_device_step():
     """cube2_kdk_step_host (pinned host state, uploads, step, overlapped
-    downloads) leaves the host arrays bitwise equal to a device-side step."""
+    downloads) leaves the host arrays bitwise equal to a device-side step; the
+    host's start array is not read (the device forms it from count)."""
     w, st, _, ctx = case("C2_SMALL")
     p = cube2.IOSState.from_numpy(st)
     ctx.force(p)
     a = w.scale_factors()
     host = cube2.IOSState(*(x.cpu().pin_memory() for x in (p.off, p.count, p.start, p.vel, p.acc)))
+    host.start.fill_(-7)          # not read: formed on the device from count
     dev = p.clone()
     ctx.kdk_step(p, a[0], a[1])
     ctx.kdk_step_host(dev, host, a[0], a[1])
