@@ -72,7 +72,12 @@ __global__ void __launch_bounds__(DEP_THREADS) deposit_kernel(DepParams P) {
     const int nrows = (ey + 2) * (ez + 2);
     const int nseg = 3 * nrows;
 
-    for (int i = threadIdx.x; i < 2 * P.tile_total; i += blockDim.x) smem_u32[i] = 0u;
+    if (P.tile_total % 2 == 0) {   // 2 * tile_total words as 16-byte stores
+        for (int i = threadIdx.x; i < P.tile_total / 2; i += blockDim.x)
+            reinterpret_cast<uint4 *>(smem_u32)[i] = make_uint4(0u, 0u, 0u, 0u);
+    } else {
+        for (int i = threadIdx.x; i < 2 * P.tile_total; i += blockDim.x) smem_u32[i] = 0u;
+    }
     // halo row (hy, hz) spans cells x in [c0x-1, c0x+ex]; segment 0 is the part
     // inside [0, n), segments 1 and 2 the cells that wrap on the left and right
     for (int sg = threadIdx.x; sg < nseg; sg += blockDim.x) {
@@ -221,6 +226,27 @@ __global__ void __launch_bounds__(DEP_THREADS) deposit_kernel(DepParams P) {
         const int ezl = s >= 0 ? (ez >> s) : (ez << (-s));
         const int tile_off = l == 0 ? 0 : own0 * own0 * own0;
         const unsigned int *tlo = lo + tile_off, *thi = hi + tile_off;
+        if (L.out_f32 && own % 4 == 0 && exl % 4 == 0 && ox % 4 == 0 && L.n % 4 == 0 && tile_off % 4 == 0 &&
+            P.tile_total % 4 == 0) {
+            // four cells of a row per thread: 16-byte shared loads of both
+            // words and one 16-byte store of the FP32 values
+            const int q = exl >> 2, groups = q * eyl * ezl;
+            for (int gi = threadIdx.x; gi < groups; gi += blockDim.x) {
+                const int r = gi / q, ix = (gi - r * q) << 2;
+                const int iy = r % eyl, iz = r / eyl;
+                const int cell = (iz * own + iy) * own + ix;
+                const uint4 l4 = *reinterpret_cast<const uint4 *>(&tlo[cell]);
+                const uint4 h4 = *reinterpret_cast<const uint4 *>(&thi[cell]);
+                const int64_t g = ((int64_t)(oz + iz) * L.n + (oy + iy)) * L.n + (ox + ix);
+                float4 f;
+                f.x = u64_delta_to_f32(((uint64_t)h4.x << 32) | l4.x, L.mean_int, L.scale);
+                f.y = u64_delta_to_f32(((uint64_t)h4.y << 32) | l4.y, L.mean_int, L.scale);
+                f.z = u64_delta_to_f32(((uint64_t)h4.z << 32) | l4.z, L.mean_int, L.scale);
+                f.w = u64_delta_to_f32(((uint64_t)h4.w << 32) | l4.w, L.mean_int, L.scale);
+                *reinterpret_cast<float4 *>(&L.out_f32[g]) = f;
+            }
+            continue;
+        }
         const int cells = exl * eyl * ezl;
         for (int i = threadIdx.x; i < cells; i += blockDim.x) {
             const int ix = i % exl, iy = (i / exl) % eyl, iz = i / (exl * eyl);
