@@ -4,7 +4,9 @@
 // One CTA per brick of BI^3 IOS cells, every level in one pass.  For each level
 // the CTA stages in shared memory the phi tile its particles can reach: the
 // brick's mesh cells, one more for the upper CIC corner and two on each side
-// for the 4-point difference.  The 4-point difference is not stored as a
+// for the 4-point difference; along x the tile starts one more cell down, at
+// a multiple of 4, and is a multiple of 4 long, so that it is staged in
+// 16-byte copies (4-byte copies where a level's sizes do not allow it).  The 4-point difference is not stored as a
 // field: along axis d the CIC pair of corners (weights w0 on i0, w1 on i0+1)
 // sees phi at i0-2 .. i0+3 with the combined coefficients
 //   i0-2: +w0/12      i0-1: -2/3 w0 + w1/12   i0: -2/3 w1
@@ -53,7 +55,7 @@ __device__ __forceinline__ int mod_n(int j, int n) {
 
 template <int NL, int DA, int DB>
 __global__ void __launch_bounds__(INTERP_THREADS) interp_kernel(InterpParams P) {
-    extern __shared__ float tiles[];
+    extern __shared__ __align__(16) float tiles[];
     __shared__ int row_pre[INTERP_MAX_ROWS + 1], row_start[INTERP_MAX_ROWS];
     const int n_ios = P.n_ios, bi = P.bi;
     const int brick = blockIdx.x;
@@ -68,33 +70,50 @@ __global__ void __launch_bounds__(INTERP_THREADS) interp_kernel(InterpParams P) 
         row_start[r] = st;
         row_pre[r] = P.start[rb + c0x + ex - 1] + P.count[rb + c0x + ex - 1] - st;
     }
-    // stage the phi tiles (origin three cells below the brick's mesh origin):
-    // wrapped per-axis indices first, then one warp per tile row
+    // stage the phi tiles (origin three cells below the brick's mesh origin in
+    // y and z, four in x): wrapped per-axis indices first, then the copies
     __shared__ int widx[3][64];
     const int nwarps_s = blockDim.x >> 5, lane_s = threadIdx.x & 31, w_s = threadIdx.x >> 5;
 #pragma unroll
     for (int l = 0; l < NL; ++l) {
         const InterpLevel &L = P.lev[l];
         const int s = L.shift, n = L.n;
-        constexpr int D0 = DA;
-        const int D = l == 0 ? DA : DB;
-        (void)D0;
+        const int D = l == 0 ? DA : DB, DX = D + 2;
         __syncthreads();
-        if (threadIdx.x < 3 * D) {
-            const int a = threadIdx.x / D, k = threadIdx.x % D;
+        if (threadIdx.x < 3 * DX) {
+            const int a = threadIdx.x / DX, k = threadIdx.x % DX;
             const int c0a = a == 0 ? c0x : (a == 1 ? c0y : c0z);
-            widx[a][k] = mod_n((s >= 0 ? (c0a >> s) : (c0a << (-s))) - 3 + k, n);
+            if (a > 0 && k >= D) {
+            } else {
+                widx[a][k] = mod_n((s >= 0 ? (c0a >> s) : (c0a << (-s))) - (a == 0 ? 4 : 3) + k, n);
+            }
         }
         __syncthreads();
         float *tile = tiles + L.tile_off;
         const int64_t nn = (int64_t)n * n;
-        // asynchronous 4-byte global -> shared copies: every row in flight at once
-        for (int row = w_s; row < D * D; row += nwarps_s) {
-            const int y = row % D, z = row / D;
-            const float *src = L.phi + widx[2][z] * nn + (int64_t)widx[1][y] * n;
-            for (int x = lane_s; x < D; x += 32) {
-                const unsigned dst = (unsigned)__cvta_generic_to_shared(tile + row * D + x);
-                asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(dst), "l"(src + widx[0][x]) : "memory");
+        // 16-byte copies where the x origin, the row length and the mesh allow
+        const int x0m = (s >= 0 ? (c0x >> s) : (c0x << (-s))) - 4;
+        const bool vec = (x0m & 3) == 0 && (DX & 3) == 0 && (n & 3) == 0 && (L.tile_off & 3) == 0;
+        if (vec) {
+            // 16-byte chunks of all rows dealt to all threads: a warp copies
+            // 32 chunks (about five rows) per instruction
+            const int q = DX >> 2, chunks = D * D * q;
+            for (int c = threadIdx.x; c < chunks; c += blockDim.x) {
+                const int row = c / q, x = (c - row * q) << 2;
+                const int y = row % D, z = row / D;
+                const float *src = L.phi + widx[2][z] * nn + (int64_t)widx[1][y] * n + widx[0][x];
+                const unsigned dst = (unsigned)__cvta_generic_to_shared(tile + row * DX + x);
+                asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(src) : "memory");
+            }
+        } else {
+            for (int row = w_s; row < D * D; row += nwarps_s) {
+                const int y = row % D, z = row / D;
+                const float *src = L.phi + widx[2][z] * nn + (int64_t)widx[1][y] * n;
+                for (int x = lane_s; x < DX; x += 32) {
+                    const unsigned dst = (unsigned)__cvta_generic_to_shared(tile + row * DX + x);
+                    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(dst), "l"(src + widx[0][x])
+                                 : "memory");
+                }
             }
         }
     }
@@ -141,23 +160,21 @@ __global__ void __launch_bounds__(INTERP_THREADS) interp_kernel(InterpParams P) 
         for (int l = 0; l < NL; ++l) {
             const InterpLevel &L = P.lev[l];
             const int s = L.shift;
-            constexpr int DMAX = DA > DB ? DA : DB;
-            (void)DMAX;
-            const int D = l == 0 ? DA : DB;
+            const int D = l == 0 ? DA : DB, DX = D + 2;
             int li[3];
             float w0[3], w1[3];
 #pragma unroll
             for (int a = 0; a < 3; ++a) {
                 const int xm = s >= 0 ? (X[a] >> s) : (X[a] * (1 << (-s)));
                 const int tt = xm - (FIX >> 1);
-                const int org = (s >= 0 ? (c0[a] >> s) : (c0[a] << (-s))) - 3;
+                const int org = (s >= 0 ? (c0[a] >> s) : (c0[a] << (-s))) - (a == 0 ? 4 : 3);
                 li[a] = (tt >> FIX_BITS) - org;            // lower corner in the tile, >= 2
                 const int f = tt & (FIX - 1);
                 w1[a] = (float)f * (1.0f / FIX);
                 w0[a] = (float)(FIX - f) * (1.0f / FIX);
             }
             const float *tile = tiles + L.tile_off;
-            const int DD = D * D;
+            const int DD = D * DX;   // plane; rows are DX long
             float cx6[6], cy6[6], cz6[6];
             fd_coeffs(w0[0], w1[0], cx6);
             fd_coeffs(w0[1], w1[1], cy6);
@@ -169,7 +186,7 @@ __global__ void __launch_bounds__(INTERP_THREADS) interp_kernel(InterpParams P) 
 #pragma unroll
                 for (int by2 = 0; by2 < 2; ++by2) {
                     const float wy = by2 ? w1[1] : w0[1];
-                    const float *row = tile + (li[2] + bz2) * DD + (li[1] + by2) * D + li[0] - 2;
+                    const float *row = tile + (li[2] + bz2) * DD + (li[1] + by2) * DX + li[0] - 2;
                     float sx = 0.f;
 #pragma unroll
                     for (int m = 0; m < 6; ++m) sx += cx6[m] * row[m];
@@ -182,10 +199,10 @@ __global__ void __launch_bounds__(INTERP_THREADS) interp_kernel(InterpParams P) 
 #pragma unroll
                 for (int bx2 = 0; bx2 < 2; ++bx2) {
                     const float wx = bx2 ? w1[0] : w0[0];
-                    const float *col = tile + (li[2] + bz2) * DD + (li[1] - 2) * D + li[0] + bx2;
+                    const float *col = tile + (li[2] + bz2) * DD + (li[1] - 2) * DX + li[0] + bx2;
                     float sy = 0.f;
 #pragma unroll
-                    for (int m = 0; m < 6; ++m) sy += cy6[m] * col[m * D];
+                    for (int m = 0; m < 6; ++m) sy += cy6[m] * col[m * DX];
                     ey_ += wx * wz * sy;
                 }
             }
@@ -195,7 +212,7 @@ __global__ void __launch_bounds__(INTERP_THREADS) interp_kernel(InterpParams P) 
 #pragma unroll
                 for (int bx2 = 0; bx2 < 2; ++bx2) {
                     const float wx = bx2 ? w1[0] : w0[0];
-                    const float *col = tile + (li[2] - 2) * DD + (li[1] + by2) * D + li[0] + bx2;
+                    const float *col = tile + (li[2] - 2) * DD + (li[1] + by2) * DX + li[0] + bx2;
                     float sz = 0.f;
 #pragma unroll
                     for (int m = 0; m < 6; ++m) sz += cz6[m] * col[m * DD];
@@ -262,7 +279,7 @@ cudaError_t launch_interp(cube2_ctx *ctx, int level, const cube2_particles *p, i
         const int E = L.shift >= 0 ? (P.bi >> L.shift) : (P.bi << (-L.shift));
         I.D = E + 6;
         I.tile_off = off;
-        off += I.D * I.D * I.D;
+        off += I.D * I.D * (I.D + 2);   // x rows are D + 2 long
     }
     if (ctx->N == 0) return cudaSuccess;
     const size_t smem = (size_t)off * sizeof(float);
