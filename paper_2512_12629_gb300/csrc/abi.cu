@@ -327,7 +327,7 @@ int cube2_init_mesh(cube2_ctx **out, const cube2_config *cfg, void *stream) {
     alloc((void **)&c->nstart, (size_t)c->n_cells * 4);
     alloc((void **)&c->perm2, N * 4);
     alloc((void **)&c->big, (size_t)c->n_cells * 4);
-    alloc((void **)&c->big_n, sizeof(int));
+    alloc((void **)&c->big_n, 2 * sizeof(int));
     alloc((void **)&c->pos4, N * 16);
     alloc((void **)&c->pp_perm, N * 4);
     alloc((void **)&c->pp_stats, 4 * sizeof(unsigned long long));

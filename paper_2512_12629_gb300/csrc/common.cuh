@@ -107,7 +107,7 @@ struct cube2_ctx {
     int32_t *nstart = nullptr;     // [n_cells] its exclusive scan
     int32_t *perm2 = nullptr;      // [N] merge scratch of the segmented sort
     int32_t *big = nullptr;        // [n_cells] cells too large for the per-thread sort
-    int *big_n = nullptr;          // their number
+    int *big_n = nullptr;          // [2] their numbers (up to 1024 particles, more)
     float4 *pos4 = nullptr;        // [N] in-cell offsets as floats (+ cell id bits), PP order
     int32_t *pp_perm = nullptr;    // [N] particle index of each PP slot (sub-cell order in dense cells)
     unsigned long long *pp_stats = nullptr;  // [4] in-range ordered pairs, candidates; the same of per-lane walks

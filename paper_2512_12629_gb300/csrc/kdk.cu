@@ -217,9 +217,12 @@ __global__ void scatter_kernel(const int32_t *tcell, const int32_t *tslot, const
 }
 
 // Sort each cell's segment of perm ascending (old index = stable order).  One
-// thread per cell sorts segments of up to 32 by insertion; larger cells are
-// listed for sort_big_kernel.
+// thread per cell sorts segments of up to 32 by insertion; cells of up to
+// WARP_SORT are listed from the front of `big` for sort_mid_kernel (one warp
+// per cell), larger ones from the back for sort_big_kernel (one CTA per cell).
 constexpr int SMALL_SORT = 32;
+constexpr int WARP_SORT = 1024;
+constexpr int MID_WARPS = 8;
 constexpr int BIG_SORT_SMEM = 8192;
 constexpr int BIG_SORT_THREADS = 512;
 
@@ -230,7 +233,10 @@ __global__ void sort_small_kernel(const int32_t *count, const int32_t *start, in
     const int cnt = count[c];
     if (cnt < 2) return;
     if (cnt > SMALL_SORT) {
-        big[atomicAdd(big_n, 1)] = (int32_t)c;
+        if (cnt <= WARP_SORT)
+            big[atomicAdd(&big_n[0], 1)] = (int32_t)c;
+        else
+            big[n_cells - 1 - atomicAdd(&big_n[1], 1)] = (int32_t)c;
         return;
     }
     int32_t *seg = perm + start[c];
@@ -290,13 +296,51 @@ __device__ void merge_runs(const int32_t *a, int la, const int32_t *b, int lb, i
     }
 }
 
+// Cells of 33 .. WARP_SORT particles: one warp per cell, a bitonic sort of the
+// segment (padded to a power of two) in the warp's own shared buffer, every
+// lane exchanging pairs at each stage, with warp barriers only.
+__global__ void __launch_bounds__(MID_WARPS * 32) sort_mid_kernel(const int32_t *count, const int32_t *start,
+                                                                 int32_t *perm, const int32_t *big,
+                                                                 const int *big_n) {
+    __shared__ int32_t buf[MID_WARPS][WARP_SORT];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int32_t *s = buf[w];
+    const int total = big_n[0];
+    for (int item = blockIdx.x * MID_WARPS + w; item < total; item += gridDim.x * MID_WARPS) {
+        const int64_t c = big[item];
+        const int n = count[c];
+        int32_t *seg = perm + start[c];
+        int np2 = 64;
+        while (np2 < n) np2 <<= 1;
+        for (int i = lane; i < np2; i += 32) s[i] = i < n ? seg[i] : 0x7fffffff;
+        __syncwarp();
+        for (int k = 2; k <= np2; k <<= 1)
+            for (int j = k >> 1; j > 0; j >>= 1) {
+                for (int q = lane; q < (np2 >> 1); q += 32) {
+                    const int i = ((q & ~(j - 1)) << 1) | (q & (j - 1));   // lower index of pair q
+                    const int ixj = i | j;
+                    const bool up = (i & k) == 0;
+                    const int32_t a = s[i], b = s[ixj];
+                    if ((a > b) == up) {
+                        s[i] = b;
+                        s[ixj] = a;
+                    }
+                }
+                __syncwarp();
+            }
+        for (int i = lane; i < n; i += 32) seg[i] = s[i];
+        __syncwarp();
+    }
+}
+
 __global__ void __launch_bounds__(BIG_SORT_THREADS) sort_big_kernel(const int32_t *count, const int32_t *start,
                                                                     int32_t *perm, int32_t *perm2,
-                                                                    const int32_t *big, const int *big_n) {
+                                                                    const int32_t *big, const int *big_n,
+                                                                    int64_t n_cells) {
     __shared__ int32_t s[BIG_SORT_SMEM];
-    const int total = *big_n;
+    const int total = big_n[1];
     for (int item = blockIdx.x; item < total; item += gridDim.x) {
-        const int64_t c = big[item];
+        const int64_t c = big[n_cells - 1 - item];
         const int n = count[c];
         int32_t *seg = perm + start[c];
         if (n <= BIG_SORT_SMEM) {
@@ -513,7 +557,7 @@ cudaError_t launch_rebin(cube2_ctx *ctx, const cube2_particles *p) {
             scatter_kernel<<<(unsigned)pb, 256, 0, ctx->stream>>>(ctx->tcell, ctx->tslot, ctx->nstart, ctx->perm,
                                                                   ctx->N);
         }
-        e = cudaMemsetAsync(ctx->big_n, 0, sizeof(int), ctx->stream);
+        e = cudaMemsetAsync(ctx->big_n, 0, 2 * sizeof(int), ctx->stream);
         if (e != cudaSuccess) return e;
         {
             ProfScope prof(ctx, P_SORT, 0);
@@ -522,9 +566,12 @@ cudaError_t launch_rebin(cube2_ctx *ctx, const cube2_particles *p) {
         }
         {
             ProfScope prof(ctx, P_SORT_BIG, 0);
+            sort_mid_kernel<<<(unsigned)(ctx->num_sms * 6), MID_WARPS * 32, 0, ctx->stream>>>(
+                ctx->ncount, ctx->nstart, ctx->perm, ctx->big, ctx->big_n);
             sort_big_kernel<<<(unsigned)(ctx->num_sms * 2), BIG_SORT_THREADS, 0, ctx->stream>>>(
-                ctx->ncount, ctx->nstart, ctx->perm, ctx->perm2, ctx->big, ctx->big_n);
+                ctx->ncount, ctx->nstart, ctx->perm, ctx->perm2, ctx->big, ctx->big_n, ctx->n_cells);
         }
+        ctx->launches++;
         GatherParams G{};
         G.perm = ctx->perm;
         G.tcell = ctx->tcell;

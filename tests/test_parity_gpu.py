@@ -273,13 +273,14 @@ def test_kdk_far_movers_take_the_general_rebin_path():
     assert_force_close(got["vel"], ref["vel"], "velocity")
 
 
-def test_rebin_sorts_huge_cells_stably():
-    # 20000 particles packed into one IOS cell: the atomic slots scramble the
-    # cell, and the CTA sort (runs of 8192 merged through scratch) must restore
-    # the old order exactly; a vanishing step moves nobody.
+@pytest.mark.parametrize("n", [33, 1000, 1024, 1025, 20000])
+def test_rebin_sorts_huge_cells_stably(n):
+    # n particles packed into one IOS cell: the atomic slots scramble the cell,
+    # and the sort must restore the old order exactly (a vanishing step moves
+    # nobody): one warp per cell up to 1024 particles, one CTA above (runs of
+    # 8192 merged through scratch for 20000)
     w = CLUSTER
     rng = np.random.default_rng(5)
-    n = 20000
     cell = np.array([5.3, 9.1, 13.7])
     pos = (np.floor(cell / 4.0) * 4.0)[:, None] + rng.uniform(0.0, 4.0, size=(3, n))
     pos = np.concatenate([pos, rng.uniform(0, w.box, size=(3, 3000))], axis=1)
