@@ -439,15 +439,8 @@ static cudaError_t deposit_levels(cube2_ctx *ctx, int level, const cube2_particl
 }
 
 static cudaError_t interp_levels(cube2_ctx *ctx, int level, const cube2_particles *p, int accumulate) {
-    if (ctx->cfg.assign_order != 3) return launch_interp(ctx, level, p, accumulate);
-    cudaError_t e = cudaSuccess;
-    bool first = true;
-    for (int l = 0; l < ctx->nl && e == cudaSuccess; ++l)
-        if (level < 0 || l == level) {
-            e = launch_tsc_interp(ctx, ctx->lev[l], p, (accumulate || !first) ? 1 : 0);
-            first = false;
-        }
-    return e;
+    // CIC and TSC: the tiled gather over every level in one pass
+    return launch_interp(ctx, level, p, accumulate);
 }
 
 int cube2_deposit(cube2_ctx *ctx, int level, const cube2_particles *p) {

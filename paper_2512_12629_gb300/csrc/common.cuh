@@ -179,7 +179,6 @@ __device__ __forceinline__ int green_index(int kx, int ky, int kz, int n) {
     return c * (c + 1) * (c + 2) / 6 + b * (b + 1) / 2 + a;
 }
 cudaError_t launch_tsc_deposit(cube2_ctx *ctx, Level &L, const cube2_particles *p);
-cudaError_t launch_tsc_interp(cube2_ctx *ctx, Level &L, const cube2_particles *p, int accumulate);
 cudaError_t launch_deposit(cube2_ctx *ctx, int level, const cube2_particles *p, uint64_t *out_u64);
 cudaError_t launch_fft_forward(cube2_ctx *ctx, Level &L);          // real -> spec (x, y passes)
 cudaError_t launch_fft_z_green(cube2_ctx *ctx, Level &L);          // z fwd * G * z inv

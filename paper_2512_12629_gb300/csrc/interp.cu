@@ -53,7 +53,22 @@ __device__ __forceinline__ int mod_n(int j, int n) {
     return r < 0 ? r + n : r;
 }
 
-template <int NL, int DA, int DB>
+// 7-point coefficients of the TSC-weighted 4-point difference along one axis
+// (TSC weights w on cells i-1, i, i+1; coefficients on cells i-3 .. i+3).
+__device__ __forceinline__ void fd7_coeffs(const float w[3], float c[7]) {
+    const float a = 2.0f / 3.0f, b = 1.0f / 12.0f;
+    c[0] = b * w[0];
+    c[1] = -a * w[0] + b * w[1];
+    c[2] = -a * w[1] + b * w[2];
+    c[3] = a * (w[0] - w[2]);
+    c[4] = -b * w[0] + a * w[1];
+    c[5] = -b * w[1] + a * w[2];
+    c[6] = -b * w[2];
+}
+
+// ORD 2: CIC; ORD 3: TSC (Eq. filter), whose 7-cell reach along each axis is
+// the same tile as the CIC corner pair's 4-point difference.
+template <int NL, int DA, int DB, int ORD>
 __global__ void __launch_bounds__(INTERP_THREADS) interp_kernel(InterpParams P) {
     extern __shared__ __align__(16) float tiles[];
     __shared__ int row_pre[INTERP_MAX_ROWS + 1], row_start[INTERP_MAX_ROWS];
@@ -161,6 +176,50 @@ __global__ void __launch_bounds__(INTERP_THREADS) interp_kernel(InterpParams P) 
             const InterpLevel &L = P.lev[l];
             const int s = L.shift;
             const int D = l == 0 ? DA : DB, DX = D + 2;
+            if constexpr (ORD == 3) {
+                // TSC: cell i holding the position, weights on i-1, i, i+1
+                int ti[3];
+                float tw[3][3];
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    const int xm = s >= 0 ? (X[a] >> s) : (X[a] * (1 << (-s)));
+                    const int org = (s >= 0 ? (c0[a] >> s) : (c0[a] << (-s))) - (a == 0 ? 4 : 3);
+                    ti[a] = (xm >> FIX_BITS) - org;        // in the tile, >= 3
+                    const float d = (float)(xm & (FIX - 1)) * (1.0f / FIX) - 0.5f;
+                    tw[a][0] = 0.5f * (0.5f - d) * (0.5f - d);
+                    tw[a][1] = 0.75f - d * d;
+                    tw[a][2] = 0.5f * (0.5f + d) * (0.5f + d);
+                }
+                float c7x[7], c7y[7], c7z[7];
+                fd7_coeffs(tw[0], c7x);
+                fd7_coeffs(tw[1], c7y);
+                fd7_coeffs(tw[2], c7z);
+                const float *tile = tiles + L.tile_off;
+                const int DD = D * DX;
+                float ex_ = 0.f, ey_ = 0.f, ez_ = 0.f;
+#pragma unroll
+                for (int j1 = 0; j1 < 3; ++j1)
+#pragma unroll
+                    for (int j2 = 0; j2 < 3; ++j2) {
+                        const float *rx = tile + (ti[2] + j2 - 1) * DD + (ti[1] + j1 - 1) * DX + ti[0] - 3;
+                        const float *ry = tile + (ti[2] + j2 - 1) * DD + (ti[1] - 3) * DX + ti[0] + j1 - 1;
+                        const float *rz = tile + (ti[2] - 3) * DD + (ti[1] + j2 - 1) * DX + ti[0] + j1 - 1;
+                        float sx = 0.f, sy = 0.f, sz = 0.f;
+#pragma unroll
+                        for (int m = 0; m < 7; ++m) {
+                            sx += c7x[m] * rx[m];
+                            sy += c7y[m] * ry[m * DX];
+                            sz += c7z[m] * rz[m * DD];
+                        }
+                        ex_ += tw[1][j1] * tw[2][j2] * sx;
+                        ey_ += tw[0][j1] * tw[2][j2] * sy;
+                        ez_ += tw[0][j1] * tw[1][j2] * sz;
+                    }
+                F[0] += L.scale * ex_;
+                F[1] += L.scale * ey_;
+                F[2] += L.scale * ez_;
+                continue;
+            }
             int li[3];
             float w0[3], w1[3];
 #pragma unroll
@@ -254,6 +313,7 @@ cudaError_t launch_cellid(cube2_ctx *ctx, const cube2_particles *p) {
 }
 
 cudaError_t launch_interp(cube2_ctx *ctx, int level, const cube2_particles *p, int accumulate) {
+    const int ord = ctx->cfg.assign_order == 3 ? 3 : 2;
     InterpParams P{};
     P.off0 = p->off[0]; P.off1 = p->off[1]; P.off2 = p->off[2];
     P.cellid = ctx->cellid;
@@ -288,17 +348,18 @@ cudaError_t launch_interp(cube2_ctx *ctx, int level, const cube2_particles *p, i
     const int d0 = P.lev[0].D, d1 = P.nl > 1 ? P.lev[1].D : d0;
     cudaError_t e = cudaErrorInvalidValue;
     // tile edges are 8, 10, 14 or 22 (brick 8 or 4, shifts -2..1); the coarse level has the smaller edge
-#define CUBE2_INTERP_CASE(NL_, A_, B_)                                                              \
-    if (P.nl == NL_ && d0 == A_ && d1 == B_) {                                                      \
+#define CUBE2_INTERP_CASE_O(NL_, A_, B_, O_)                                                        \
+    if (P.nl == NL_ && d0 == A_ && d1 == B_ && ord == O_) {                                         \
         static bool attr = false;                                                                   \
         if (!attr) {                                                                                \
-            cudaFuncSetAttribute(interp_kernel<NL_, A_, B_>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
-                                 200 * 1024);                                                       \
+            cudaFuncSetAttribute(interp_kernel<NL_, A_, B_, O_>,                                     \
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);           \
             attr = true;                                                                            \
         }                                                                                           \
-        interp_kernel<NL_, A_, B_><<<(unsigned)blocks, INTERP_THREADS, smem, ctx->stream>>>(P);     \
+        interp_kernel<NL_, A_, B_, O_><<<(unsigned)blocks, INTERP_THREADS, smem, ctx->stream>>>(P); \
         e = cudaGetLastError();                                                                     \
     }
+#define CUBE2_INTERP_CASE(NL_, A_, B_) CUBE2_INTERP_CASE_O(NL_, A_, B_, 2) CUBE2_INTERP_CASE_O(NL_, A_, B_, 3)
     CUBE2_INTERP_CASE(1, 8, 8)
     CUBE2_INTERP_CASE(1, 10, 10)
     CUBE2_INTERP_CASE(1, 14, 14)
@@ -310,6 +371,7 @@ cudaError_t launch_interp(cube2_ctx *ctx, int level, const cube2_particles *p, i
     CUBE2_INTERP_CASE(2, 10, 22)
     CUBE2_INTERP_CASE(2, 14, 22)
 #undef CUBE2_INTERP_CASE
+#undef CUBE2_INTERP_CASE_O
     ctx->launches++;
     return e;
 }

@@ -10,12 +10,13 @@
 // with -1 (the overdensity of an empty cell): sums are correct to FP32
 // rounding, their last bits depend on the atomic order.
 //
-// Interpolation evaluates the 4-point difference of Eq. diff on the fly like
-// the CIC gather: along axis d the three weights and the stencil combine into
-// 7 coefficients on cells i-3 .. i+3,
+// Interpolation is the tiled gather of interp.cu (ORD = 3): it evaluates the
+// 4-point difference of Eq. diff on the fly like the CIC gather; along axis d
+// the three weights and the stencil combine into 7 coefficients on cells
+// i-3 .. i+3,
 //   c_m = sum_j w_j f_(m-j),  f = (1/12, -2/3, 0, 2/3, -1/12) on offsets -2..2,
 // applied on the 3x3 lines of the two other axes (63 potential reads per
-// component).
+// component, from the shared-memory tile).
 #include "common.cuh"
 
 namespace cube2 {
@@ -45,11 +46,7 @@ struct TscParams {
     int64_t N;
     int n_ios, n, shift;
     float scale;         // n^3 / N (deposit)
-    float hscale;        // -H (interpolation)
     float *grid;         // density (deposit)
-    const float *phi;    // potential (interpolation)
-    float *acc0, *acc1, *acc2;
-    int accumulate;
 };
 
 __device__ __forceinline__ void particle_axes(const TscParams &P, int64_t i, TscAxis a[3]) {
@@ -115,68 +112,6 @@ __global__ void __launch_bounds__(256) tsc_deposit_kernel(TscParams P) {
     }
 }
 
-// 7-point coefficients of the TSC-weighted 4-point difference along one axis.
-__device__ __forceinline__ void fd7(const float w[3], float c[7]) {
-    const float a = 2.0f / 3.0f, b = 1.0f / 12.0f;
-    c[0] = b * w[0];
-    c[1] = -a * w[0] + b * w[1];
-    c[2] = -a * w[1] + b * w[2];
-    c[3] = a * (w[0] - w[2]);
-    c[4] = -b * w[0] + a * w[1];
-    c[5] = -b * w[1] + a * w[2];
-    c[6] = -b * w[2];
-}
-
-__device__ __forceinline__ float phi_at(const float *phi, int n, int x, int y, int z) {
-    return __ldg(&phi[((int64_t)wrapc(z, n) * n + wrapc(y, n)) * n + wrapc(x, n)]);
-}
-
-// Four CTAs per SM (64 registers, a few spilled): the gather is bound by the
-// latency of its 189 potential reads per particle, and the extra resident
-// warps hide more of it (measured 26 % faster at 512^3 than 96 registers).
-#ifndef TSC_MINB
-#define TSC_MINB 4
-#endif
-__global__ void __launch_bounds__(256, TSC_MINB) tsc_interp_kernel(TscParams P) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= P.N) return;
-    TscAxis a[3];
-    particle_axes(P, i, a);
-    const int n = P.n;
-    const float *f = P.phi;
-    float cx[7], cy[7], cz[7];
-    fd7(a[0].w, cx);
-    fd7(a[1].w, cy);
-    fd7(a[2].w, cz);
-    const int ix = a[0].i, iy = a[1].i, iz = a[2].i;
-    float ex = 0.f, ey = 0.f, ez = 0.f;
-#pragma unroll 1
-    for (int j1 = 0; j1 < 3; ++j1)
-#pragma unroll 1
-        for (int j2 = 0; j2 < 3; ++j2) {
-            float sx = 0.f, sy = 0.f, sz = 0.f;
-#pragma unroll
-            for (int m = 0; m < 7; ++m) {
-                sx += cx[m] * phi_at(f, n, ix + m - 3, iy + j1 - 1, iz + j2 - 1);
-                sy += cy[m] * phi_at(f, n, ix + j1 - 1, iy + m - 3, iz + j2 - 1);
-                sz += cz[m] * phi_at(f, n, ix + j1 - 1, iy + j2 - 1, iz + m - 3);
-            }
-            ex += a[1].w[j1] * a[2].w[j2] * sx;
-            ey += a[0].w[j1] * a[2].w[j2] * sy;
-            ez += a[0].w[j1] * a[1].w[j2] * sz;
-        }
-    const float fx = P.hscale * ex, fy = P.hscale * ey, fz = P.hscale * ez;
-    if (P.accumulate) {
-        P.acc0[i] += fx;
-        P.acc1[i] += fy;
-        P.acc2[i] += fz;
-    } else {
-        P.acc0[i] = fx;
-        P.acc1[i] = fy;
-        P.acc2[i] = fz;
-    }
-}
-
 TscParams tsc_params(cube2_ctx *ctx, const Level &L, const cube2_particles *p) {
     TscParams P{};
     P.off0 = p->off[0]; P.off1 = p->off[1]; P.off2 = p->off[2];
@@ -186,10 +121,7 @@ TscParams tsc_params(cube2_ctx *ctx, const Level &L, const cube2_particles *p) {
     P.n = L.n;
     P.shift = L.shift;
     P.scale = (float)((double)L.n * L.n * L.n / (double)(ctx->N > 0 ? ctx->N : 1));
-    P.hscale = (float)(-L.H);
     P.grid = L.real;
-    P.phi = L.real;
-    P.acc0 = p->acc[0]; P.acc1 = p->acc[1]; P.acc2 = p->acc[2];
     return P;
 }
 
@@ -205,17 +137,6 @@ cudaError_t launch_tsc_deposit(cube2_ctx *ctx, Level &L, const cube2_particles *
         tsc_deposit_kernel<<<(unsigned)((ctx->N + 255) / 256), 256, 0, ctx->stream>>>(tsc_params(ctx, L, p));
         ctx->launches++;
     }
-    return cudaGetLastError();
-}
-
-// acc (=, or += with accumulate) -H TSC-gather of D * phi, phi in L.real.
-cudaError_t launch_tsc_interp(cube2_ctx *ctx, Level &L, const cube2_particles *p, int accumulate) {
-    if (ctx->N == 0) return cudaSuccess;
-    ProfScope prof(ctx, P_INTERP, L.index);
-    TscParams P = tsc_params(ctx, L, p);
-    P.accumulate = accumulate;
-    tsc_interp_kernel<<<(unsigned)((ctx->N + 255) / 256), 256, 0, ctx->stream>>>(P);
-    ctx->launches++;
     return cudaGetLastError();
 }
 
