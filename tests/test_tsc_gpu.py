@@ -23,6 +23,9 @@ from paper_2512_12629_gb300 import cube2  # noqa: E402
 
 C1_TSC = C1.with_(name="pm1-32c-64mesh-tsc", assign_order=3)
 CLUSTER_TSC = C1.with_(name="clustered-tsc", n_ios=16, levels=(Level(32, 2.0),), b_pp=0.4, assign_order=3)
+# the brick deposit's other mesh-to-IOS ratios: mesh cell = IOS cell, and a quarter of it
+CLUSTER_TSC0 = C1.with_(name="clustered-tsc-16mesh", n_ios=16, levels=(Level(16, 1.0),), b_pp=0.4, assign_order=3)
+CLUSTER_TSC2 = C1.with_(name="clustered-tsc-64mesh", n_ios=16, levels=(Level(64, 2.0),), b_pp=0.4, assign_order=3)
 
 
 def _case(name):
@@ -30,10 +33,11 @@ def _case(name):
         return C1_TSC, zeldovich_ios(C1_TSC)
     if name == "C2_SMALL_TSC":
         return C2_SMALL_TSC, zeldovich_ios(C2_SMALL_TSC)
-    return CLUSTER_TSC, random_ios(5000, 16, CLUSTER_TSC.box, seed=32, clustered=0.8)
+    w = {"CLUSTER_TSC": CLUSTER_TSC, "CLUSTER_TSC0": CLUSTER_TSC0, "CLUSTER_TSC2": CLUSTER_TSC2}[name]
+    return w, random_ios(5000, 16, w.box, seed=32, clustered=0.8)
 
 
-@pytest.mark.parametrize("name", ["C1_TSC", "C2_SMALL_TSC", "CLUSTER_TSC"])
+@pytest.mark.parametrize("name", ["C1_TSC", "C2_SMALL_TSC", "CLUSTER_TSC", "CLUSTER_TSC0", "CLUSTER_TSC2"])
 def test_tsc_path_matches_oracle(name):
     w, st = _case(name)
     n_part = int(st["count"].sum())
@@ -58,7 +62,7 @@ def test_tsc_path_matches_oracle(name):
     mag = np.linalg.norm(ref, axis=0)
     rel = err / np.maximum(mag, 1e-3 * np.sqrt(np.mean(mag ** 2)))
     assert np.median(rel) <= 1e-5 and np.quantile(rel, 0.999) <= 1e-3, (np.median(rel), np.quantile(rel, 0.999))
-    if name != "CLUSTER_TSC":        # a Zel'dovich state: one KDK step of its schedule
+    if not name.startswith("CLUSTER"):   # a Zel'dovich state: one KDK step of its schedule
         a = w.scale_factors()
         ctx.kdk_step(p, a[0], a[1])
         ctx.check()
