@@ -193,11 +193,30 @@ __device__ __forceinline__ void x_r2c_block(float2 *S, const float *__restrict__
                                             int64_t nrows, int kxp, const float2 *__restrict__ tw, int64_t vb) {
     constexpr int L = Tile<N>::L, LP = Tile<N>::LP, T = Tile<N>::T;
     const int64_t row0 = vb * 2 * L;
-    for (int i = threadIdx.x; i < 2 * L * N; i += T) {
-        const int r = i / N, x = i % N;
-        const int64_t row = row0 + r;
-        const float v = row < nrows ? __ldg(&in[row * N + x]) : 0.0f;
-        reinterpret_cast<float *>(&S[x * LP + (r >> 1)])[r & 1] = v;
+    if constexpr (N % 4 == 0) {
+        // four x of the two rows of a line per thread (16-byte loads, 8-byte
+        // shared stores), lanes over the lines: 8 % faster than one element per
+        // thread at 512^3 (the inverse pass's matching 16-byte stores, 16 rows
+        // per warp instruction, measured 1.6x slower, so it keeps the original)
+        constexpr int Q = N / 4;
+        for (int i = threadIdx.x; i < L * Q; i += T) {
+            const int l = i % L, x = 4 * (i / L);
+            const int64_t ra = row0 + 2 * l;
+            const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+            const float4 a = ra < nrows ? __ldg(reinterpret_cast<const float4 *>(in + ra * N + x)) : z4;
+            const float4 b = ra + 1 < nrows ? __ldg(reinterpret_cast<const float4 *>(in + (ra + 1) * N + x)) : z4;
+            S[(x + 0) * LP + l] = make_float2(a.x, b.x);
+            S[(x + 1) * LP + l] = make_float2(a.y, b.y);
+            S[(x + 2) * LP + l] = make_float2(a.z, b.z);
+            S[(x + 3) * LP + l] = make_float2(a.w, b.w);
+        }
+    } else {
+        for (int i = threadIdx.x; i < 2 * L * N; i += T) {
+            const int r = i / N, x = i % N;
+            const int64_t row = row0 + r;
+            const float v = row < nrows ? __ldg(&in[row * N + x]) : 0.0f;
+            reinterpret_cast<float *>(&S[x * LP + (r >> 1)])[r & 1] = v;
+        }
     }
     __syncthreads();
     fft_lines<N, L, LP, T, 1, false>(S, tw);
@@ -248,10 +267,12 @@ __device__ __forceinline__ void x_c2r_block(float2 *S, const float2 *__restrict_
     }
     __syncthreads();
     fft_lines<N, L, LP, T, 1, true>(S, tw);
-    for (int i = threadIdx.x; i < 2 * L * N; i += T) {
-        const int r = i / N, x = i % N;
-        const int64_t row = row0 + r;
-        if (row < nrows) out[row * N + x] = reinterpret_cast<const float *>(&S[x * LP + (r >> 1)])[r & 1];
+    {
+        for (int i = threadIdx.x; i < 2 * L * N; i += T) {
+            const int r = i / N, x = i % N;
+            const int64_t row = row0 + r;
+            if (row < nrows) out[row * N + x] = reinterpret_cast<const float *>(&S[x * LP + (r >> 1)])[r & 1];
+        }
     }
 }
 
