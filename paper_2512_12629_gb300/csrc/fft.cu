@@ -197,7 +197,7 @@ __device__ __forceinline__ void x_r2c_block(float2 *S, const float *__restrict__
         // four x of the two rows of a line per thread (16-byte loads, 8-byte
         // shared stores), lanes over the lines: 8 % faster than one element per
         // thread at 512^3 (the inverse pass's matching 16-byte stores, 16 rows
-        // per warp instruction, measured 1.6x slower, so it keeps the original)
+        // per warp instruction, measured 1.6x slower)
         constexpr int Q = N / 4;
         for (int i = threadIdx.x; i < L * Q; i += T) {
             const int l = i % L, x = 4 * (i / L);
@@ -267,12 +267,14 @@ __device__ __forceinline__ void x_c2r_block(float2 *S, const float2 *__restrict_
     }
     __syncthreads();
     fft_lines<N, L, LP, T, 1, true>(S, tw);
-    {
-        for (int i = threadIdx.x; i < 2 * L * N; i += T) {
-            const int r = i / N, x = i % N;
-            const int64_t row = row0 + r;
-            if (row < nrows) out[row * N + x] = reinterpret_cast<const float *>(&S[x * LP + (r >> 1)])[r & 1];
-        }
+    // one x of a line per thread: its two rows from one 8-byte shared load,
+    // written by two coalesced 4-byte stores
+    for (int i = threadIdx.x; i < L * N; i += T) {
+        const int l = i / N, x = i % N;
+        const int64_t ra = row0 + 2 * l;
+        const float2 v = S[x * LP + l];
+        if (ra < nrows) out[ra * N + x] = v.x;
+        if (ra + 1 < nrows) out[(ra + 1) * N + x] = v.y;
     }
 }
 
