@@ -115,6 +115,7 @@ void free_ctx(cube2_ctx *c) {
         cudaFree(c->lev[l].real);
         cudaFree(c->lev[l].spec);
         cudaFree(c->lev[l].green);
+        cudaFree(c->lev[l].green2);
         cudaFree(c->lev[l].tw);
     }
     cudaFree(c->cellid);
@@ -313,6 +314,10 @@ int cube2_init_mesh(cube2_ctx **out, const cube2_config *cfg, void *stream) {
         alloc((void **)&L.spec, nh * sizeof(float2));
         L.green_len = green_table_len(L.n);
         alloc((void **)&L.green, (size_t)L.green_len * sizeof(float));
+        if (L.n <= 1024) {
+            const size_t h = (size_t)(L.n / 2 + 1);
+            alloc((void **)&L.green2, h * h * (size_t)L.kxp * sizeof(float));
+        }
         alloc((void **)&L.tw, (size_t)L.n * sizeof(float2));
         if (e == cudaSuccess) e = cudaMemsetAsync(L.spec, 0, nh * sizeof(float2), c->stream);
     }
@@ -400,6 +405,7 @@ int cube2_set_green(cube2_ctx *ctx, int level, const char *cache_path) {
                 fclose(f);
                 if (ok) {
                     cudaError_t e = cudaMemcpyAsync(L.green, buf.data(), nh * 4, cudaMemcpyHostToDevice, ctx->stream);
+                    if (e == cudaSuccess) e = launch_green_fold(ctx, L);
                     if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
                     if (e != cudaSuccess) return cuda_error(ctx, e, "green cache upload");
                     L.has_green = true;
@@ -411,6 +417,7 @@ int cube2_set_green(cube2_ctx *ctx, int level, const char *cache_path) {
         }
     }
     cudaError_t e = launch_green(ctx, L, ctx->cfg.alias_max, ctx->cfg.assign_order);
+    if (e == cudaSuccess) e = launch_green_fold(ctx, L);
     if (e != cudaSuccess) return cuda_error(ctx, e, "green kernel");
     L.has_green = true;
     if (cache_path && cache_path[0]) {

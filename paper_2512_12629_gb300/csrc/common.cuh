@@ -47,6 +47,9 @@ struct Level {
     float *real = nullptr;   // [n^3]  density, then potential
     float2 *spec = nullptr;  // [n][n][kxp] half spectrum scratch
     float *green = nullptr;  // symmetry-reduced Green's table (1/n^3 folded in), see green_index
+    // the same entries folded in ky and kz only, [n/2+1 (kz)][n/2+1 (ky)][kxp]
+    // (zero past kx = n/2): read by the z pass with plain indices (n <= 1024)
+    float *green2 = nullptr;
     int64_t green_len = 0;   // entries of the reduced table
     float2 *tw = nullptr;    // [n] twiddles exp(-2 pi i k / n)
     uint64_t mean_int = 0;   // M = floor(N 2^48 / n^3)
@@ -160,7 +163,8 @@ int cuda_error(cube2_ctx *ctx, cudaError_t e, const char *what);
 // the cudaError_t of its last launch and bumps ctx->launches.
 cudaError_t launch_init_twiddles(cube2_ctx *ctx, Level &L);
 cudaError_t launch_green(cube2_ctx *ctx, Level &L, int alias, int order);
-cudaError_t launch_green_expand(cube2_ctx *ctx, const Level &L, float *out);   // full [n][n][n/2+1] copy
+cudaError_t launch_green_expand(cube2_ctx *ctx, const Level &L, float *out);
+cudaError_t launch_green_fold(cube2_ctx *ctx, const Level &L);   // full [n][n][n/2+1] copy
 
 // Eq. (Gk) is even in every k_d and symmetric under permutations of the axes
 // (cubic mesh, symmetric image sums), so the table is stored once per sorted

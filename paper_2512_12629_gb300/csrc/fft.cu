@@ -334,7 +334,8 @@ __global__ void __launch_bounds__(Tile<N>::T) fft_y(float2 *__restrict__ data, i
 
 // ------------------------------------------------------------ Z (+ Green)
 // GMODE 0: forward z FFT only; 1: G from a full [kz][ky][kxp] table; 2: G
-// from the symmetry-reduced table (green_index).
+// from the symmetry-reduced table (green_index); 3: G from the table folded in
+// ky and kz ([kz <= N/2][ky <= N/2][kxp], the reduced table's entries).
 template <int N, int GMODE>
 __device__ __forceinline__ void z_block(float2 *S, float2 *__restrict__ data, const float *__restrict__ green,
                                         int kxp, const float2 *__restrict__ tw, int64_t vb) {
@@ -360,6 +361,10 @@ __device__ __forceinline__ void z_block(float2 *S, float2 *__restrict__ data, co
             float2 gv;
             if (GMODE == 1) {
                 gv = __ldg(reinterpret_cast<const float2 *>(&g[z * zstride + l2]));
+            } else if (GMODE == 3) {
+                const int zf = z <= N / 2 ? z : N - z, kyf = ky <= N / 2 ? (int)ky : N - (int)ky;
+                gv = __ldg(reinterpret_cast<const float2 *>(
+                    &green[((int64_t)zf * (N / 2 + 1) + kyf) * kxp + tx * L + l2]));
             } else {
                 const int kx = tx * L + l2;   // padding columns (kx > N/2) hold zeros
                 gv.x = kx <= N / 2 ? __ldg(&green[green_index(kx, (int)ky, z, N)]) : 0.0f;
@@ -428,7 +433,10 @@ struct Launcher {
     static cudaError_t z_pass_v(cube2_ctx *ctx, Level &Lv, bool green) {
         const unsigned bz = pass_grid(ctx, Lv, (int64_t)Lv.batch * N * (Lv.kxp / Tile<N>::L));
         ProfScope prof(ctx, B ? -1 : P_FFT_Z_GREEN, Lv.index);
-        if (green)
+        if (green && !B && Lv.green2)
+            fft_z<N, 3, false><<<bz, Tile<N>::T, Tile<N>::SMEMY, ctx->stream>>>(Lv.spec, Lv.green2, Lv.kxp, Lv.tw,
+                                                                              Lv.active);
+        else if (green)
             fft_z<N, 2, B><<<bz, Tile<N>::T, Tile<N>::SMEMY, ctx->stream>>>(Lv.spec, Lv.green, Lv.kxp, Lv.tw, Lv.active);
         else
             fft_z<N, 0, B><<<bz, Tile<N>::T, Tile<N>::SMEMY, ctx->stream>>>(Lv.spec, nullptr, Lv.kxp, Lv.tw, Lv.active);
@@ -488,6 +496,7 @@ struct Launcher {
         if (done) return;
         setup_v<false>();
         cudaFuncSetAttribute(fft_z<N, 1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Tile<N>::SMEM);
+        cudaFuncSetAttribute(fft_z<N, 3, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Tile<N>::SMEM);
         if constexpr (N <= BATCH_MAX_N) setup_v<true>();
         done = true;
     }

@@ -133,6 +133,16 @@ __global__ void green_expand_kernel(const float *__restrict__ G, float *__restri
     out[idx] = G[green_index(kx, ky, kz, n)];
 }
 
+// [kz <= n/2][ky <= n/2][kx < kxp] from the reduced table (zero past kx = n/2).
+__global__ void green_fold_kernel(const float *__restrict__ G, float *__restrict__ out, int n, int kxp) {
+    const int h = n / 2 + 1;
+    const int64_t total = (int64_t)h * h * kxp;
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= total) return;
+    const int kx = (int)(idx % kxp), ky = (int)((idx / kxp) % h), kz = (int)(idx / ((int64_t)kxp * h));
+    out[idx] = kx <= n / 2 ? G[green_index(kx, ky, kz, n)] : 0.0f;
+}
+
 __global__ void twiddle_kernel(float2 *tw, int n) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n) return;
@@ -152,6 +162,14 @@ cudaError_t launch_init_twiddles(cube2_ctx *ctx, Level &L) {
 cudaError_t launch_green_expand(cube2_ctx *ctx, const Level &L, float *out) {
     const int64_t total = (int64_t)L.n * L.n * (L.n / 2 + 1);
     green_expand_kernel<<<(unsigned)((total + 255) / 256), 256, 0, ctx->stream>>>(L.green, out, L.n);
+    ctx->launches++;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_green_fold(cube2_ctx *ctx, const Level &L) {
+    if (!L.green2) return cudaSuccess;
+    const int64_t h = L.n / 2 + 1, total = h * h * L.kxp;
+    green_fold_kernel<<<(unsigned)((total + 255) / 256), 256, 0, ctx->stream>>>(L.green, L.green2, L.n, L.kxp);
     ctx->launches++;
     return cudaGetLastError();
 }
