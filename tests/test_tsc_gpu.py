@@ -26,6 +26,8 @@ CLUSTER_TSC = C1.with_(name="clustered-tsc", n_ios=16, levels=(Level(32, 2.0),),
 # the brick deposit's other mesh-to-IOS ratios: mesh cell = IOS cell, and a quarter of it
 CLUSTER_TSC0 = C1.with_(name="clustered-tsc-16mesh", n_ios=16, levels=(Level(16, 1.0),), b_pp=0.4, assign_order=3)
 CLUSTER_TSC2 = C1.with_(name="clustered-tsc-64mesh", n_ios=16, levels=(Level(64, 2.0),), b_pp=0.4, assign_order=3)
+# 12^3 IOS cells: bricks of 8 and 4 cells (a partial brick on every axis)
+RAGGED_TSC = C1.with_(name="ragged-tsc", box=48.0, n_ios=12, levels=(Level(24, 2.0),), b_pp=0.4, assign_order=3)
 
 
 def _case(name):
@@ -33,11 +35,14 @@ def _case(name):
         return C1_TSC, zeldovich_ios(C1_TSC)
     if name == "C2_SMALL_TSC":
         return C2_SMALL_TSC, zeldovich_ios(C2_SMALL_TSC)
+    if name == "RAGGED_TSC":
+        return RAGGED_TSC, random_ios(12 ** 3, 12, RAGGED_TSC.box, seed=31, clustered=0.3)
     w = {"CLUSTER_TSC": CLUSTER_TSC, "CLUSTER_TSC0": CLUSTER_TSC0, "CLUSTER_TSC2": CLUSTER_TSC2}[name]
     return w, random_ios(5000, 16, w.box, seed=32, clustered=0.8)
 
 
-@pytest.mark.parametrize("name", ["C1_TSC", "C2_SMALL_TSC", "CLUSTER_TSC", "CLUSTER_TSC0", "CLUSTER_TSC2"])
+@pytest.mark.parametrize("name", ["C1_TSC", "C2_SMALL_TSC", "CLUSTER_TSC", "CLUSTER_TSC0", "CLUSTER_TSC2",
+                                  "RAGGED_TSC"])
 def test_tsc_path_matches_oracle(name):
     w, st = _case(name)
     n_part = int(st["count"].sum())
@@ -62,7 +67,7 @@ def test_tsc_path_matches_oracle(name):
     mag = np.linalg.norm(ref, axis=0)
     rel = err / np.maximum(mag, 1e-3 * np.sqrt(np.mean(mag ** 2)))
     assert np.median(rel) <= 1e-5 and np.quantile(rel, 0.999) <= 1e-3, (np.median(rel), np.quantile(rel, 0.999))
-    if not name.startswith("CLUSTER"):   # a Zel'dovich state: one KDK step of its schedule
+    if not name.startswith(("CLUSTER", "RAGGED")):   # a Zel'dovich state: one KDK step of its schedule
         a = w.scale_factors()
         ctx.kdk_step(p, a[0], a[1])
         ctx.check()
