@@ -189,26 +189,36 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(rows)}
 
 
+def numa_cpus(bus_id, root="/sys"):
+    """(node, CPUs) of the NUMA node sysfs names for the PCI device `bus_id`
+    ("DDDDDDDD:BB:DD.F" as torch reports it), or None."""
+    try:
+        dom, bus, devfn = bus_id.lower().split(":")
+        node = int(open(f"{root}/bus/pci/devices/{dom[-4:]}:{bus}:{devfn}/numa_node").read())
+        if node < 0:
+            return None
+        cpus = set()
+        for part in open(f"{root}/devices/system/node/node{node}/cpulist").read().strip().split(","):
+            if part:
+                lo, _, hi = part.partition("-")
+                cpus.update(range(int(lo), int(hi or lo) + 1))
+        return (node, cpus) if cpus else None
+    except (OSError, ValueError, AttributeError):
+        return None
+
+
 def bind_local_numa(bus_id):
     """Restrict this process to the CPUs of the NUMA node the GPU hangs off (as
     sysfs reports it), so that pinned host buffers allocated afterwards are
     local to that node; returns the node or None (nothing changed)."""
-    try:
-        dom, bus, devfn = bus_id.lower().split(":")
-        node = int(open(f"/sys/bus/pci/devices/{dom[-4:]}:{bus}:{devfn}/numa_node").read())
-        if node < 0:
-            return None
-        cpus = set()
-        for part in open(f"/sys/devices/system/node/node{node}/cpulist").read().strip().split(","):
-            if part:
-                lo, _, hi = part.partition("-")
-                cpus.update(range(int(lo), int(hi or lo) + 1))
-        if not cpus:
-            return None
-        os.sched_setaffinity(0, cpus)
-        return node
-    except (OSError, ValueError, AttributeError):
+    found = numa_cpus(bus_id)
+    if not found:
         return None
+    try:
+        os.sched_setaffinity(0, found[1])
+    except OSError:
+        return None
+    return found[0]
 
 
 def bus_id_of(dev):

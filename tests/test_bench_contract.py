@@ -36,3 +36,21 @@ def test_arms_without_oracle_say_so():
     for wl in ("c4-ensemble-64x20", "c3-adjoint-128c-256mesh", "c5-force-1024c-512x2048mesh"):
         d = _run("--impl", "reference", "--workload", wl)
         assert d["impl"] == "reference" and "unavailable" in d
+
+
+def test_numa_node_of_the_gpu_from_sysfs(tmp_path):
+    # the e2e leg binds to the CPUs of the GPU's NUMA node before allocating its
+    # pinned host buffers; the node and its CPU list come from sysfs
+    sys.path.insert(0, ROOT)
+    import bench
+    dev = tmp_path / "bus" / "pci" / "devices" / "0009:01:00.0"
+    dev.mkdir(parents=True)
+    (dev / "numa_node").write_text("1\n")
+    node = tmp_path / "devices" / "system" / "node" / "node1"
+    node.mkdir(parents=True)
+    (node / "cpulist").write_text("0-3,8,10-11\n")
+    assert bench.numa_cpus("00000009:01:00.0", root=str(tmp_path)) == (1, {0, 1, 2, 3, 8, 10, 11})
+    (dev / "numa_node").write_text("-1\n")                      # no affinity reported: nothing to bind
+    assert bench.numa_cpus("00000009:01:00.0", root=str(tmp_path)) is None
+    assert bench.numa_cpus("00000009:02:00.0", root=str(tmp_path)) is None   # no such device
+    assert bench.numa_cpus(None, root=str(tmp_path)) is None
