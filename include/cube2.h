@@ -153,8 +153,12 @@ int cube2_init_mesh(cube2_ctx **ctx, const cube2_config *cfg, void *stream);
  * G is even in each k_d and symmetric under axis permutations, so it is
  * computed and stored once per sorted triple 0 <= a <= b <= c <= n/2 of
  * |m_x|, |m_y|, |m_z| (entry c(c+1)(c+2)/6 + b(b+1)/2 + a, FP32,
- * (n/2+1)(n/2+2)(n/2+3)/6 entries: 11 MB at n = 512, 0.7 GB at n = 2048) and
- * looked up by the z pass; cube2_get_green expands it.
+ * (n/2+1)(n/2+2)(n/2+3)/6 entries: 11 MB at n = 512, 0.7 GB at n = 2048);
+ * cube2_get_green expands it.  For n <= 1024 the context also keeps the same
+ * entries folded in k_y and k_z only ([n/2+1][n/2+1][n/2+1 padded to a
+ * multiple of 16], 72 MB at n = 512), built here from the reduced table, which
+ * the z pass reads with plain indices; larger meshes look up the reduced
+ * table directly.
  * With cfg.iso_length > 0 the coarsest level's images are weighted by
  * 1 - sinc(|k_n| iso_length) (Eq. isok, isolated boundary conditions).
  * cache_path (optional, may be NULL) names a file: if it holds a table for
