@@ -33,6 +33,10 @@ RAGGED = C1.with_(name="ragged-12", n_p=12, box=24.0, n_ios=12,
                   levels=(Level(12, 3.0), Level(24, 2.0)), b_pp=0.2)
 # clustered random particles in a C1-like box (uneven cell counts)
 CLUSTER = C1.with_(name="clustered", n_ios=16, levels=(Level(32, 2.0),), b_pp=0.4)
+# a coarse mesh at half and a fine mesh at four times the IOS resolution: 4-cell
+# bricks, whose coarse tiles start off the 4-cell alignment of the 16-byte
+# tile copies in half of the bricks (the gather's 4-byte staging path)
+MIXED = C1.with_(name="mixed-8-64", n_ios=16, levels=(Level(8, 3.5), Level(64, 2.0)), b_pp=0.2)
 
 
 def rel_err(f_gpu, f_or):
@@ -58,6 +62,8 @@ def _state(name):
         return RAGGED, random_ios(12 ** 3, 12, RAGGED.box, seed=31, clustered=0.3)
     if name == "CLUSTER":
         return CLUSTER, random_ios(5000, 16, CLUSTER.box, seed=32, clustered=0.8)
+    if name == "MIXED":
+        return MIXED, random_ios(5000, 16, MIXED.box, seed=34, clustered=0.5)
     if name == "C4_24":
         # an ensemble box with a radix-3 mesh: 24^3 particles, 48^3 mesh
         from inputs.workloads import c4_ensemble
@@ -91,7 +97,7 @@ def case(name):
     return _CACHE[name]
 
 
-ALL = ["C1", "C2_SMALL", "RAGGED", "CLUSTER", "DENSE", "C4_24"]
+ALL = ["C1", "C2_SMALL", "RAGGED", "CLUSTER", "DENSE", "C4_24", "MIXED"]
 
 
 @pytest.mark.parametrize("name", ALL)
