@@ -86,24 +86,27 @@ __global__ void __launch_bounds__(INTERP_THREADS) interp_kernel(InterpParams P) 
         row_pre[r] = P.start[rb + c0x + ex - 1] + P.count[rb + c0x + ex - 1] - st;
     }
     // stage the phi tiles (origin three cells below the brick's mesh origin in
-    // y and z, four in x): wrapped per-axis indices first, then the copies
-    __shared__ int widx[3][64];
+    // y and z, four in x): the wrapped per-axis indices of every level first,
+    // then the copies
+    static_assert(DA + 2 <= 32 && DB + 2 <= 32, "tile rows longer than the index table");
+    __shared__ int widx[NL][3][32];
+    for (int q = threadIdx.x; q < NL * 96; q += blockDim.x) {
+        const int l = q / 96, a = (q / 32) % 3, k = q % 32;
+        const int D = l == 0 ? DA : DB;
+        if (k < (a == 0 ? D + 2 : D)) {
+            const InterpLevel &L = P.lev[l];
+            const int c0a = a == 0 ? c0x : (a == 1 ? c0y : c0z);
+            widx[l][a][k] = mod_n((L.shift >= 0 ? (c0a >> L.shift) : (c0a << (-L.shift))) - (a == 0 ? 4 : 3) + k, L.n);
+        }
+    }
+    __syncthreads();
     const int nwarps_s = blockDim.x >> 5, lane_s = threadIdx.x & 31, w_s = threadIdx.x >> 5;
 #pragma unroll
     for (int l = 0; l < NL; ++l) {
         const InterpLevel &L = P.lev[l];
         const int s = L.shift, n = L.n;
         const int D = l == 0 ? DA : DB, DX = D + 2;
-        __syncthreads();
-        if (threadIdx.x < 3 * DX) {
-            const int a = threadIdx.x / DX, k = threadIdx.x % DX;
-            const int c0a = a == 0 ? c0x : (a == 1 ? c0y : c0z);
-            if (a > 0 && k >= D) {
-            } else {
-                widx[a][k] = mod_n((s >= 0 ? (c0a >> s) : (c0a << (-s))) - (a == 0 ? 4 : 3) + k, n);
-            }
-        }
-        __syncthreads();
+        const int (*wi)[32] = widx[l];
         float *tile = tiles + L.tile_off;
         const int64_t nn = (int64_t)n * n;
         // 16-byte copies where the x origin, the row length and the mesh allow
@@ -116,24 +119,24 @@ __global__ void __launch_bounds__(INTERP_THREADS) interp_kernel(InterpParams P) 
             for (int c = threadIdx.x; c < chunks; c += blockDim.x) {
                 const int row = c / q, x = (c - row * q) << 2;
                 const int y = row % D, z = row / D;
-                const float *src = L.phi + widx[2][z] * nn + (int64_t)widx[1][y] * n + widx[0][x];
+                const float *src = L.phi + wi[2][z] * nn + (int64_t)wi[1][y] * n + wi[0][x];
                 const unsigned dst = (unsigned)__cvta_generic_to_shared(tile + row * DX + x);
                 asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(src) : "memory");
             }
         } else {
             for (int row = w_s; row < D * D; row += nwarps_s) {
                 const int y = row % D, z = row / D;
-                const float *src = L.phi + widx[2][z] * nn + (int64_t)widx[1][y] * n;
+                const float *src = L.phi + wi[2][z] * nn + (int64_t)wi[1][y] * n;
                 for (int x = lane_s; x < DX; x += 32) {
                     const unsigned dst = (unsigned)__cvta_generic_to_shared(tile + row * DX + x);
-                    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(dst), "l"(src + widx[0][x])
+                    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(dst), "l"(src + wi[0][x])
                                  : "memory");
                 }
             }
         }
     }
-    asm volatile("cp.async.wait_all;\n" ::: "memory");
-    __syncthreads();
+    // the row scan (row sizes written before the barrier above) while the
+    // copies are in flight; one barrier then covers both
     if (threadIdx.x < 32) {            // exclusive scan of the row sizes
         const int lane = threadIdx.x;
         const int per = (nrows + 31) / 32;
@@ -149,6 +152,7 @@ __global__ void __launch_bounds__(INTERP_THREADS) interp_kernel(InterpParams P) 
         for (int i = b0; i < b1; ++i) { const int v = row_pre[i]; row_pre[i] = run; run += v; }
         if (lane == 31) row_pre[nrows] = incl;
     }
+    asm volatile("cp.async.wait_all;\n" ::: "memory");
     __syncthreads();
     const int total = row_pre[nrows];
     const int nwarps = blockDim.x >> 5, lane = threadIdx.x & 31, w = threadIdx.x >> 5;
